@@ -1,0 +1,207 @@
+/*
+ * bigmeans.h -- C ABI of libbigmeans, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of competitive-sample-size Big-means clustering
+ * (R. Mussabayev, R. Mussabayev, "Superior Parallel Big Data Clustering
+ * through Competitive Stochastic Sample Size Optimization in Big-means",
+ * arXiv 2403.18766).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Data X is row-major m x n float32 (n fastest).  Centroids C are row-major
+ *   k x n float32.  Labels are int32.  Sample indices are int64.
+ * - Pointers named *_dev are CUDA device pointers owned by the caller; they
+ *   must stay valid until the call returns.  Pointers named *_host are host
+ *   pointers.  The library allocates its own workspace inside each call (or
+ *   inside a bm_fit context) and frees it before returning (or on destroy).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   All device work is enqueued on it.  Every call returns only after its
+ *   device work has completed, so outputs are ready on return.
+ * - Errors are reported by status code only; nothing is thrown across the
+ *   ABI.  bm_last_error() returns a thread-local message for the last
+ *   non-OK status of the calling thread.
+ * - Limits: 1 <= n <= 64, 1 <= k, k <= s_min, m < 2^31, and the centroid
+ *   accumulators of one cluster must fit in shared memory
+ *   (k * round_up(n) * 32 bytes <= 200 KB; e.g. k <= 100 at n = 64).
+ *   Non-finite values in X are rejected with BM_EINVAL.
+ *
+ * Numeric definition ("exact mode", the only mode so far)
+ * -------------------------------------------------------
+ * The paper fixes no precision, so per-point decisions are taken in FP32 with
+ * one fixed operation order and every sum that feeds a decision is exact:
+ *   d(x, c)   = FP32 direct form: t = x_d - c_d, acc = acc + t*t over
+ *               ascending d, each operation rounded, no fused multiply-add;
+ *   label(x)  = argmin_j d(x, c_j), lowest j on ties;
+ *   f(C, P)   = the exact sum over x in P of d(x, c_label(x)), rounded once to
+ *               double (Eq. 1 of the paper);
+ *   centroid  = float( double(exact sum of members) / count ); an empty
+ *               cluster keeps its centroid and is degenerate.
+ * Exact sums are formed in integer fixed point; a value too small for the
+ * fixed-point grid of its data set (below 2^-72 of the largest |x| for
+ * coordinates, or below 2^-63 of the largest squared coordinate for distances)
+ * is truncated and counted in bm_report.inexact_terms.
+ */
+#ifndef BIGMEANS_H
+#define BIGMEANS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BM_OK = 0,
+    BM_EINVAL = 1,     /* bad argument, unsupported size, non-finite X      */
+    BM_ENOMEM = 2,     /* workspace allocation failed                       */
+    BM_ECUDA = 3,      /* a CUDA runtime call failed (message has details)  */
+    BM_ETIMEOUT = 4,   /* a bounded device wait ran out                     */
+    BM_EINTERNAL = 5   /* sampling ran out of draws or another device flag  */
+} bm_status;
+
+/* Purposes of the counter-based random streams (Philox4x64-10, Salmon et al.
+ * SC'11).  key = {seed, purpose<<56 | worker<<40 | round<<16 | pass},
+ * counter = {draw index, sub-stream, 0, 0}.  Bounded integers use Lemire's
+ * multiply-and-reject rule on the four words of one block. */
+typedef enum {
+    BM_RNG_SIZE = 1,   /* s_w of a (worker, round)               Alg. 1      */
+    BM_RNG_EVAL = 2,   /* sample that recomputes f_hat_w         Alg. 1      */
+    BM_RNG_PASS = 3,   /* sample S_w of a pass                   Sec. 4.1    */
+    BM_RNG_KPP = 4,    /* K-means++ draws of a pass              Sec. 4.1, 5 */
+    BM_RNG_FINAL = 5   /* common sample of size s_opt            Alg. 1      */
+} bm_rng_purpose;
+
+/* Sample-size policy of Algorithm 1: each round every worker draws s_w
+ * uniformly from [s_min, s_max] (set_len == 0) or uniformly from set[]
+ * (set_len > 0, at most 16 entries).  s_max and the set entries are clipped
+ * to m (Sec. 5: s_max = min(2 s, m)). */
+typedef struct {
+    int64_t s_min;
+    int64_t s_max;
+    int64_t set[16];
+    int32_t set_len;
+    int32_t workers;   /* W, competing workers (>= 1)                       */
+    int32_t passes;    /* p, passes per round (Sec. 5: 10)                  */
+} bm_sample_policy;
+
+/* Stop conditions (Alg. 1 round count T and/or a wall-clock budget) and the
+ * K-means settings of Sec. 5. */
+typedef struct {
+    int32_t rounds;                /* T; 0 = unlimited (seconds must be > 0)  */
+    double seconds;                /* wall budget; 0 = none                   */
+    int32_t max_lloyd;             /* Lloyd iterations cap (Sec. 5: 300)      */
+    double tol;                    /* relative objective tolerance (1e-4)     */
+    int32_t kpp_candidates;        /* K-means++ trials per centroid (3)       */
+    int32_t eval_full_each_round;  /* 1: after each round evaluate f(C, X) of
+                                      the worker with least f_hat_w and keep
+                                      the least value seen (the incumbent)    */
+} bm_budget;
+
+/* Filled on return when the caller passes a non-NULL pointer. */
+typedef struct {
+    double f_full;          /* f(C_best, X), Eq. (1)                          */
+    double f_incumbent;     /* least full f seen over rounds (or f_full)      */
+    int64_t s_opt;          /* rounded mean of L                              */
+    int32_t best_worker;    /* argmin of the common recheck                   */
+    int32_t rounds_done;    /* rounds completed by every worker               */
+    int64_t passes_done;    /* passes over all workers                        */
+    int64_t lloyd_iters;    /* centroid updates over all Lloyd runs           */
+    int64_t assign_rows;    /* rows assigned inside Lloyd runs (sum s_w per
+                               assignment); Lloyd pts*k = assign_rows * k     */
+    int64_t accepts;        /* |L|                                            */
+    int64_t L_sum;          /* sum of L                                       */
+    int64_t rescored_rows;  /* rows whose FP32 expanded-form argmin was not
+                               certified and were re-scored in direct form    */
+    int64_t inexact_terms;  /* values truncated by the fixed-point grids      */
+    double t_total_s;       /* wall time of the call                          */
+} bm_report;
+
+/* ---------------------------------------------------------------------------
+ * bigmeans_fit -- Algorithm 1 end to end (Sec. 4.2, 4.3; settings Sec. 5).
+ * X_dev: m x n float32 device, 16-byte aligned.  C_out_dev: k x n float32
+ * device (written).  labels_out_dev: m int32 device, may be NULL.
+ * Returns C_best, the labels Y of X and f(C_best, X) (in the report).
+ * ------------------------------------------------------------------------- */
+bm_status bigmeans_fit(const float* X_dev, int64_t m, int32_t n, int32_t k,
+                       const bm_sample_policy* policy, const bm_budget* budget,
+                       uint64_t seed, void* stream,
+                       float* C_out_dev, int32_t* labels_out_dev,
+                       bm_report* report_out);
+
+/* Same as bigmeans_fit with host buffers: X_host is copied to the device,
+ * C_out_host (k x n) and labels_out_host (m, may be NULL) are copied back,
+ * all inside the call. */
+bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k,
+                            const bm_sample_policy* policy, const bm_budget* budget,
+                            uint64_t seed, void* stream,
+                            float* C_out_host, int32_t* labels_out_host,
+                            bm_report* report_out);
+
+/* ---------------------------------------------------------------------------
+ * Staged fit: the same computation as bigmeans_fit, split so that rounds can
+ * be run (and timed) one batch at a time.  bm_fit_create validates X,
+ * allocates the workspace and initialises the workers (Alg. 1
+ * initialisation); bm_fit_rounds runs the next `rounds` rounds;
+ * bm_fit_finish does s_opt, the common recheck and the full assignment.
+ * The context owns its workspace until bm_fit_destroy.
+ * ------------------------------------------------------------------------- */
+typedef struct bm_fit_ctx bm_fit_ctx;
+bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k,
+                        const bm_sample_policy* policy, const bm_budget* budget,
+                        uint64_t seed, void* stream, bm_fit_ctx** out);
+bm_status bm_fit_rounds(bm_fit_ctx* ctx, int32_t rounds);
+bm_status bm_fit_finish(bm_fit_ctx* ctx, float* C_out_dev, int32_t* labels_out_dev,
+                        bm_report* report_out);
+void bm_fit_destroy(bm_fit_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Step entry points (each one is a single step of the hot path; the fit runs
+ * the same device code fused into one kernel per round).
+ * ------------------------------------------------------------------------- */
+
+/* a1 -- uniform sample without replacement (Sec. 4.1 "uniformly random
+ * sample"): the first s distinct bounded draws r_0, r_1, ... in [0, m) of
+ * stream (purpose, worker, round, pass), in order of first occurrence.
+ * idx_out_dev: s int64 device.  Requires 0 <= s <= m. */
+bm_status bm_sample(uint64_t seed, int32_t purpose, int32_t worker, int32_t round,
+                    int32_t pass, int64_t m, int64_t s, int64_t* idx_out_dev,
+                    void* stream);
+
+/* a2 -- gather S[i, :] = X[idx[i], :] (Alg. 1, S_w).  S_out_dev: s x n. */
+bm_status bm_gather(const float* X_dev, int64_t m, int32_t n, const int64_t* idx_dev,
+                    int64_t s, float* S_out_dev, void* stream);
+
+/* a3 -- greedy K-means++ re-seeding of the degenerate centroids (Sec. 4.1,
+ * Sec. 5: `trials` candidates) on sample S (s x n), in increasing index
+ * order; other centroids count as chosen.  The draws use stream
+ * (BM_RNG_KPP, worker, round, pass).  C_inout_dev: k x n device;
+ * degenerate_dev: k bytes device (nonzero = degenerate). */
+bm_status bm_kmeanspp(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev,
+                      int32_t k, const uint8_t* degenerate_dev, int32_t trials,
+                      uint64_t seed, int32_t worker, int32_t round, int32_t pass,
+                      void* stream);
+
+/* a4-a6 -- Lloyd K-means on S from C (Sec. 4.1; Sec. 5 stop rule): at most
+ * max_iter centroid updates, stopping when f_prev - f_new <= tol * f_prev.
+ * On return C_inout_dev holds the result, *f_out_host = f(C, S), *iters_out_host
+ * the number of updates, empty_out_dev (k bytes, may be NULL) marks clusters
+ * with no member in the final assignment. */
+bm_status bm_lloyd(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev,
+                   int32_t k, int32_t max_iter, double tol, double* f_out_host,
+                   int32_t* iters_out_host, uint8_t* empty_out_dev, void* stream);
+
+/* a9 -- full-data pass (Alg. 1 last step; Eq. 1): labels of every row of X
+ * and f(C, X).  labels_out_dev may be NULL.  *f_out_host receives f. */
+bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev,
+                    int32_t k, int32_t* labels_out_dev, double* f_out_host,
+                    bm_report* report_out, void* stream);
+
+/* Thread-local message for the last non-OK status of this thread. */
+const char* bm_last_error(void);
+
+/* Library version string. */
+const char* bm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIGMEANS_H */

@@ -1,0 +1,632 @@
+// C ABI of libbigmeans (include/bigmeans.h): argument checks, workspace
+// layout, and the launch sequence of Algorithm 1 (arXiv 2403.18766):
+//
+//   prepass(X)                  validate, largest |x| -> fixed-point grids
+//   worker kernel (rounds)      one cluster per worker: Alg. 1 rounds
+//   [full pass, incumbent]      optional, after every round
+//   worker kernel (final eval)  common sample of size s_opt, f_hat_w for all w
+//   full pass                   labels and f(C_best, X)
+//
+// Everything is enqueued on the caller's stream; each entry point
+// synchronises that stream once before returning.
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bigmeans.h"
+#include "bm_device.cuh"
+#include "bm_worker.cuh"
+
+namespace bm {
+size_t worker_smem(int np, int k);
+cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
+size_t fullpass_smem_bytes(int np, int k);
+cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
+                            const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
+                            int incumbent, int grid, cudaStream_t st);
+cudaError_t launch_prepass(const float* v, long long count, Globals* g, int grid, cudaStream_t st);
+cudaError_t launch_pad(const float* src, long long rows, int n, int np, float* dst, cudaStream_t st);
+cudaError_t launch_unpad(const float* src, long long rows, int n, int np, float* dst, cudaStream_t st);
+cudaError_t launch_select_unpad(const float* Cw, const double* sel_f, int W, int k, int n, int np,
+                                float* dst, cudaStream_t st);
+cudaError_t launch_init_state(double* fhat, int W, unsigned char* deg, long long kdeg, Globals* g,
+                              cudaStream_t st);
+cudaError_t launch_globaltimer(unsigned long long* out, cudaStream_t st);
+}  // namespace bm
+
+using namespace bm;
+
+namespace {
+
+thread_local std::string g_err;
+
+bm_status fail(bm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CU(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? BM_ENOMEM : BM_ECUDA,           \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                  \
+    } while (0)
+
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kRowsPerCta = 4096;
+
+int padded_dim(int n) {
+    if (n <= 4) return 4;
+    if (n <= 8) return 8;
+    if (n <= 16) return 16;
+    if (n <= 32) return 32;
+    return 64;
+}
+
+int sm_count() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+// gamma_q = q u / (1 - q u), u = 2^-24, rounded up to float.
+float gamma_up(int q) {
+    const double u = std::ldexp(1.0, -24);
+    const double gq = q * u / (1.0 - q * u);
+    return std::nextafter((float)gq, INFINITY);
+}
+void cert_constants(int np, float& gB, float& gp2) {
+    gB = std::nextafter(gamma_up(2 * np + 2) * (1.0f + 1e-6f), INFINITY);
+    const double g2 = 2.0 * (1.0 + std::ldexp(1.0, -14)) * (double)gamma_up(np + 2);
+    gp2 = std::nextafter((float)g2 * (1.0f + 1e-6f), INFINITY);
+}
+
+// Expected and safe number of bounded draws to collect s distinct values of m.
+long long draw_cap(long long m, long long s) {
+    double mean = 0.0, var = 0.0;
+    if (s <= m / 2) {
+        // each draw is new with probability >= 1/2: mean <= 2 s, tiny variance
+        for (long long i = 0; i < s; i += 1 + s / 4096) {
+            const double p = (double)(m - i) / (double)m;
+            const long long cnt = std::min<long long>(1 + s / 4096, s - i);
+            mean += cnt / p;
+            var += cnt * (1.0 - p) / (p * p);
+        }
+    } else {
+        for (long long i = 0; i < s; ++i) {
+            const double p = (double)(m - i) / (double)m;
+            mean += 1.0 / p;
+            var += (1.0 - p) / (p * p);
+        }
+    }
+    const double cap = mean + 8.0 * std::sqrt(var) + 1024.0 + 0.05 * mean;
+    return (long long)std::ceil(cap);
+}
+
+long long next_pow2(long long v) {
+    long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+}  // namespace
+
+struct bm_fit_ctx {
+    cudaStream_t st = nullptr;
+    const float* X = nullptr;
+    long long m = 0;
+    int n = 0, k = 0, np = 0, cs = 1;
+    bm_sample_policy pol{};
+    bm_budget bud{};
+    unsigned long long seed = 0;
+    long long s_lo = 0, s_hi = 0, s_cap = 0, Tcap = 0, H = 0, L_cap = 0;
+    size_t smem = 0;
+    float gB = 0, gp2 = 0;
+    int rounds_run = 0;
+    unsigned long long t0_gpu = 0;
+    std::chrono::steady_clock::time_point t0;
+    // device buffers
+    void* base = nullptr;
+    Globals* glob = nullptr;
+    float* S = nullptr; long long* idx = nullptr; unsigned int* draws = nullptr;
+    unsigned int* hkey = nullptr; unsigned int* htmin = nullptr; float* D2 = nullptr;
+    float* Cw = nullptr; float* Cw_cta = nullptr; unsigned char* deg = nullptr;
+    double* fhat = nullptr; double* f_final = nullptr; long long* L_buf = nullptr;
+    unsigned long long* timer = nullptr;
+};
+
+namespace {
+
+WorkerArgs make_args(const bm_fit_ctx* c, int mode) {
+    WorkerArgs a;
+    memset(&a, 0, sizeof a);
+    a.X = c->X; a.m = c->m; a.n = c->n; a.k = c->k;
+    a.s_min = c->pol.s_min; a.s_max = c->s_hi;
+    for (int i = 0; i < 16; ++i) a.set[i] = c->pol.set[i];
+    a.set_len = c->pol.set_len;
+    a.W = c->pol.workers; a.P = c->pol.passes;
+    a.max_lloyd = c->bud.max_lloyd; a.trials = c->bud.kpp_candidates; a.tol = c->bud.tol;
+    a.seed = c->seed;
+    a.mode = mode; a.cs = c->cs; a.glob = c->glob;
+    a.S = c->S; a.S_stride = c->s_cap * c->np;
+    a.idx = c->idx; a.idx_stride = c->s_cap;
+    a.draws = c->draws; a.draws_stride = c->Tcap; a.Tcap = c->Tcap;
+    a.hkey = c->hkey; a.htmin = c->htmin; a.H = c->H; a.hash_stride = c->H;
+    a.D2 = c->D2; a.D2_stride = c->s_cap;
+    a.Cw = c->Cw; a.Cw_cta = c->Cw_cta; a.deg = c->deg; a.fhat = c->fhat;
+    a.L_buf = c->L_buf; a.L_cap = c->L_cap; a.f_final = c->f_final;
+    a.gB = c->gB; a.gp2 = c->gp2;
+    return a;
+}
+
+// Carve one device allocation into the workspace of `W` workers.
+bm_status alloc_workspace(bm_fit_ctx* c, int W) {
+    const long long k = c->k, np = c->np;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_glob = take(sizeof(Globals));
+    const size_t o_S = take((size_t)W * c->s_cap * np * 4);
+    const size_t o_idx = take((size_t)W * c->s_cap * 8);
+    const size_t o_draws = take((size_t)W * c->Tcap * 4);
+    const size_t o_hkey = take((size_t)W * c->H * 4);
+    const size_t o_htmin = take((size_t)W * c->H * 4);
+    const size_t o_D2 = take((size_t)W * c->s_cap * 4);
+    const size_t o_Cw = take((size_t)W * k * np * 4);
+    const size_t o_Cwc = take((size_t)W * c->cs * k * np * 4);
+    const size_t o_deg = take((size_t)W * k);
+    const size_t o_fhat = take((size_t)W * 8);
+    const size_t o_ff = take((size_t)W * 8);
+    const size_t o_L = take((size_t)c->L_cap * 8);
+    const size_t o_t = take(8);
+    cudaError_t e = cudaMallocAsync(&c->base, off, c->st);
+    if (e != cudaSuccess) {
+        c->base = nullptr;
+        return fail(BM_ENOMEM, "workspace of %zu bytes: %s", off, cudaGetErrorString(e));
+    }
+    char* b = (char*)c->base;
+    c->glob = (Globals*)(b + o_glob);
+    c->S = (float*)(b + o_S); c->idx = (long long*)(b + o_idx); c->draws = (unsigned int*)(b + o_draws);
+    c->hkey = (unsigned int*)(b + o_hkey); c->htmin = (unsigned int*)(b + o_htmin);
+    c->D2 = (float*)(b + o_D2); c->Cw = (float*)(b + o_Cw); c->Cw_cta = (float*)(b + o_Cwc);
+    c->deg = (unsigned char*)(b + o_deg); c->fhat = (double*)(b + o_fhat); c->f_final = (double*)(b + o_ff);
+    c->L_buf = (long long*)(b + o_L); c->timer = (unsigned long long*)(b + o_t);
+    CU(cudaMemsetAsync(c->glob, 0, sizeof(Globals), c->st));
+    CU(cudaMemsetAsync(c->Cw, 0, (size_t)W * k * np * 4, c->st));
+    CU(cudaMemsetAsync(c->S, 0, (size_t)W * c->s_cap * np * 4, c->st));
+    return BM_OK;
+}
+
+bm_status check_ptr(const void* p, const char* what) {
+    if (!p) return fail(BM_EINVAL, "%s is NULL", what);
+    if (((uintptr_t)p) & 15) return fail(BM_EINVAL, "%s is not 16-byte aligned", what);
+    return BM_OK;
+}
+
+// Size checks shared by the fit and the step entry points.
+bm_status check_shape(long long m, int n, int k) {
+    if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range [1, 2^31)", m);
+    if (n < 1 || n > 64) return fail(BM_EINVAL, "n = %d out of range [1, 64]", n);
+    if (k < 1) return fail(BM_EINVAL, "k = %d must be >= 1", k);
+    const size_t smem = worker_smem(padded_dim(n), k);
+    if (smem > kSmemLimit)
+        return fail(BM_EINVAL, "k = %d with n = %d needs %zu bytes of shared memory (limit %zu)", k, n,
+                    smem, kSmemLimit);
+    return BM_OK;
+}
+
+bm_status read_globals(bm_fit_ctx* c, Globals* h) {
+    CU(cudaMemcpyAsync(h, c->glob, sizeof(Globals), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return BM_OK;
+}
+
+bm_status status_from_flags(const Globals& h) {
+    if (h.nonfinite) return fail(BM_EINVAL, "X contains %u non-finite values", h.nonfinite);
+    if (h.maxbits >= 0x7e800000u)
+        return fail(BM_EINVAL, "max |x| must be below 2^126");
+    if (h.err & kErrSample) return fail(BM_EINTERNAL, "sampler needed more draws than its cap");
+    if (h.err & kErrDigits) return fail(BM_EINTERNAL, "fixed-point accumulator range exceeded");
+    if (h.err & kErrTimeout) return fail(BM_ETIMEOUT, "a bounded device wait gave up");
+    if (h.err & kErrArgs) return fail(BM_EINVAL, "an index was outside [0, m) or a device consistency check failed");
+    if (h.err) return fail(BM_EINTERNAL, "device error flags 0x%x", h.err);
+    return BM_OK;
+}
+
+bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
+    WorkerArgs a = make_args(c, kModeRounds);
+    a.round_begin = r0;
+    a.round_end = r1;
+    a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
+    const int big = 0x7fffffff;
+    CU(cudaMemcpyAsync(&c->glob->rounds_done, &big, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    CU(launch_worker(c->np, a, c->pol.workers, c->st));
+    return BM_OK;
+}
+
+bm_status run_fullpass(bm_fit_ctx* c, const double* sel, int* labels, int incumbent) {
+    const int grid = sm_count();
+    CU(launch_fullpass(c->np, c->X, c->m, c->n, c->Cw, c->k, sel, c->pol.workers, labels, c->glob, c->gB,
+                       c->gp2, incumbent, grid, c->st));
+    return BM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bm_last_error(void) { return g_err.c_str(); }
+const char* bm_version(void) { return "bigmeans-gb300 0.1 (sm_103a)"; }
+
+bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                        const bm_budget* budget, uint64_t seed, void* stream, bm_fit_ctx** out) {
+    if (!out) return fail(BM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!policy || !budget) return fail(BM_EINVAL, "policy and budget are required");
+    bm_status s = check_ptr(X_dev, "X_dev");
+    if (s) return s;
+    if ((s = check_shape(m, n, k))) return s;
+    bm_sample_policy pol = *policy;
+    bm_budget bud = *budget;
+    if (pol.workers < 1 || pol.workers > 4096) return fail(BM_EINVAL, "workers = %d out of range", pol.workers);
+    if (pol.passes < 1) return fail(BM_EINVAL, "passes = %d must be >= 1", pol.passes);
+    if (pol.set_len < 0 || pol.set_len > 16) return fail(BM_EINVAL, "set_len = %d out of range", pol.set_len);
+    long long s_lo, s_hi;
+    if (pol.set_len > 0) {
+        s_lo = s_hi = std::min<long long>(pol.set[0], m);
+        for (int i = 0; i < pol.set_len; ++i) {
+            pol.set[i] = std::min<long long>(pol.set[i], m);
+            s_lo = std::min<long long>(s_lo, pol.set[i]);
+            s_hi = std::max<long long>(s_hi, pol.set[i]);
+        }
+    } else {
+        pol.s_max = std::min<long long>(pol.s_max, m);
+        s_lo = pol.s_min;
+        s_hi = pol.s_max;
+        if (s_lo > s_hi) return fail(BM_EINVAL, "s_min = %lld > s_max = %lld", s_lo, s_hi);
+    }
+    if (s_lo < k) return fail(BM_EINVAL, "smallest sample size %lld is below k = %d", s_lo, k);
+    if (bud.rounds < 0 || (bud.rounds == 0 && !(bud.seconds > 0)))
+        return fail(BM_EINVAL, "need rounds > 0 or seconds > 0");
+    if (bud.max_lloyd < 0) return fail(BM_EINVAL, "max_lloyd < 0");
+    if (bud.kpp_candidates < 1 || bud.kpp_candidates > 3)
+        return fail(BM_EINVAL, "kpp_candidates = %d out of range [1, 3]", bud.kpp_candidates);
+    if (!(bud.tol >= 0) && bud.tol != -1.0 && !(bud.tol < 0))
+        return fail(BM_EINVAL, "tol is NaN");
+
+    bm_fit_ctx* c = new bm_fit_ctx();
+    c->t0 = std::chrono::steady_clock::now();
+    c->st = (cudaStream_t)stream;
+    c->X = X_dev; c->m = m; c->n = n; c->k = k; c->np = padded_dim(n);
+    c->pol = pol; c->bud = bud; c->seed = seed;
+    c->s_lo = s_lo; c->s_hi = s_hi; c->s_cap = s_hi;
+    c->cs = (int)std::min<long long>(8, std::max<long long>(1, (s_hi + kRowsPerCta - 1) / kRowsPerCta));
+    c->Tcap = draw_cap(m, s_hi);
+    if (c->Tcap >= (1ll << 32) - 1) { delete c; return fail(BM_EINVAL, "sample size too close to m"); }
+    c->H = next_pow2(2 * c->Tcap);
+    if (c->H > (1ll << 31)) { delete c; return fail(BM_EINVAL, "sample sizes need a sampler table above 2^31"); }
+    c->L_cap = (bud.rounds > 0 ? (long long)bud.rounds : 4096ll) * pol.workers * pol.passes;
+    c->L_cap = std::min<long long>(c->L_cap, 1ll << 24);
+    c->smem = worker_smem(c->np, k);
+    cert_constants(c->np, c->gB, c->gp2);
+    if ((s = alloc_workspace(c, pol.workers))) { delete c; return s; }
+    cudaError_t e;
+    if ((e = launch_init_state(c->fhat, pol.workers, c->deg, (long long)pol.workers * k, c->glob, c->st)) ||
+        (e = launch_prepass(X_dev, m * n, c->glob, 2 * sm_count(), c->st)) ||
+        (e = launch_globaltimer(c->timer, c->st))) {
+        bm_fit_destroy(c);
+        return fail(BM_ECUDA, "launch failed: %s", cudaGetErrorString(e));
+    }
+    Globals h;
+    if ((s = read_globals(c, &h))) { bm_fit_destroy(c); return s; }
+    if ((s = status_from_flags(h))) { bm_fit_destroy(c); return s; }
+    if ((e = cudaMemcpy(&c->t0_gpu, c->timer, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        bm_fit_destroy(c);
+        return fail(BM_ECUDA, "%s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return BM_OK;
+}
+
+bm_status bm_fit_rounds(bm_fit_ctx* c, int32_t rounds) {
+    if (!c) return fail(BM_EINVAL, "ctx is NULL");
+    if (rounds < 0) return fail(BM_EINVAL, "rounds < 0");
+    if (rounds == 0) return BM_OK;
+    bm_status s;
+    const bool per_round = c->bud.eval_full_each_round || c->bud.seconds > 0;
+    if (!per_round) {
+        if ((s = run_round_launch(c, c->rounds_run, c->rounds_run + rounds))) return s;
+        c->rounds_run += rounds;
+    } else {
+        for (int r = 0; r < rounds; ++r) {
+            if (c->bud.seconds > 0) {
+                const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
+                if (el >= c->bud.seconds) break;
+            }
+            if ((s = run_round_launch(c, c->rounds_run, c->rounds_run + 1))) return s;
+            c->rounds_run += 1;
+            if (c->bud.eval_full_each_round)
+                if ((s = run_fullpass(c, c->fhat, nullptr, 1))) return s;
+            if (c->bud.seconds > 0) CU(cudaStreamSynchronize(c->st));
+        }
+    }
+    Globals h;
+    if ((s = read_globals(c, &h))) return s;
+    return status_from_flags(h);
+}
+
+bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep) {
+    if (!c) return fail(BM_EINVAL, "ctx is NULL");
+    bm_status s = check_ptr(C_out_dev, "C_out_dev");
+    if (s) return s;
+    WorkerArgs a = make_args(c, kModeFinalEval);
+    CU(launch_worker(c->np, a, c->pol.workers, c->st));
+    if ((s = run_fullpass(c, c->f_final, labels_out_dev, 1))) return s;
+    CU(launch_select_unpad(c->Cw, c->f_final, c->pol.workers, c->k, c->n, c->np, C_out_dev, c->st));
+    Globals h;
+    if ((s = read_globals(c, &h))) return s;
+    if ((s = status_from_flags(h))) return s;
+    if (rep) {
+        memset(rep, 0, sizeof *rep);
+        rep->f_full = h.f_full;
+        rep->f_incumbent = std::min(h.f_incumbent, h.f_full);
+        rep->s_opt = h.s_opt;
+        rep->best_worker = h.best_worker;
+        rep->rounds_done = c->rounds_run;
+        rep->passes_done = (int64_t)h.passes;
+        rep->lloyd_iters = (int64_t)h.lloyd_iters;
+        rep->assign_rows = (int64_t)h.assign_rows;
+        rep->accepts = (int64_t)h.accepts;
+        rep->L_sum = (int64_t)h.L_sum;
+        rep->rescored_rows = (int64_t)h.rescored;
+        rep->inexact_terms = (int64_t)h.inexact;
+        rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
+    }
+    return BM_OK;
+}
+
+void bm_fit_destroy(bm_fit_ctx* c) {
+    if (!c) return;
+    if (c->base) {
+        cudaFreeAsync(c->base, c->st);
+        cudaStreamSynchronize(c->st);
+    }
+    delete c;
+}
+
+bm_status bigmeans_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                       const bm_budget* budget, uint64_t seed, void* stream, float* C_out_dev,
+                       int32_t* labels_out_dev, bm_report* report_out) {
+    bm_fit_ctx* c = nullptr;
+    bm_status s = bm_fit_create(X_dev, m, n, k, policy, budget, seed, stream, &c);
+    if (s) return s;
+    const int T = budget->rounds > 0 ? budget->rounds : 0x3fffffff;
+    if ((s = bm_fit_rounds(c, T))) { bm_fit_destroy(c); return s; }
+    s = bm_fit_finish(c, C_out_dev, labels_out_dev, report_out);
+    bm_fit_destroy(c);
+    return s;
+}
+
+bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k,
+                            const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
+                            void* stream, float* C_out_host, int32_t* labels_out_host, bm_report* rep) {
+    if (!X_host || !C_out_host) return fail(BM_EINVAL, "X_host and C_out_host are required");
+    bm_status s = check_shape(m, n, k);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    float* Xd = nullptr; float* Cd = nullptr; int32_t* Ld = nullptr;
+    const size_t xb = (size_t)m * n * 4;
+    CU(cudaMallocAsync((void**)&Xd, xb, st));
+    if (cudaMallocAsync((void**)&Cd, (size_t)k * n * 4 + 16, st) != cudaSuccess ||
+        (labels_out_host && cudaMallocAsync((void**)&Ld, (size_t)m * 4, st) != cudaSuccess)) {
+        cudaFreeAsync(Xd, st);
+        if (Cd) cudaFreeAsync(Cd, st);
+        cudaStreamSynchronize(st);
+        return fail(BM_ENOMEM, "device buffers for the host-buffer fit");
+    }
+    cudaError_t e = cudaMemcpyAsync(Xd, X_host, xb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        s = bigmeans_fit(Xd, m, n, k, policy, budget, seed, stream, Cd, Ld, rep);
+        if (s == BM_OK) {
+            e = cudaMemcpyAsync(C_out_host, Cd, (size_t)k * n * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess && labels_out_host)
+                e = cudaMemcpyAsync(labels_out_host, Ld, (size_t)m * 4, cudaMemcpyDeviceToHost, st);
+        }
+    }
+    cudaFreeAsync(Xd, st);
+    cudaFreeAsync(Cd, st);
+    if (Ld) cudaFreeAsync(Ld, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s) return s;
+    if (e != cudaSuccess) return fail(BM_ECUDA, "copy: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(BM_ECUDA, "sync: %s", cudaGetErrorString(e2));
+    if (rep) rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return BM_OK;
+}
+
+// ------------------------------------------------------------- step calls
+// A one-worker context with explicit sizes, used by the step entry points.
+static bm_status step_ctx(bm_fit_ctx* c, const float* X, long long m, int n, int k, long long s_cap,
+                          unsigned long long seed, void* stream) {
+    c->st = (cudaStream_t)stream;
+    c->X = X; c->m = m; c->n = n; c->k = k; c->np = padded_dim(n);
+    c->pol = bm_sample_policy{};
+    c->pol.workers = 1; c->pol.passes = 1; c->pol.s_min = s_cap; c->pol.s_max = s_cap;
+    c->bud = bm_budget{};
+    c->bud.rounds = 1; c->bud.max_lloyd = 300; c->bud.tol = 1e-4; c->bud.kpp_candidates = 3;
+    c->seed = seed;
+    c->s_lo = c->s_hi = c->s_cap = std::max<long long>(s_cap, 1);
+    c->cs = (int)std::min<long long>(8, std::max<long long>(1, (c->s_cap + kRowsPerCta - 1) / kRowsPerCta));
+    c->Tcap = m > 0 ? draw_cap(m, std::min<long long>(c->s_cap, m)) : 1024;
+    c->H = next_pow2(2 * c->Tcap);
+    c->L_cap = 1;
+    c->smem = worker_smem(c->np, k);
+    cert_constants(c->np, c->gB, c->gp2);
+    return alloc_workspace(c, 1);
+}
+
+struct CtxGuard {
+    bm_fit_ctx* c;
+    ~CtxGuard() { bm_fit_destroy(c); }
+};
+
+bm_status bm_sample(uint64_t seed, int32_t purpose, int32_t worker, int32_t round, int32_t pass, int64_t m,
+                    int64_t s, int64_t* idx_out_dev, void* stream) {
+    if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range", (long long)m);
+    if (s < 0 || s > m) return fail(BM_EINVAL, "s = %lld out of range [0, m]", (long long)s);
+    if (s > 0 && !idx_out_dev) return fail(BM_EINVAL, "idx_out_dev is NULL");
+    if (worker < 0 || worker >= (1 << 16) || round < 0 || round >= (1 << 24) || pass < 0 || pass >= (1 << 16))
+        return fail(BM_EINVAL, "stream coordinates out of range");
+    bm_fit_ctx* c = new bm_fit_ctx();
+    CtxGuard guard{c};
+    bm_status st = step_ctx(c, nullptr, m, 1, 1, s, seed, stream);
+    if (st) return st;
+    WorkerArgs a = make_args(c, kModeStepSample);
+    a.idx = reinterpret_cast<long long*>(idx_out_dev); a.idx_stride = 0;
+    a.step_s = s; a.step_purpose = purpose; a.step_worker = worker; a.step_round = round; a.step_pass = pass;
+    CU(launch_worker(c->np, a, 1, c->st));
+    Globals h;
+    if ((st = read_globals(c, &h))) return st;
+    return status_from_flags(h);
+}
+
+bm_status bm_gather(const float* X_dev, int64_t m, int32_t n, const int64_t* idx_dev, int64_t s,
+                    float* S_out_dev, void* stream) {
+    bm_status st = check_shape(m, n, 1);
+    if (st) return st;
+    if (s < 0) return fail(BM_EINVAL, "s < 0");
+    if (s == 0) return BM_OK;
+    if (!X_dev || !idx_dev || !S_out_dev) return fail(BM_EINVAL, "NULL pointer");
+    bm_fit_ctx* c = new bm_fit_ctx();
+    CtxGuard guard{c};
+    if ((st = step_ctx(c, X_dev, m, n, 1, s, 0, stream))) return st;
+    WorkerArgs a = make_args(c, kModeStepGather);
+    a.idx = const_cast<long long*>(reinterpret_cast<const long long*>(idx_dev));
+    a.idx_stride = 0;
+    a.step_s = s;
+    CU(launch_worker(c->np, a, 1, c->st));
+    CU(launch_unpad(c->S, s, n, c->np, S_out_dev, c->st));
+    Globals h;
+    if ((st = read_globals(c, &h))) return st;
+    return status_from_flags(h);
+}
+
+static bm_status stage_sample_and_centroids(bm_fit_ctx* c, const float* S_dev, long long s, const float* C_dev,
+                                            int k) {
+    CU(launch_pad(S_dev, s, c->n, c->np, c->S, c->st));
+    CU(launch_pad(C_dev, k, c->n, c->np, c->Cw, c->st));
+    CU(launch_prepass(S_dev, s * c->n, c->glob, 2 * sm_count(), c->st));
+    CU(launch_prepass(C_dev, (long long)k * c->n, c->glob, 1, c->st));
+    return BM_OK;
+}
+
+bm_status bm_kmeanspp(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev, int32_t k,
+                      const uint8_t* degenerate_dev, int32_t trials, uint64_t seed, int32_t worker,
+                      int32_t round, int32_t pass, void* stream) {
+    bm_status st = check_shape(s, n, k);
+    if (st) return st;
+    if (!S_dev || !C_inout_dev || !degenerate_dev) return fail(BM_EINVAL, "NULL pointer");
+    if (trials < 1 || trials > 3) return fail(BM_EINVAL, "trials = %d out of range [1, 3]", trials);
+    bm_fit_ctx* c = new bm_fit_ctx();
+    CtxGuard guard{c};
+    if ((st = step_ctx(c, S_dev, s, n, k, s, seed, stream))) return st;
+    if ((st = stage_sample_and_centroids(c, S_dev, s, C_inout_dev, k))) return st;
+    CU(cudaMemcpyAsync(c->deg, degenerate_dev, k, cudaMemcpyDeviceToDevice, c->st));
+    WorkerArgs a = make_args(c, kModeStepKpp);
+    a.trials = trials; a.step_s = s; a.step_worker = worker; a.step_round = round; a.step_pass = pass;
+    CU(launch_worker(c->np, a, 1, c->st));
+    CU(launch_unpad(c->Cw, k, n, c->np, C_inout_dev, c->st));
+    Globals h;
+    if ((st = read_globals(c, &h))) return st;
+    return status_from_flags(h);
+}
+
+bm_status bm_lloyd(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev, int32_t k, int32_t max_iter,
+                   double tol, double* f_out_host, int32_t* iters_out_host, uint8_t* empty_out_dev,
+                   void* stream) {
+    bm_status st = check_shape(s, n, k);
+    if (st) return st;
+    if (!S_dev || !C_inout_dev) return fail(BM_EINVAL, "NULL pointer");
+    if (max_iter < 0) return fail(BM_EINVAL, "max_iter < 0");
+    bm_fit_ctx* c = new bm_fit_ctx();
+    CtxGuard guard{c};
+    if ((st = step_ctx(c, S_dev, s, n, k, s, 0, stream))) return st;
+    if ((st = stage_sample_and_centroids(c, S_dev, s, C_inout_dev, k))) return st;
+    CU(cudaMemsetAsync(c->deg, 0, k, c->st));
+    WorkerArgs a = make_args(c, kModeStepLloyd);
+    a.max_lloyd = max_iter; a.tol = tol; a.step_s = s;
+    a.step_f = c->f_final; a.step_iters = (int*)c->L_buf;
+    a.step_empty = empty_out_dev ? empty_out_dev : c->deg;
+    CU(launch_worker(c->np, a, 1, c->st));
+    CU(launch_unpad(c->Cw, k, n, c->np, C_inout_dev, c->st));
+    double f = 0;
+    int it = 0;
+    CU(cudaMemcpyAsync(&f, c->f_final, 8, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(&it, c->L_buf, 4, cudaMemcpyDeviceToHost, c->st));
+    Globals h;
+    if ((st = read_globals(c, &h))) return st;
+    if ((st = status_from_flags(h))) return st;
+    if (f_out_host) *f_out_host = f;
+    if (iters_out_host) *iters_out_host = it;
+    return BM_OK;
+}
+
+bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev, int32_t k,
+                    int32_t* labels_out_dev, double* f_out_host, bm_report* rep, void* stream) {
+    bm_status st = check_shape(m, n, k);
+    if (st) return st;
+    if ((st = check_ptr(X_dev, "X_dev"))) return st;
+    if (!C_dev) return fail(BM_EINVAL, "C_dev is NULL");
+    cudaStream_t sm = (cudaStream_t)stream;
+    const int np = padded_dim(n);
+    const size_t smem = fullpass_smem_bytes(np, k);
+    if (smem > kSmemLimit) return fail(BM_EINVAL, "k too large for the full pass");
+    void* base = nullptr;
+    const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
+    CU(cudaMallocAsync(&base, gb + (size_t)k * np * 4, sm));
+    Globals* g = (Globals*)base;
+    float* Cp = (float*)((char*)base + gb);
+    float gB, gp2;
+    cert_constants(np, gB, gp2);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
+        (e = launch_pad(C_dev, k, n, np, Cp, sm)) ||
+        (e = launch_prepass(X_dev, m * n, g, 2 * sm_count(), sm)) ||
+        (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
+        (e = launch_fullpass(np, X_dev, m, n, Cp, k, nullptr, 1, labels_out_dev, g, gB, gp2, 0, sm_count(), sm))) {
+        cudaFreeAsync(base, sm);
+        cudaStreamSynchronize(sm);
+        return fail(BM_ECUDA, "full pass launch: %s", cudaGetErrorString(e));
+    }
+    Globals h;
+    e = cudaMemcpyAsync(&h, g, sizeof(Globals), cudaMemcpyDeviceToHost, sm);
+    cudaFreeAsync(base, sm);
+    const cudaError_t e2 = cudaStreamSynchronize(sm);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(BM_ECUDA, "full pass: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if ((st = status_from_flags(h))) return st;
+    if (f_out_host) *f_out_host = h.f_full;
+    if (rep) {
+        memset(rep, 0, sizeof *rep);
+        rep->f_full = h.f_full;
+        rep->f_incumbent = h.f_full;
+        rep->rescored_rows = (int64_t)h.rescored;
+        rep->inexact_terms = (int64_t)h.inexact;
+    }
+    return BM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Launch arguments of the fused worker kernel (host and device view).
+#pragma once
+#include <cstdint>
+
+#include "bm_device.cuh"
+
+namespace bm {
+
+enum WorkerMode : int {
+    kModeRounds = 0,      // Algorithm 1 rounds [round_begin, round_end)
+    kModeFinalEval = 1,   // common recheck on the FINAL sample of size s_opt
+    kModeStepSample = 2,  // a1 only
+    kModeStepGather = 3,  // a1 indices given -> a2
+    kModeStepKpp = 4,     // a3 on a given sample
+    kModeStepLloyd = 5,   // a4-a6 on a given sample
+};
+
+struct WorkerArgs {
+    // data
+    const float* X;
+    long long m;
+    int n, k;
+    // policy / budget
+    long long s_min, s_max;        // s_max already clipped to m
+    long long set[16];
+    int set_len;
+    int W, P;
+    int max_lloyd, trials;
+    double tol;
+    unsigned long long seed;
+    int round_begin, round_end;
+    unsigned long long deadline_ns;   // %globaltimer deadline, 0 = none
+    int mode;
+    int cs;                           // CTAs per cluster
+    Globals* glob;
+    // per-worker workspace
+    float* S; long long S_stride;                 // s_cap * NP floats
+    long long* idx; long long idx_stride;         // s_cap
+    unsigned int* draws; long long draws_stride;  // Tcap
+    long long Tcap;
+    unsigned int* hkey; unsigned int* htmin; long long H; long long hash_stride;
+    float* D2; long long D2_stride;               // s_cap
+    // worker state
+    float* Cw;               // W * k * NP (canonical, read at launch start)
+    float* Cw_cta;           // W * cs * k * NP (per-CTA working copies)
+    unsigned char* deg;      // W * k
+    double* fhat;            // W
+    long long* L_buf; long long L_cap;
+    double* f_final;         // W (common recheck)
+    // step-mode I/O (worker 0 only)
+    long long step_s;
+    int step_purpose, step_worker, step_round, step_pass;
+    double* step_f; int* step_iters; unsigned char* step_empty;
+    // certificate constants (rounded up)
+    float gB, gp2;
+};
+
+struct Xch {
+    unsigned long long f_lo, f_hi;     // CTA partial of the exact objective
+    unsigned long long inexact, rescored;
+    long long wsum;                    // CTA sum of K-means++ weights
+    long long pot[4];                  // CTA partial candidate potentials
+    long long nkeep;                   // CTA count of first-occurrence draws
+    unsigned int maxbits;              // CTA max of D^2 bits
+    int cand[4];                       // candidate row found by this CTA, -1 if none
+    int stop;                          // rank-0 decision broadcast
+    int flag;                          // rank-0 flag broadcast
+    double fval;                       // rank-0 objective broadcast
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+template <int NP>
+__host__ __device__ inline size_t worker_smem_bytes(int k) {
+    size_t b = 0;
+    b += align16((size_t)k * NP * 4);           // Ccur
+    b += align16((size_t)k * NP * 4);           // Cnew
+    b += align16((size_t)k * 4);                // CC
+    b += align16((size_t)k * NP * 3 * 8);       // ACC
+    b += align16((size_t)k * 4);                // cnt
+    b += align16((size_t)k) * 3;                // deg, empty, emptyall
+    b += align16(sizeof(Xch));
+    b += align16(sizeof(unsigned __int128) * kWarps);
+    b += align16(8 * (kWarps + 1));
+    b += align16(4 * kWarps);
+    b += align16(sizeof(CertC));
+    b += align16(8 * 16);
+    return b;
+}
+
+cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
+size_t worker_smem(int np, int k);
+
+}  // namespace bm

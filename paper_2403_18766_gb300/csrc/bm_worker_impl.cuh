@@ -1,0 +1,822 @@
+#pragma once
+// Fused Big-means worker kernel (template body; instantiated per padded
+// width NP in bm_worker_np*.cu): one thread-block cluster per competing
+// worker of Algorithm 1 (arXiv 2403.18766, Sec. 4.2-4.3).
+//
+// A worker's sample is split into contiguous row slices, one per CTA of its
+// cluster.  Per pass the cluster draws the sample (a1), gathers it (a2),
+// re-seeds degenerate centroids with greedy K-means++ (a3), runs Lloyd's
+// iterations (a4-a6) and applies the incumbent rule.  Cross-CTA exchange goes
+// through distributed shared memory; every cross-CTA dependency is separated
+// by a hardware cluster barrier (barrier.cluster, no spinning in this code).
+// All control flow that reaches a cluster barrier is cluster-uniform: it only
+// depends on kernel arguments and on values every CTA reads after a barrier
+// from the same place, so all CTAs execute the same sequence of barriers.
+#include <cstdint>
+
+#include "bm_device.cuh"
+#include "bm_worker.cuh"
+
+namespace bm {
+
+template <int NP>
+struct Sm {
+    float* Ccur;          // k * NP  centroids of the current step
+    float* Cnew;          // k * NP  owner-computed updates
+    float* CC;            // k       fl(||c||^2) FMA chain
+    long long* ACC;       // k * NP * 3 fixed-point coordinate sums
+    int* cnt;             // k
+    unsigned char* deg;   // k       worker's degenerate flags (identical copies)
+    unsigned char* empty; // k       owner-computed empties of the last assignment
+    unsigned char* emptyall;  // k   gathered empties
+    Xch* x;
+    unsigned __int128* red128;    // kWarps
+    long long* red64;             // kWarps + 1
+    unsigned int* redu;           // kWarps
+    CertC* cert;
+    long long* bcast;             // broadcast slots: 0 f, 1 stop, 2 M/pick, 3 base,
+                                  // 4 total, 5-7 candidates, 8 deadline flag
+};
+
+template <int NP>
+__device__ inline Sm<NP> carve(int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* p = smem_raw;
+    Sm<NP> s;
+    s.Ccur = (float*)p;            p += align16((size_t)k * NP * 4);
+    s.Cnew = (float*)p;            p += align16((size_t)k * NP * 4);
+    s.CC = (float*)p;              p += align16((size_t)k * 4);
+    s.ACC = (long long*)p;         p += align16((size_t)k * NP * 3 * 8);
+    s.cnt = (int*)p;               p += align16((size_t)k * 4);
+    s.deg = p;                     p += align16((size_t)k);
+    s.empty = p;                   p += align16((size_t)k);
+    s.emptyall = p;                p += align16((size_t)k);
+    s.x = (Xch*)p;                 p += align16(sizeof(Xch));
+    s.red128 = (unsigned __int128*)p; p += align16(sizeof(unsigned __int128) * kWarps);
+    s.red64 = (long long*)p;       p += align16(8 * (kWarps + 1));
+    s.redu = (unsigned int*)p;     p += align16(4 * kWarps);
+    s.cert = (CertC*)p;            p += align16(sizeof(CertC));
+    s.bcast = (long long*)p;
+    return s;
+}
+
+template <int NP>
+struct RowsPerThread { static constexpr int v = (64 / NP) > 8 ? 8 : ((64 / NP) < 1 ? 1 : 64 / NP); };
+
+// ---------------------------------------------------------------- the CTA
+template <int NP>
+struct Worker {
+    const WorkerArgs& a;
+    cg::cluster_group cl;
+    Sm<NP> sm;
+    int rank, cs, w, k, n;
+    Grids g;
+    float* S; long long* idx; unsigned int* draws; unsigned int* hkey; unsigned int* htmin;
+    float* D2; float* Cw_mine;
+
+    __device__ Worker(const WorkerArgs& args, cg::cluster_group c) : a(args), cl(c) {
+        cs = a.cs;
+        rank = (int)cl.block_rank();
+        w = blockIdx.x / cs;
+        k = a.k;
+        n = a.n;
+        sm = carve<NP>(k);
+        g = grids_from_maxbits(a.glob->maxbits);
+        S = a.S + (long long)w * a.S_stride;
+        idx = a.idx + (long long)w * a.idx_stride;
+        draws = a.draws + (long long)w * a.draws_stride;
+        hkey = a.hkey + (long long)w * a.hash_stride;
+        htmin = a.htmin + (long long)w * a.hash_stride;
+        D2 = a.D2 + (long long)w * a.D2_stride;
+        Cw_mine = a.Cw_cta + ((long long)w * cs + rank) * (long long)k * NP;
+    }
+
+    __device__ Xch* rx(int q) { return cl.map_shared_rank(sm.x, q); }
+
+    __device__ void slice(long long s, long long& lo, long long& hi) const {
+        lo = s * rank / cs;
+        hi = s * (rank + 1) / cs;
+    }
+
+    // cluster barrier that also orders global-memory writes
+    __device__ void csync_global() {
+        __threadfence();
+        cl.sync();
+    }
+
+    // ------------------------------------------------------ centroid prep
+    __device__ void load_centroids(const float* src) {
+        for (int e = threadIdx.x; e < k * NP; e += kThreads) sm.Ccur[e] = src[e];
+        __syncthreads();
+    }
+    __device__ void store_centroids(float* dst) {
+        for (int e = threadIdx.x; e < k * NP; e += kThreads) dst[e] = sm.Ccur[e];
+        __syncthreads();
+    }
+    // fl(||c_j||^2) as an FMA chain and the certificate's upper bounds.
+    __device__ void prep_centroids() {
+        unsigned int mx = 0;
+        for (int j = threadIdx.x; j < k; j += kThreads) {
+            const float* c = sm.Ccur + (size_t)j * NP;
+            float acc = 0.f, up = 0.f;
+#pragma unroll
+            for (int d = 0; d < NP; ++d) {
+                acc = __fmaf_rn(c[d], c[d], acc);
+                up = __fmaf_ru(c[d], c[d], up);
+            }
+            sm.CC[j] = acc;
+            mx = max(mx, __float_as_uint(up));
+        }
+        const unsigned int m = block_max_u32(mx, sm.redu);
+        if (threadIdx.x == 0) {
+            sm.cert->cmax2 = __uint_as_float(m);
+            sm.cert->cmax = __fsqrt_ru(__uint_as_float(m));
+        }
+        __syncthreads();
+    }
+
+    // ------------------------------------------------------------ a1: sample
+    __device__ unsigned int hash_slot(unsigned int r) const {
+        return (unsigned int)((r * 0x9E3779B1u) & (unsigned int)(a.H - 1));
+    }
+    __device__ void hash_insert(unsigned int r, unsigned int t) {
+        const unsigned int key = r + 1u, mask = (unsigned int)(a.H - 1);
+        unsigned int h = hash_slot(r);
+        for (long long probe = 0; probe < a.H; ++probe) {
+            const unsigned int prev = atomicCAS(&hkey[h], 0u, key);
+            if (prev == 0u || prev == key) { atomicMin(&htmin[h], t); return; }
+            h = (h + 1u) & mask;
+        }
+    }
+    __device__ bool is_first(unsigned int r, unsigned int t) const {
+        const unsigned int key = r + 1u, mask = (unsigned int)(a.H - 1);
+        unsigned int h = hash_slot(r);
+        for (long long probe = 0; probe < a.H; ++probe) {
+            const unsigned int kk = hkey[h];
+            if (kk == key) return htmin[h] == t;
+            if (kk == 0u) return false;
+            h = (h + 1u) & mask;
+        }
+        return false;
+    }
+
+    // First s distinct Lemire draws in [0, m) of stream k1, in order of first
+    // occurrence, written to idx[0..s).  Returns false (uniformly) if more
+    // than Tcap draws would be needed.
+    __device__ bool sample(unsigned long long k1, long long s, long long* out) {
+        const long long m = a.m;
+        {
+            const long long per = (a.H + cs - 1) / cs;
+            const long long b0 = per * rank, b1 = min(a.H, b0 + per);
+            for (long long i = b0 + threadIdx.x; i < b1; i += kThreads) { hkey[i] = 0u; htmin[i] = 0xffffffffu; }
+        }
+        csync_global();
+        if (s == 0) return true;
+        const unsigned long long thr = lemire_thr((unsigned long long)m);
+        long long T_done = 0;
+        long long T = min(a.Tcap, s + (s * s) / m + 64);
+        bool ok = false;
+        for (int batch = 0; batch < 64; ++batch) {
+            {   // draws [T_done, T)
+                const long long span = T - T_done;
+                const long long b0 = T_done + span * rank / cs, b1 = T_done + span * (rank + 1) / cs;
+                for (long long t = b0 + threadIdx.x; t < b1; t += kThreads) {
+                    const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
+                    const unsigned int r = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
+                    draws[t] = r;
+                    hash_insert(r, (unsigned int)t);
+                }
+            }
+            csync_global();
+            // first occurrences over [0, T): contiguous chunk per thread
+            const long long b0 = T * rank / cs, b1 = T * (rank + 1) / cs;
+            const long long ch = (b1 - b0 + kThreads - 1) / kThreads;
+            const long long c0 = b0 + ch * threadIdx.x, c1 = min(b1, c0 + ch);
+            long long mine = 0;
+            for (long long t = c0; t < c1; ++t) mine += is_first(draws[t], (unsigned int)t) ? 1 : 0;
+            long long ctaTot;
+            const long long excl = block_exscan(mine, sm.red64, &ctaTot);
+            if (threadIdx.x == 0) sm.x->nkeep = ctaTot;
+            cl.sync();
+            long long base = 0, total = 0;
+            for (int q = 0; q < cs; ++q) {
+                const long long v = rx(q)->nkeep;
+                if (q < rank) base += v;
+                total += v;
+            }
+            if (total >= s) {
+                long long pos = base + excl;
+                for (long long t = c0; t < c1 && pos < s; ++t) {
+                    const unsigned int r = draws[t];
+                    if (is_first(r, (unsigned int)t)) out[pos++] = (long long)r;
+                }
+                ok = true;
+                break;
+            }
+            if (T >= a.Tcap) break;
+            T_done = T;
+            T = min(a.Tcap, 2 * T);
+        }
+        csync_global();
+        return ok;
+    }
+
+    // ------------------------------------------------------------ a2: gather
+    __device__ void gather(long long s, const long long* ix) {
+        long long lo, hi;
+        slice(s, lo, hi);
+        constexpr int Q = NP / 4;
+        const long long items = (hi - lo) * Q;
+        for (long long e = threadIdx.x; e < items; e += kThreads) {
+            const long long i = lo + e / Q;
+            const int q = (int)(e % Q);
+            const long long row = ix[i];
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row >= 0 && row < a.m) {
+                const float* xr = a.X + row * (long long)n;
+                v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
+                v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
+                v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
+                v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+            } else if (q == 0) {
+                atomicOr(&a.glob->err, kErrArgs);          // index outside [0, m)
+            }
+            reinterpret_cast<float4*>(S + i * NP)[q] = v;
+        }
+    }
+
+    // --------------------------------------------- a4/a5: assign + accumulate
+    // Assign the CTA's rows against Ccur; accumulate exact sums and counts
+    // when `acc` is set; leave the CTA partial objective in sm.x.
+    __device__ void assign_slice(long long s, bool acc) {
+        constexpr int RT = RowsPerThread<NP>::v;
+        long long lo, hi;
+        slice(s, lo, hi);
+        if (acc) {
+            for (int e = threadIdx.x; e < k * NP * 3; e += kThreads) sm.ACC[e] = 0;
+            for (int e = threadIdx.x; e < k; e += kThreads) sm.cnt[e] = 0;
+        }
+        __syncthreads();
+        const CertC cc = *sm.cert;
+        const float gB = a.gB, gp2 = a.gp2;
+        const int gx = g.gx, gf = g.gf;
+        unsigned __int128 facc = 0;
+        unsigned int inex = 0, resc = 0;
+        bool ok = true;
+        for (long long base = lo + (long long)threadIdx.x * RT; base < hi; base += (long long)kThreads * RT) {
+            float m2x[RT][NP];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const long long row = base + r;
+                if (row < hi) {
+                    const float4* p = reinterpret_cast<const float4*>(S + row * NP);
+#pragma unroll
+                    for (int q = 0; q < NP / 4; ++q) {
+                        const float4 v = p[q];
+                        m2x[r][4 * q + 0] = -2.f * v.x;
+                        m2x[r][4 * q + 1] = -2.f * v.y;
+                        m2x[r][4 * q + 2] = -2.f * v.z;
+                        m2x[r][4 * q + 3] = -2.f * v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < NP; ++d) m2x[r][d] = 0.f;
+                }
+            }
+            float g1[RT], g2[RT];
+            int j1[RT];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) { g1[r] = __int_as_float(0x7f800000); g2[r] = g1[r]; j1[r] = 0; }
+            for (int j = 0; j < k; ++j) {
+                const float* cj = sm.Ccur + (size_t)j * NP;
+                const float ccj = sm.CC[j];
+                float e[RT];
+#pragma unroll
+                for (int r = 0; r < RT; ++r) e[r] = ccj;
+#pragma unroll
+                for (int q = 0; q < NP / 4; ++q) {
+                    const float4 cv = reinterpret_cast<const float4*>(cj)[q];
+#pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        e[r] = __fmaf_rn(m2x[r][4 * q + 0], cv.x, e[r]);
+                        e[r] = __fmaf_rn(m2x[r][4 * q + 1], cv.y, e[r]);
+                        e[r] = __fmaf_rn(m2x[r][4 * q + 2], cv.z, e[r]);
+                        e[r] = __fmaf_rn(m2x[r][4 * q + 3], cv.w, e[r]);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    g2[r] = fminf(g2[r], fmaxf(g1[r], e[r]));
+                    j1[r] = (e[r] < g1[r]) ? j : j1[r];
+                    g1[r] = fminf(g1[r], e[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const long long row = base + r;
+                if (row >= hi) continue;
+                float x[NP];
+                float xn2 = 0.f;
+#pragma unroll
+                for (int d = 0; d < NP; ++d) {
+                    x[d] = -0.5f * m2x[r][d];
+                    xn2 = __fmaf_ru(x[d], x[d], xn2);
+                }
+                const float xn = __fsqrt_ru(xn2);
+                int lab;
+                float dv;
+                if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
+                    lab = j1[r];
+                    dv = d32<NP>(x, sm.Ccur + (size_t)lab * NP);
+                } else {
+                    resc++;
+                    lab = 0;
+                    dv = d32<NP>(x, sm.Ccur);
+                    for (int j = 1; j < k; ++j) {
+                        const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
+                        if (dj < dv) { dv = dj; lab = j; }
+                    }
+                }
+                acc_obj(facc, dv, gf, inex);
+                if (acc) {
+                    atomicAdd(&sm.cnt[lab], 1);
+                    long long* wb = sm.ACC + (size_t)lab * NP * 3;
+#pragma unroll
+                    for (int d = 0; d < NP; ++d)
+                        if (d < n) ok &= acc_digits(wb + d * 3, x[d], gx, inex);
+                }
+            }
+        }
+        if (!ok) atomicOr(&a.glob->err, kErrDigits);
+        const unsigned __int128 F = block_sum_u128(facc, sm.red128);
+        const unsigned long long I = block_sum<unsigned long long>(inex, reinterpret_cast<unsigned long long*>(sm.red64));
+        const unsigned long long R = block_sum<unsigned long long>(resc, reinterpret_cast<unsigned long long*>(sm.red64));
+        if (threadIdx.x == 0) {
+            sm.x->f_lo = (unsigned long long)F;
+            sm.x->f_hi = (unsigned long long)(F >> 64);
+            sm.x->inexact = I;
+            sm.x->rescored = R;
+        }
+        __syncthreads();
+    }
+
+    // After a barrier: rank 0 combines the CTA partials into f (exact sum,
+    // rounded once) and records the counters.
+    __device__ double combine_objective() {
+        unsigned __int128 F = 0;
+        unsigned long long I = 0, R = 0;
+        for (int q = 0; q < cs; ++q) {
+            const Xch* p = rx(q);
+            F += ((unsigned __int128)p->f_hi << 64) | (unsigned __int128)p->f_lo;
+            I += p->inexact;
+            R += p->rescored;
+        }
+        if (I) atomicAdd(&a.glob->inexact, I);
+        if (R) atomicAdd(&a.glob->rescored, R);
+        return u128_to_double(F, g.gf);
+    }
+
+    // a6 (owner part): new centroid of each owned cluster j (j % cs == rank):
+    // float(double(exact sum) / count); an empty cluster keeps its centroid.
+    __device__ void owner_update() {
+        const int nOwned = (k - rank + cs - 1) / cs;
+        for (int e = threadIdx.x; e < nOwned * NP; e += kThreads) {
+            const int j = rank + (e / NP) * cs;
+            const int d = e % NP;
+            long long cntj = 0;
+            __int128 V = 0;
+            for (int q = 0; q < cs; ++q) {
+                cntj += cl.map_shared_rank(sm.cnt, q)[j];
+                const long long* wq = cl.map_shared_rank(sm.ACC, q) + ((size_t)j * NP + d) * 3;
+                V += (__int128)wq[0] + (__int128)wq[1] * ((__int128)1 << 32) + (__int128)wq[2] * ((__int128)1 << 64);
+            }
+            float c = sm.Ccur[(size_t)j * NP + d];
+            if (cntj > 0 && d < n) {
+                const double sum = i128_to_double(V, g.gx);
+                c = __double2float_rn(__ddiv_rn(sum, (double)cntj));
+            }
+            sm.Cnew[(size_t)j * NP + d] = c;
+            if (d == 0) sm.empty[j] = (cntj == 0) ? 1 : 0;
+        }
+    }
+
+    __device__ void pull_new_centroids() {
+        for (int e = threadIdx.x; e < k * NP; e += kThreads) {
+            const int j = e / NP;
+            sm.Ccur[e] = cl.map_shared_rank(sm.Cnew, j % cs)[e];
+        }
+        __syncthreads();
+    }
+    __device__ void pull_empty() {
+        for (int j = threadIdx.x; j < k; j += kThreads)
+            sm.emptyall[j] = cl.map_shared_rank(sm.empty, j % cs)[j];
+        __syncthreads();
+    }
+
+    // Broadcast rank 0's decision to every thread of this CTA.
+    __device__ void read_decision(double& f, int& stop) {
+        if (threadIdx.x == 0) {
+            const Xch* p0 = rx(0);
+            sm.bcast[0] = __double_as_longlong(p0->fval);
+            sm.bcast[1] = p0->stop;
+        }
+        __syncthreads();
+        f = __longlong_as_double(sm.bcast[0]);
+        stop = (int)sm.bcast[1];
+        __syncthreads();
+    }
+
+    // f(Ccur, S) without updating centroids (recompute of f_hat_w, recheck).
+    __device__ double eval(long long s) {
+        assign_slice(s, false);
+        cl.sync();
+        if (rank == 0 && threadIdx.x == 0) {
+            sm.x->fval = combine_objective();
+            sm.x->stop = 1;
+        }
+        cl.sync();
+        double f; int stop;
+        read_decision(f, stop);
+        if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->eval_rows, (unsigned long long)s);
+        return f;
+    }
+
+    // Lloyd from Ccur (Sec. 4.1; Sec. 5 stop rule).  On return Ccur holds the
+    // result C_a, emptyall its empty clusters, `iters` the number of updates.
+    __device__ double lloyd(long long s, int& iters) {
+        double f_prev = 0.0;
+        int it = 0;
+        for (;;) {
+            assign_slice(s, true);
+            cl.sync();                                       // partials ready
+            owner_update();
+            if (rank == 0 && threadIdx.x == 0) {
+                const double f = combine_objective();
+                int stop;
+                if (it == 0) stop = (a.max_lloyd <= 0);
+                else stop = (__dsub_rn(f_prev, f) <= __dmul_rn(a.tol, f_prev)) || (it >= a.max_lloyd);
+                sm.x->fval = f;
+                sm.x->stop = stop;
+            }
+            cl.sync();                                       // updates + decision ready
+            double f; int stop;
+            read_decision(f, stop);
+            if (stop) {
+                pull_empty();
+                iters = it;
+                return f;
+            }
+            pull_new_centroids();
+            prep_centroids();
+            f_prev = f;
+            ++it;
+        }
+    }
+
+    // ------------------------------------------------ a3: greedy K-means++
+    __device__ static int frexp_exp(unsigned int mb) {   // M = f * 2^E, f in [0.5, 1)
+        const unsigned ef = mb >> 23;
+        if (ef) return (int)ef - 126;
+        return (32 - __clz((int)(mb & 0x7fffff))) - 149;
+    }
+    __device__ static long long quant(float v, int E) {   // floor(v * 2^(31 - E))
+        const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
+        if (!b) return 0;
+        uint32_t mant; int e2;
+        f32_parts(b, mant, e2);
+        const int sh = e2 + 31 - E;
+        if (sh >= 0) return (long long)mant << sh;
+        if (-sh >= 32) return 0;
+        return (long long)(mant >> (-sh));
+    }
+
+    __device__ void load_row(long long i, float (&x)[NP]) const {
+        const float4* p = reinterpret_cast<const float4*>(S + i * NP);
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) {
+            const float4 v = p[q];
+            x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+        }
+    }
+
+    __device__ void kmeanspp(long long s, unsigned long long k1) {
+        long long lo, hi;
+        slice(s, lo, hi);
+        bool any_live = false;
+        for (int j = 0; j < k; ++j) any_live |= (sm.deg[j] == 0);
+        unsigned int mloc = 0;
+        if (any_live) {
+            for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+                float x[NP];
+                load_row(i, x);
+                float dm = __int_as_float(0x7f800000);
+                for (int j = 0; j < k; ++j)
+                    if (!sm.deg[j]) dm = fminf(dm, d32<NP>(x, sm.Ccur + (size_t)j * NP));
+                D2[i] = dm;
+                mloc = max(mloc, __float_as_uint(dm));
+            }
+        }
+        __syncthreads();
+        const int trials = a.trials < 1 ? 1 : (a.trials > 3 ? 3 : a.trials);
+        const long long ch = (hi - lo + kThreads - 1) / kThreads;
+        const long long c0 = lo + ch * threadIdx.x, c1 = min(hi, c0 + ch);
+        for (int j = 0; j < k; ++j) {
+            if (!sm.deg[j]) continue;
+            long long pick;
+            if (!any_live) {
+                pick = (long long)draw_below(a.seed, k1, 0, (unsigned long long)j, (unsigned long long)s);
+            } else {
+                const unsigned int mb = block_max_u32(mloc, sm.redu);
+                if (threadIdx.x == 0) sm.x->maxbits = mb;
+                cl.sync();                                                   // [A]
+                if (threadIdx.x == 0) {
+                    unsigned int M = 0;
+                    for (int q = 0; q < cs; ++q) M = max(M, rx(q)->maxbits);
+                    sm.bcast[2] = M;
+                }
+                __syncthreads();
+                const unsigned int M = (unsigned int)sm.bcast[2];
+                if (M == 0) {
+                    pick = (long long)draw_below(a.seed, k1, 0, (unsigned long long)j, (unsigned long long)s);
+                } else {
+                    const int E = frexp_exp(M);
+                    long long wmine = 0;
+                    for (long long i = c0; i < c1; ++i) wmine += quant(D2[i], E);
+                    long long ctaTot;
+                    const long long excl = block_exscan(wmine, sm.red64, &ctaTot);
+                    if (threadIdx.x == 0) sm.x->wsum = ctaTot;
+                    cl.sync();                                               // [B]
+                    if (threadIdx.x < 4) sm.x->cand[threadIdx.x] = -1;
+                    if (threadIdx.x == 0) {
+                        long long base = 0, tot = 0;
+                        for (int q = 0; q < cs; ++q) {
+                            const long long v = rx(q)->wsum;
+                            if (q < rank) base += v;
+                            tot += v;
+                        }
+                        sm.bcast[3] = base;
+                        sm.bcast[4] = tot;
+                    }
+                    __syncthreads();
+                    const long long base = sm.bcast[3];
+                    const unsigned long long Wtot = (unsigned long long)sm.bcast[4];
+                    for (int l = 0; l < trials; ++l) {
+                        const unsigned long long u = draw_below(a.seed, k1, (unsigned long long)l,
+                                                                (unsigned long long)j, Wtot);
+                        const long long lo_w = base + excl;
+                        if ((long long)u >= lo_w && (long long)u < lo_w + wmine) {
+                            long long run = lo_w;
+                            for (long long i = c0; i < c1; ++i) {
+                                run += quant(D2[i], E);
+                                if (run > (long long)u) { sm.x->cand[l] = (int)i; break; }
+                            }
+                        }
+                    }
+                    cl.sync();                                               // [C]
+                    if (threadIdx.x < trials) {
+                        int c = -1;
+                        for (int q = 0; q < cs; ++q) c = max(c, rx(q)->cand[threadIdx.x]);
+                        sm.bcast[5 + threadIdx.x] = c;
+                    }
+                    __syncthreads();
+                    int cand[3];
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        cand[l] = (l < trials) ? (int)sm.bcast[5 + l] : 0;
+                        if (cand[l] < 0 || cand[l] >= s) {          // cannot happen: prefix covers [0, W)
+                            if (threadIdx.x == 0) atomicOr(&a.glob->err, kErrArgs);
+                            cand[l] = 0;
+                        }
+                    }
+                    long long pot[3] = {0, 0, 0};
+                    for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+                        float x[NP];
+                        load_row(i, x);
+                        const float d2 = D2[i];
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) {
+                            if (l < trials) {
+                                const float dc = d32<NP>(x, S + (long long)cand[l] * NP);
+                                pot[l] += quant(fminf(d2, dc), E);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int l = 0; l < 3; ++l) {
+                        if (l < trials) {
+                            const long long t = block_sum<long long>(pot[l], sm.red64);
+                            if (threadIdx.x == 0) sm.x->pot[l] = t;
+                        }
+                    }
+                    cl.sync();                                               // [D]
+                    if (threadIdx.x == 0) {
+                        long long best = 0;
+                        int bl = 0;
+                        for (int l = 0; l < trials; ++l) {
+                            long long t = 0;
+                            for (int q = 0; q < cs; ++q) t += rx(q)->pot[l];
+                            if (l == 0 || t < best) { best = t; bl = l; }
+                        }
+                        sm.bcast[2] = cand[bl];
+                    }
+                    __syncthreads();
+                    pick = sm.bcast[2];
+                    __syncthreads();
+                }
+            }
+            // centroid j = S[pick]
+            for (int d = threadIdx.x; d < NP; d += kThreads) sm.Ccur[(size_t)j * NP + d] = S[pick * NP + d];
+            __syncthreads();
+            mloc = 0;
+            for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+                float x[NP];
+                load_row(i, x);
+                const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
+                const float v = any_live ? fminf(D2[i], dj) : dj;
+                D2[i] = v;
+                mloc = max(mloc, __float_as_uint(v));
+            }
+            __syncthreads();
+            any_live = true;
+        }
+    }
+};
+
+// trials > 3 would need more broadcast slots; the host caps it at 3.
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a) {
+    Worker<NP> W(a, cg::this_cluster());
+    if (a.glob->nonfinite) return;            // uniform: read before any barrier
+    const int w = W.w;
+
+    if (a.mode == kModeStepSample) {
+        W.sample(stream_k1(a.step_purpose, a.step_worker, a.step_round, a.step_pass), a.step_s, a.idx);
+        W.cl.sync();
+        return;
+    }
+    if (a.mode == kModeStepGather) {
+        W.gather(a.step_s, a.idx);
+        W.csync_global();
+        return;
+    }
+    if (a.mode == kModeStepKpp || a.mode == kModeStepLloyd) {
+        // S (padded) and C (padded, in a.Cw) were staged by the host.
+        W.load_centroids(a.Cw);
+        for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = a.deg[j];
+        __syncthreads();
+        W.cl.sync();
+        if (a.mode == kModeStepKpp) {
+            W.kmeanspp(a.step_s, stream_k1(kPurposeKpp, a.step_worker, a.step_round, a.step_pass));
+        } else {
+            W.prep_centroids();
+            int iters = 0;
+            const double f = W.lloyd(a.step_s, iters);
+            if (W.rank == 0 && threadIdx.x == 0) { *a.step_f = f; *a.step_iters = iters; }
+            if (W.rank == 0)
+                for (int j = threadIdx.x; j < W.k; j += kThreads) a.step_empty[j] = W.sm.emptyall[j];
+        }
+        if (W.rank == 0) W.store_centroids(a.Cw);
+        W.csync_global();
+        return;
+    }
+
+    // worker state for this launch
+    for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = a.deg[(long long)w * W.k + j];
+    for (int e = threadIdx.x; e < W.k * NP; e += kThreads)
+        W.Cw_mine[e] = a.Cw[(long long)w * W.k * NP + e];
+    __syncthreads();
+    double fhat = a.fhat[w];
+
+    if (a.mode == kModeFinalEval) {
+        long long s_lo = a.s_min, s_hi = a.s_max;
+        if (a.set_len > 0) {
+            s_lo = a.set[0]; s_hi = a.set[0];
+            for (int i = 1; i < a.set_len; ++i) { s_lo = min(s_lo, a.set[i]); s_hi = max(s_hi, a.set[i]); }
+        }
+        const long long acc = (long long)a.glob->accepts, Ls = (long long)a.glob->L_sum;
+        long long s_opt = s_hi;
+        if (acc > 0) s_opt = min(max((2 * Ls + acc) / (2 * acc), s_lo), s_hi);
+        if (w == 0 && W.rank == 0 && threadIdx.x == 0) a.glob->s_opt = (int)s_opt;
+        const bool ok = W.sample(stream_k1(kPurposeFinal, 0, 0, 0), s_opt, W.idx);
+        if (!ok) {
+            if (threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
+            W.cl.sync();
+            return;
+        }
+        W.gather(s_opt, W.idx);
+        __syncthreads();
+        W.load_centroids(W.Cw_mine);
+        W.prep_centroids();
+        const double f = W.eval(s_opt);
+        if (W.rank == 0 && threadIdx.x == 0) a.f_final[w] = f;
+        W.cl.sync();
+        return;
+    }
+
+    // ---------------------------------------------------- Algorithm 1 rounds
+    bool failed = false, out_of_time = false;
+    int rounds_completed = 0;
+    for (int t = a.round_begin; t < a.round_end && !failed && !out_of_time; ++t) {
+        long long s_w;
+        {
+            const unsigned long long k1 = stream_k1(kPurposeSize, w, t, 0);
+            if (a.set_len > 0) s_w = a.set[draw_below(a.seed, k1, 0, 0, (unsigned long long)a.set_len)];
+            else s_w = a.s_min + (long long)draw_below(a.seed, k1, 0, 0, (unsigned long long)(a.s_max - a.s_min + 1));
+        }
+        bool all_deg = true;
+        for (int j = 0; j < W.k; ++j) all_deg &= (W.sm.deg[j] != 0);
+        if (!all_deg) {                                  // recompute f_hat_w with the new s_w
+            if (!W.sample(stream_k1(kPurposeEval, w, t, 0), s_w, W.idx)) { failed = true; break; }
+            W.gather(s_w, W.idx);
+            __syncthreads();
+            W.load_centroids(W.Cw_mine);
+            W.prep_centroids();
+            fhat = W.eval(s_w);
+        }
+        for (int p = 0; p < a.P; ++p) {
+            if (a.deadline_ns) {
+                if (W.rank == 0 && threadIdx.x == 0) {
+                    unsigned long long now;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+                    W.sm.x->flag = (now >= a.deadline_ns) ? 1 : 0;
+                }
+                W.cl.sync();
+                if (threadIdx.x == 0) W.sm.bcast[8] = W.rx(0)->flag;
+                __syncthreads();
+                const bool late = W.sm.bcast[8] != 0;
+                W.cl.sync();
+                if (late) { out_of_time = true; break; }
+            }
+            if (!W.sample(stream_k1(kPurposePass, w, t, p), s_w, W.idx)) { failed = true; break; }
+            W.gather(s_w, W.idx);
+            W.csync_global();                            // whole sample visible to the cluster
+            W.load_centroids(W.Cw_mine);
+            bool any_deg = false;
+            for (int j = 0; j < W.k; ++j) any_deg |= (W.sm.deg[j] != 0);
+            if (any_deg) {
+                W.kmeanspp(s_w, stream_k1(kPurposeKpp, w, t, p));
+                W.store_centroids(W.Cw_mine);            // re-seeding is in place (Alg. 1)
+            }
+            W.prep_centroids();
+            int iters = 0;
+            const double f = W.lloyd(s_w, iters);
+            if (f < fhat) {                              // incumbent rule
+                fhat = f;
+                for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = W.sm.emptyall[j];
+                W.store_centroids(W.Cw_mine);
+                if (W.rank == 0 && threadIdx.x == 0) {
+                    const unsigned long long pos = atomicAdd(&a.glob->accepts, 1ull);
+                    atomicAdd(&a.glob->L_sum, (unsigned long long)s_w);
+                    if ((long long)pos < a.L_cap) a.L_buf[pos] = s_w;
+                }
+            }
+            __syncthreads();
+            if (W.rank == 0 && threadIdx.x == 0) {
+                atomicAdd(&a.glob->passes, 1ull);
+                atomicAdd(&a.glob->lloyd_iters, (unsigned long long)iters);
+                atomicAdd(&a.glob->assign_rows, (unsigned long long)(s_w * (iters + 1)));
+            }
+        }
+        if (!failed && !out_of_time) ++rounds_completed;
+    }
+    if (failed && W.rank == 0 && threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
+    // persist worker state
+    if (W.rank == 0) {
+        for (int e = threadIdx.x; e < W.k * NP; e += kThreads)
+            a.Cw[(long long)w * W.k * NP + e] = W.Cw_mine[e];
+        for (int j = threadIdx.x; j < W.k; j += kThreads) a.deg[(long long)w * W.k + j] = W.sm.deg[j];
+        if (threadIdx.x == 0) {
+            a.fhat[w] = fhat;
+            atomicMin(&a.glob->rounds_done, a.round_begin + rounds_completed);
+        }
+    }
+    W.csync_global();
+}
+
+template <int NP>
+cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) {
+    const size_t smem = worker_smem_bytes<NP>(a.k);
+    cudaError_t e = cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    if (a.cs > 8) {
+        e = cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * a.cs), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)a.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, worker_kernel<NP>, a);
+}
+
+}  // namespace bm

@@ -1,0 +1,6 @@
+// Worker kernel instantiated for padded width NP = 8.
+#include "bm_worker_impl.cuh"
+
+namespace bm {
+template cudaError_t launch_worker_t<8>(const WorkerArgs&, int, cudaStream_t);
+}  // namespace bm

@@ -1,0 +1,236 @@
+"""Thin Python binding of libbigmeans (include/bigmeans.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device buffers are torch tensors (PyTorch provides memory and
+streams); they are passed to the C ABI as raw pointers.  If the compiled
+library is missing this module raises at import -- there is no CPU path.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbigmeans.so")
+
+BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EINTERNAL = range(6)
+STATUS_NAMES = {0: "BM_OK", 1: "BM_EINVAL", 2: "BM_ENOMEM", 3: "BM_ECUDA", 4: "BM_ETIMEOUT",
+                5: "BM_EINTERNAL"}
+RNG_SIZE, RNG_EVAL, RNG_PASS, RNG_KPP, RNG_FINAL = 1, 2, 3, 4, 5
+
+
+class SamplePolicy(ctypes.Structure):
+    _fields_ = [("s_min", ctypes.c_int64), ("s_max", ctypes.c_int64),
+                ("set", ctypes.c_int64 * 16), ("set_len", ctypes.c_int32),
+                ("workers", ctypes.c_int32), ("passes", ctypes.c_int32)]
+
+
+class Budget(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("seconds", ctypes.c_double),
+                ("max_lloyd", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("kpp_candidates", ctypes.c_int32), ("eval_full_each_round", ctypes.c_int32)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("f_full", ctypes.c_double), ("f_incumbent", ctypes.c_double),
+                ("s_opt", ctypes.c_int64), ("best_worker", ctypes.c_int32),
+                ("rounds_done", ctypes.c_int32), ("passes_done", ctypes.c_int64),
+                ("lloyd_iters", ctypes.c_int64), ("assign_rows", ctypes.c_int64),
+                ("accepts", ctypes.c_int64), ("L_sum", ctypes.c_int64),
+                ("rescored_rows", ctypes.c_int64), ("inexact_terms", ctypes.c_int64),
+                ("t_total_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class BigmeansError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+lib = ctypes.CDLL(LIB_PATH)
+
+_p = ctypes.c_void_p
+_i32, _i64, _u64, _dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+_PP, _BP, _RP = ctypes.POINTER(SamplePolicy), ctypes.POINTER(Budget), ctypes.POINTER(Report)
+
+# Every symbol include/bigmeans.h declares, with its signature.
+SIGNATURES = {
+    "bigmeans_fit": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
+    "bigmeans_fit_host": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
+    "bm_fit_create": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_p)]),
+    "bm_fit_rounds": (_i32, [_p, _i32]),
+    "bm_fit_finish": (_i32, [_p, _p, _p, _RP]),
+    "bm_fit_destroy": (None, [_p]),
+    "bm_sample": (_i32, [_u64, _i32, _i32, _i32, _i32, _i64, _i64, _p, _p]),
+    "bm_gather": (_i32, [_p, _i64, _i32, _p, _i64, _p, _p]),
+    "bm_kmeanspp": (_i32, [_p, _i64, _i32, _p, _i32, _p, _i32, _u64, _i32, _i32, _i32, _p]),
+    "bm_lloyd": (_i32, [_p, _i64, _i32, _p, _i32, _i32, _dbl, ctypes.POINTER(_dbl),
+                        ctypes.POINTER(_i32), _p, _p]),
+    "bm_assign": (_i32, [_p, _i64, _i32, _p, _i32, _p, ctypes.POINTER(_dbl), _RP, _p]),
+    "bm_last_error": (ctypes.c_char_p, []),
+    "bm_version": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def _check(status):
+    if status != BM_OK:
+        raise BigmeansError(status, lib.bm_last_error().decode())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_f32(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    return t.contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10):
+    pol = SamplePolicy()
+    if sizes:
+        sizes = list(sizes)
+        assert 1 <= len(sizes) <= 16
+        for i, v in enumerate(sizes):
+            pol.set[i] = int(v)
+        pol.set_len = len(sizes)
+        pol.s_min, pol.s_max = min(sizes), max(sizes)
+    else:
+        pol.s_min, pol.s_max, pol.set_len = int(s_min), int(s_max), 0
+    pol.workers, pol.passes = int(workers), int(passes)
+    return pol
+
+
+def make_budget(rounds=2, seconds=0.0, max_lloyd=300, tol=1e-4, kpp_candidates=3,
+                eval_full_each_round=False):
+    b = Budget()
+    b.rounds, b.seconds, b.max_lloyd, b.tol = int(rounds), float(seconds), int(max_lloyd), float(tol)
+    b.kpp_candidates, b.eval_full_each_round = int(kpp_candidates), int(bool(eval_full_each_round))
+    return b
+
+
+def fit(X, k, policy, budget, seed=0, labels=True, stream=None):
+    """bigmeans_fit on a CUDA tensor X (m x n).  Returns (C, labels|None, report)."""
+    X = _dev_f32(X, "X")
+    m, n = X.shape
+    C = torch.empty((k, n), dtype=torch.float32, device=X.device)
+    Y = torch.empty(m, dtype=torch.int32, device=X.device) if labels else None
+    rep = Report()
+    _check(lib.bigmeans_fit(_ptr(X), m, n, k, ctypes.byref(policy), ctypes.byref(budget), seed,
+                            _stream(stream), _ptr(C), _ptr(Y), ctypes.byref(rep)))
+    return C, Y, rep.as_dict()
+
+
+def fit_host(X, k, policy, budget, seed=0, labels=True, stream=None):
+    """bigmeans_fit_host on host memory (numpy or CPU tensor); copies happen inside."""
+    Xn = np.ascontiguousarray(X.numpy() if isinstance(X, torch.Tensor) else X, dtype=np.float32)
+    m, n = Xn.shape
+    C = np.empty((k, n), dtype=np.float32)
+    Y = np.empty(m, dtype=np.int32) if labels else None
+    rep = Report()
+    _check(lib.bigmeans_fit_host(Xn.ctypes.data_as(_p), m, n, k, ctypes.byref(policy),
+                                 ctypes.byref(budget), seed, _stream(stream),
+                                 C.ctypes.data_as(_p),
+                                 Y.ctypes.data_as(_p) if Y is not None else _p(0),
+                                 ctypes.byref(rep)))
+    return C, Y, rep.as_dict()
+
+
+class FitSession:
+    """Staged fit (bm_fit_create / bm_fit_rounds / bm_fit_finish)."""
+
+    def __init__(self, X, k, policy, budget, seed=0, stream=None):
+        self.X = _dev_f32(X, "X")
+        self.k = k
+        self.stream = stream
+        self.ctx = ctypes.c_void_p(0)
+        m, n = self.X.shape
+        _check(lib.bm_fit_create(_ptr(self.X), m, n, k, ctypes.byref(policy), ctypes.byref(budget),
+                                 seed, _stream(stream), ctypes.byref(self.ctx)))
+
+    def rounds(self, r):
+        _check(lib.bm_fit_rounds(self.ctx, int(r)))
+
+    def finish(self, labels=True):
+        m, n = self.X.shape
+        C = torch.empty((self.k, n), dtype=torch.float32, device=self.X.device)
+        Y = torch.empty(m, dtype=torch.int32, device=self.X.device) if labels else None
+        rep = Report()
+        _check(lib.bm_fit_finish(self.ctx, _ptr(C), _ptr(Y), ctypes.byref(rep)))
+        return C, Y, rep.as_dict()
+
+    def close(self):
+        if self.ctx:
+            lib.bm_fit_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p(0)
+
+    def __del__(self):
+        self.close()
+
+
+def sample(seed, purpose, worker, rnd, pss, m, s, device="cuda", stream=None):
+    out = torch.empty(max(int(s), 1), dtype=torch.int64, device=device)
+    _check(lib.bm_sample(seed, purpose, worker, rnd, pss, m, s, _ptr(out), _stream(stream)))
+    return out[: int(s)]
+
+
+def gather(X, idx, stream=None):
+    X = _dev_f32(X, "X")
+    idx = idx.to(torch.int64).contiguous()
+    S = torch.empty((idx.numel(), X.shape[1]), dtype=torch.float32, device=X.device)
+    _check(lib.bm_gather(_ptr(X), X.shape[0], X.shape[1], _ptr(idx), idx.numel(), _ptr(S),
+                         _stream(stream)))
+    return S
+
+
+def kmeanspp(S, C, degenerate, trials, seed, worker, rnd, pss, stream=None):
+    S = _dev_f32(S, "S")
+    C = _dev_f32(C, "C").clone()
+    deg = torch.as_tensor(degenerate, dtype=torch.uint8, device=S.device).contiguous()
+    _check(lib.bm_kmeanspp(_ptr(S), S.shape[0], S.shape[1], _ptr(C), C.shape[0], _ptr(deg), trials,
+                           seed, worker, rnd, pss, _stream(stream)))
+    return C
+
+
+def lloyd(S, C, max_iter=300, tol=1e-4, stream=None):
+    S = _dev_f32(S, "S")
+    C = _dev_f32(C, "C").clone()
+    empty = torch.empty(C.shape[0], dtype=torch.uint8, device=S.device)
+    f = ctypes.c_double(0)
+    it = ctypes.c_int32(0)
+    _check(lib.bm_lloyd(_ptr(S), S.shape[0], S.shape[1], _ptr(C), C.shape[0], max_iter, tol,
+                        ctypes.byref(f), ctypes.byref(it), _ptr(empty), _stream(stream)))
+    return C, f.value, it.value, empty.bool()
+
+
+def assign(X, C, labels=True, stream=None):
+    X = _dev_f32(X, "X")
+    C = _dev_f32(C, "C")
+    Y = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) if labels else None
+    f = ctypes.c_double(0)
+    rep = Report()
+    _check(lib.bm_assign(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(Y),
+                         ctypes.byref(f), ctypes.byref(rep), _stream(stream)))
+    return Y, f.value, rep.as_dict()
+
+
+def version():
+    return lib.bm_version().decode()

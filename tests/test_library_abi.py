@@ -1,0 +1,59 @@
+"""CPU checks of the C ABI library: it builds, loads without a GPU and exports
+every function include/bigmeans.h declares; the binding declares the same set."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bigmeans.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:bm_status|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)
+    return set(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2403_18766_gb300 import build
+    build.build()
+    import ctypes
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("bigmeans_fit", "bigmeans_fit_host", "bm_sample", "bm_gather", "bm_kmeanspp",
+              "bm_lloyd", "bm_assign", "bm_last_error", "bm_fit_create", "bm_fit_rounds",
+              "bm_fit_finish", "bm_fit_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    from paper_2403_18766_gb300 import native
+    assert set(native.SIGNATURES) == _declared()
+    assert native.version().startswith("bigmeans-gb300")
+
+
+def test_struct_layouts_match_c():
+    import ctypes
+    from paper_2403_18766_gb300 import native
+    # offsets follow C's natural alignment rules for these field lists
+    assert ctypes.sizeof(native.SamplePolicy) == 8 + 8 + 16 * 8 + 4 + 4 + 4 + 4
+    assert native.Budget.seconds.offset == 8 and native.Budget.tol.offset == 24
+    assert ctypes.sizeof(native.Report) == 8 * 3 + 4 + 4 + 8 * 7 + 8
+
+
+def test_errors_without_gpu_are_status_codes(lib):
+    from paper_2403_18766_gb300 import native
+    # argument checks happen before any CUDA call
+    st = native.lib.bm_sample(1, 3, 0, 0, 0, 10, 11, None, None)
+    assert st == native.BM_EINVAL
+    assert b"out of range" in native.lib.bm_last_error()
