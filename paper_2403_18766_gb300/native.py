@@ -104,8 +104,10 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10):
+def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10, set=None):
+    """bm_sample_policy: a size range [s_min, s_max] or a set of sizes (`sizes` or `set`)."""
     pol = SamplePolicy()
+    sizes = sizes if sizes is not None else set
     if sizes:
         sizes = list(sizes)
         assert 1 <= len(sizes) <= 16
