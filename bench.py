@@ -1,0 +1,316 @@
+"""Benchmark: competitive-sample-size Big-means on one GB300 (or N, one per rank).
+
+Workload (the configuration the headline metric is quoted on):
+  m = 1,000,000 rows, n = 16, mixture of 25 anisotropic Gaussians
+  (eigenvalues in [0.1, 4], Dirichlet(1) weights), k = 25, 16 competing
+  workers, sample sizes uniform in [1,000, 64,000], p = 10 passes per round,
+  Lloyd <= 300 iterations / tol 1e-4, K-means++ with 3 candidates, and the
+  full-data f(C, X) of the incumbent after every round.
+
+One step = one round of Algorithm 1 for all workers (f_hat recompute, 10
+passes of sample + gather + re-seed + Lloyd + incumbent rule) plus the
+full-data pass that evaluates the incumbent.  Metric: Lloyd pts*k/s = (rows
+assigned inside Lloyd runs) * k / device time.  L2 is flushed (256 MB write)
+between timed steps, outside the timed region.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "gmm_1m_n16_k25"
+K_CLUSTERS = 25
+POLICY = dict(s_min=1000, s_max=64000, workers=16, passes=10)
+BUDGET = dict(max_lloyd=300, tol=1e-4, kpp_candidates=3, eval_full_each_round=True)
+METRIC = "Lloyd pts·k/s"
+UNIT = "pts·k/s"
+FP32_LANES_PER_SM = 128                  # FP32 FMA lanes per SM (4 SMSPs x 32)
+NOMINAL_SMS, NOMINAL_MAX_MHZ = 152, 2070.0
+
+
+def config_dict(m, n):
+    return {"workload": f"{WORKLOAD}: m={m}, n={n}, 25 anisotropic Gaussians, k={K_CLUSTERS}, "
+                        f"W={POLICY['workers']} workers, s in [{POLICY['s_min']}, {POLICY['s_max']}], "
+                        f"p={POLICY['passes']}",
+            "m": m, "n": n, "k": K_CLUSTERS, "workers": POLICY["workers"],
+            "s_range": [POLICY["s_min"], POLICY["s_max"]], "passes": POLICY["passes"],
+            "step": "one Algorithm-1 round (all workers) + full-data pass of the incumbent",
+            "l2": "flushed between timed steps (256 MB write), outside the timed region"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": NOMINAL_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(device_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _traffic_for(kernel_sources):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the source."""
+    h = hashlib.sha256()
+    for p in kernel_sources:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tr = json.load(fh)
+    except OSError:
+        return None, digest
+    ent = tr.get(digest)
+    return (ent if ent else None), digest
+
+
+def cpu_baseline(X, seconds_target=20.0):
+    """The oracle as it stands, on a bounded sample of the same workload: one
+    worker, p passes per round, rounds doubled until about seconds_target/2."""
+    from oracle import bigmeans as obm
+    rounds, res, dt = 1, None, 0.0
+    while True:
+        pol = dict(POLICY, workers=1)
+        t0 = time.perf_counter()
+        res = obm.bigmeans(X, K_CLUSTERS, pol, dict(BUDGET, rounds=rounds, eval_full_each_round=False),
+                           seed=1)
+        dt = time.perf_counter() - t0
+        if dt >= seconds_target / 2 or rounds >= 64:
+            break
+        rounds *= 2
+    ptsk = res["log"]["pts_k"]
+    return {"value": ptsk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 worker x {rounds} rounds x {POLICY['passes']} passes of the same workload "
+                      f"({res['log']['lloyd_iters']} Lloyd updates, {ptsk:.3g} pts*k; time includes "
+                      f"sampling, K-means++, the recheck and the final full pass) in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    from paper_2403_18766_gb300.synthetic import workload
+    X = workload(WORKLOAD)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(X, seconds_target=3.0)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(X, seconds_target=6.0))
+    v = statistics.median([c["value"] for c in vals])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/f32 (oracle)", "data": "synthetic",
+            "config": config_dict(*X.shape),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2403_18766_gb300 import native
+    from paper_2403_18766_gb300.synthetic import workload
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    X = workload(WORKLOAD)
+    m, n = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    pol = native.make_policy(**POLICY)
+    total_rounds = args.warmup + args.steps
+    bud = native.make_budget(rounds=total_rounds, **BUDGET)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    sess = native.FitSession(Xd, K_CLUSTERS, pol, bud, seed=1000 + rank)
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        sess.rounds(1)
+    rep0 = sess.report()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sess.rounds(1)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms.append(a.elapsed_time(b))
+    rep1 = sess.report()
+    clk = clocks.stop()
+    C, _, rep_fin = sess.finish(labels=False)
+    sess.close()
+
+    t_local = sum(step_ms) / 1e3
+    rows = rep1["assign_rows"] - rep0["assign_rows"]
+    ptsk_local = rows * K_CLUSTERS
+    launches = rep1["kernel_launches"] - rep0["kernel_launches"]
+    t_worker = rep1["t_worker_s"] - rep0["t_worker_s"]
+    n_worker = args.steps                       # one sampling + W worker launches per step
+    t_full = rep1["t_fullpass_s"] - rep0["t_fullpass_s"]
+    n_full = rep1["fullpass_launches"] - rep0["fullpass_launches"]
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        p = torch.tensor([float(ptsk_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+        t_job, ptsk = float(t.item()), float(p.item())
+    else:
+        t_job, ptsk = t_local, float(ptsk_local)
+
+    peaks, peak_src = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", NOMINAL_MAX_MHZ))
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12        # TFLOP/s
+    flops = 2.0 * n * K_CLUSTERS * rows
+    achieved = flops / t_worker / 1e12 if t_worker > 0 else 0.0
+    srcs = [os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
+            for f in ("bm_worker_impl.cuh", "bm_sample.cu", "bm_device.cuh")]
+    traffic, digest = _traffic_for(srcs)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak if alu_peak else None,
+                "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
+                "kernel": "round phase: sample_kernel<16> (all samples of the round) + "
+                          "worker_kernel<16> x W (K-means++, Lloyd, incumbent rule), timed together "
+                          "from fork to join",
+                "algorithmic": "2*n*k flops per row assigned inside Lloyd; "
+                               f"{flops / max(n_worker, 1):.4g} flops per round phase",
+                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "source_digest": digest}
+    bytes_full = m * n * 4.0
+    full_gbs = bytes_full * n_full / t_full / 1e9 if t_full > 0 else 0.0
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof_full = {"bound": "hbm", "achieved": full_gbs, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": full_gbs / hbm_peak, "traffic": None,
+                 "kernel": "fullpass_kernel<16> (labels + f(C, X))",
+                 "algorithmic": f"m*n*4 = {bytes_full:.4g} bytes per launch (X read once)",
+                 "avg_launch_us": t_full / max(n_full, 1) * 1e6, "peak_source": peak_src}
+
+    # e2e: the same metric through the host-buffer C-ABI call, H2D and D2H inside
+    e2e = None
+    if rank == 0 or ws > 1:
+        Xp = torch.from_numpy(X).pin_memory()
+        e2e_bud = native.make_budget(rounds=2, **BUDGET)
+        e2e_vals = []
+        for i in range(max(2, min(args.steps, 4))):
+            t0 = time.perf_counter()
+            _, _, r = native.fit_host(Xp, K_CLUSTERS, pol, e2e_bud, seed=77 + i, labels=True)
+            dt = time.perf_counter() - t0
+            e2e_vals.append(r["assign_rows"] * K_CLUSTERS / dt)
+        e2e = {"value": statistics.median(e2e_vals), "unit": UNIT,
+               "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": K_CLUSTERS * n * 4 + m * 4,
+               "step": "one bigmeans_fit_host call (2 rounds + final recheck + labels) from "
+                       "pinned host memory"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ptsk / t_job, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_job * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_dict(m, n),
+                "roofline": roofline, "roofline_fullpass": roof_full,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk,
+                "detail": {"step_ms": step_ms, "lloyd_rows": rows, "worker_ms_per_launch":
+                           t_worker / max(n_worker, 1) * 1e3,
+                           "rescored_rows": rep1["rescored_rows"],
+                           "reseeded": rep1["reseeded"] - rep0["reseeded"],
+                           "trace_cycles": [b - a for a, b in zip(rep0["trace_cycles"],
+                                                                   rep1["trace_cycles"])],
+                           "inexact_terms": rep1["inexact_terms"],
+                           "f_incumbent": rep1["f_incumbent"], "f_final": rep_fin["f_full"],
+                           "s_opt": rep_fin["s_opt"], "peaks": peak_src}}
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -19,9 +19,10 @@
  * - Errors are reported by status code only; nothing is thrown across the
  *   ABI.  bm_last_error() returns a thread-local message for the last
  *   non-OK status of the calling thread.
- * - Limits: 1 <= n <= 64, 1 <= k, k <= s_min, m < 2^31, and the centroid
+ * - Limits: 1 <= n <= 64, 1 <= k, k <= s_min, m < 2^31, s_max <= 524,272
+ *   (16 CTAs of at most 32,767 sample rows per worker), and the centroid
  *   accumulators of one cluster must fit in shared memory
- *   (k * round_up(n) * 32 bytes <= 200 KB; e.g. k <= 100 at n = 64).
+ *   (about k * round_up(n) * 32 bytes <= 220 KB; e.g. k <= 100 at n = 64).
  *   Non-finite values in X are rejected with BM_EINVAL.
  *
  * Numeric definition ("exact mode", the only mode so far)
@@ -113,6 +114,19 @@ typedef struct {
                                certified and were re-scored in direct form    */
     int64_t inexact_terms;  /* values truncated by the fixed-point grids      */
     double t_total_s;       /* wall time of the call                          */
+    double t_worker_s;      /* device time of the worker-kernel launches
+                               (CUDA events on the caller's stream)           */
+    double t_fullpass_s;    /* device time of the full-data passes            */
+    int64_t kernel_launches;    /* kernels of this library launched so far    */
+    int64_t fullpass_launches;  /* full-pass launches                         */
+    int64_t reseeded;       /* centroids (re)seeded by K-means++              */
+    int64_t trace_cycles[8];  /* SM cycles on rank 0 of each worker cluster:
+                                 [0] K-means++, [1] Lloyd assignment,
+                                 [2] Lloyd exchange (barriers, reduction,
+                                 update), [3] f_hat recompute, [4] sum of
+                                 worker-kernel times, [5] longest worker
+                                 kernel, [6] Lloyd assignments (count),
+                                 [7] worker kernels (count)              */
 } bm_report;
 
 /* ---------------------------------------------------------------------------
@@ -151,6 +165,10 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k,
 bm_status bm_fit_rounds(bm_fit_ctx* ctx, int32_t rounds);
 bm_status bm_fit_finish(bm_fit_ctx* ctx, float* C_out_dev, int32_t* labels_out_dev,
                         bm_report* report_out);
+/* Counters and phase times so far (no final recheck); f_full and
+ * f_incumbent hold the incumbent's full objective when
+ * eval_full_each_round is set, else 0 and +inf. */
+bm_status bm_fit_report(bm_fit_ctx* ctx, bm_report* report_out);
 void bm_fit_destroy(bm_fit_ctx* ctx);
 
 /* ---------------------------------------------------------------------------

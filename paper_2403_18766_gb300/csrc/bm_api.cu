@@ -16,11 +16,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "../../include/bigmeans.h"
 #include "bm_device.cuh"
+#include "bm_sample.cuh"
 #include "bm_worker.cuh"
 
 namespace bm {
@@ -116,6 +118,39 @@ long long draw_cap(long long m, long long s) {
     return (long long)std::ceil(cap);
 }
 
+// CTAs per worker cluster: about kRowsPerCta sample rows per CTA, at most
+// max_cs, and never more than kMaxRowsPerCta rows per CTA (0 = impossible).
+int cluster_size(long long s_cap, int max_cs) {
+    long long cs = std::max<long long>(1, (s_cap + kRowsPerCta - 1) / kRowsPerCta);
+    cs = std::min<long long>(cs, max_cs);
+    while (cs < max_cs && (s_cap + cs - 1) / cs > kMaxRowsPerCta) ++cs;
+    if ((s_cap + cs - 1) / cs > kMaxRowsPerCta) return 0;
+    return (int)cs;
+}
+
+// Host copy of the library's sample-size draw (same Philox4x64-10 and Lemire
+// rule as the device code), used to size each worker's cluster.
+uint64_t host_draw_below(uint64_t seed, uint64_t k1, uint64_t c0, uint64_t c1, uint64_t bound) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = c0, x1 = c1, x2 = 0, x3 = 0, k0 = seed, kk1 = k1;
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; kk1 += W1; }
+        const unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        const uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ kk1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+    }
+    const uint64_t w[4] = {x0, x1, x2, x3};
+    const uint64_t thr = (0ull - bound) % bound;
+    for (int i = 0; i < 4; ++i) {
+        const unsigned __int128 p = (unsigned __int128)w[i] * bound;
+        if ((uint64_t)p >= thr) return (uint64_t)(p >> 64);
+    }
+    return (uint64_t)(((unsigned __int128)w[3] * bound) >> 64);
+}
+
 long long next_pow2(long long v) {
     long long p = 1;
     while (p < v) p <<= 1;
@@ -141,11 +176,24 @@ struct bm_fit_ctx {
     // device buffers
     void* base = nullptr;
     Globals* glob = nullptr;
+    int jobs = 0;                           // sample jobs per round: W * (P + 1)
+    unsigned int gen = 1;                   // next sampler-table generation
     float* S = nullptr; long long* idx = nullptr; unsigned int* draws = nullptr;
-    unsigned int* hkey = nullptr; unsigned int* htmin = nullptr; float* D2 = nullptr;
+    unsigned long long* table = nullptr; int* job_s = nullptr; float* D2 = nullptr;
     float* Cw = nullptr; float* Cw_cta = nullptr; unsigned char* deg = nullptr;
     double* fhat = nullptr; double* f_final = nullptr; long long* L_buf = nullptr;
     unsigned long long* timer = nullptr;
+    int max_cs = 8;
+    std::vector<cudaStream_t> wst;          // worker streams (fork/join with st)
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    // phase timing: event pairs around each launch, summed when the stream syncs
+    struct Span { cudaEvent_t a, b; int kind; };
+    std::vector<Span> spans;
+    std::vector<cudaEvent_t> pool;
+    double t_worker = 0, t_full = 0;
+    long long n_worker = 0, n_full = 0;
+    long long n_kernels = 0;                // kernels of this library launched so far
 };
 
 namespace {
@@ -161,10 +209,7 @@ WorkerArgs make_args(const bm_fit_ctx* c, int mode) {
     a.max_lloyd = c->bud.max_lloyd; a.trials = c->bud.kpp_candidates; a.tol = c->bud.tol;
     a.seed = c->seed;
     a.mode = mode; a.cs = c->cs; a.glob = c->glob;
-    a.S = c->S; a.S_stride = c->s_cap * c->np;
-    a.idx = c->idx; a.idx_stride = c->s_cap;
-    a.draws = c->draws; a.draws_stride = c->Tcap; a.Tcap = c->Tcap;
-    a.hkey = c->hkey; a.htmin = c->htmin; a.H = c->H; a.hash_stride = c->H;
+    a.S = c->S; a.S_stride = c->s_cap * c->np; a.job_s = c->job_s;
     a.D2 = c->D2; a.D2_stride = c->s_cap;
     a.Cw = c->Cw; a.Cw_cta = c->Cw_cta; a.deg = c->deg; a.fhat = c->fhat;
     a.L_buf = c->L_buf; a.L_cap = c->L_cap; a.f_final = c->f_final;
@@ -172,20 +217,74 @@ WorkerArgs make_args(const bm_fit_ctx* c, int mode) {
     return a;
 }
 
-// Carve one device allocation into the workspace of `W` workers.
+SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs) {
+    SampleArgs a;
+    memset(&a, 0, sizeof a);
+    a.X = c->X; a.m = c->m; a.n = c->n; a.mode = mode; a.seed = c->seed;
+    a.W = c->pol.workers; a.P = c->pol.passes;
+    a.s_min = c->pol.s_min; a.s_max = c->s_hi;
+    for (int i = 0; i < 16; ++i) a.set[i] = c->pol.set[i];
+    a.set_len = c->pol.set_len;
+    a.S = c->S; a.S_stride = c->s_cap * c->np;
+    a.idx = c->idx; a.idx_stride = c->s_cap;
+    a.draws = c->draws; a.draws_stride = c->Tcap; a.Tcap = c->Tcap;
+    a.table = c->table; a.H = c->H; a.table_stride = c->H;
+    a.gen_base = c->gen;
+    c->gen += (unsigned int)jobs;
+    a.job_s = c->job_s; a.glob = c->glob;
+    return a;
+}
+
+cudaEvent_t take_event(bm_fit_ctx* c) {
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+// Record the start of a timed launch; returns the span index.
+size_t span_begin(bm_fit_ctx* c, int kind) {
+    bm_fit_ctx::Span sp{take_event(c), take_event(c), kind};
+    cudaEventRecord(sp.a, c->st);
+    c->spans.push_back(sp);
+    return c->spans.size() - 1;
+}
+void span_end(bm_fit_ctx* c, size_t i) { cudaEventRecord(c->spans[i].b, c->st); }
+// After a stream sync: fold the finished spans into the phase totals.
+void collect_spans(bm_fit_ctx* c) {
+    for (auto& sp : c->spans) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+            if (sp.kind == 0) { c->t_worker += ms * 1e-3; c->n_worker++; }
+            else { c->t_full += ms * 1e-3; c->n_full++; }
+        }
+        c->pool.push_back(sp.a);
+        c->pool.push_back(sp.b);
+    }
+    c->spans.clear();
+}
+
+// Carve one device allocation into the workspace: per sample job (W * (P+1)
+// per round) the padded sample, its indices, draws and sampler table; per
+// worker the K-means++ D^2, centroids and state.
 bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const long long k = c->k, np = c->np;
+    const long long J = (long long)W * (c->pol.passes + 1);
+    c->jobs = (int)J;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
     const size_t o_glob = take(sizeof(Globals));
-    const size_t o_S = take((size_t)W * c->s_cap * np * 4);
-    const size_t o_idx = take((size_t)W * c->s_cap * 8);
-    const size_t o_draws = take((size_t)W * c->Tcap * 4);
-    const size_t o_hkey = take((size_t)W * c->H * 4);
-    const size_t o_htmin = take((size_t)W * c->H * 4);
+    const size_t o_S = take((size_t)J * c->s_cap * np * 4);
+    const size_t o_idx = take((size_t)J * c->s_cap * 8);
+    const size_t o_draws = take((size_t)J * c->Tcap * 4);
+    const size_t o_tab = take((size_t)J * c->H * 8);
+    const size_t o_js = take((size_t)J * 4);
     const size_t o_D2 = take((size_t)W * c->s_cap * 4);
     const size_t o_Cw = take((size_t)W * k * np * 4);
-    const size_t o_Cwc = take((size_t)W * c->cs * k * np * 4);
+    const size_t o_Cwc = take((size_t)W * kMaxCluster * k * np * 4);
     const size_t o_deg = take((size_t)W * k);
     const size_t o_fhat = take((size_t)W * 8);
     const size_t o_ff = take((size_t)W * 8);
@@ -194,18 +293,20 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     cudaError_t e = cudaMallocAsync(&c->base, off, c->st);
     if (e != cudaSuccess) {
         c->base = nullptr;
+        cudaGetLastError();
         return fail(BM_ENOMEM, "workspace of %zu bytes: %s", off, cudaGetErrorString(e));
     }
     char* b = (char*)c->base;
     c->glob = (Globals*)(b + o_glob);
     c->S = (float*)(b + o_S); c->idx = (long long*)(b + o_idx); c->draws = (unsigned int*)(b + o_draws);
-    c->hkey = (unsigned int*)(b + o_hkey); c->htmin = (unsigned int*)(b + o_htmin);
+    c->table = (unsigned long long*)(b + o_tab); c->job_s = (int*)(b + o_js);
     c->D2 = (float*)(b + o_D2); c->Cw = (float*)(b + o_Cw); c->Cw_cta = (float*)(b + o_Cwc);
     c->deg = (unsigned char*)(b + o_deg); c->fhat = (double*)(b + o_fhat); c->f_final = (double*)(b + o_ff);
     c->L_buf = (long long*)(b + o_L); c->timer = (unsigned long long*)(b + o_t);
     CU(cudaMemsetAsync(c->glob, 0, sizeof(Globals), c->st));
     CU(cudaMemsetAsync(c->Cw, 0, (size_t)W * k * np * 4, c->st));
-    CU(cudaMemsetAsync(c->S, 0, (size_t)W * c->s_cap * np * 4, c->st));
+    CU(cudaMemsetAsync(c->table, 0, (size_t)J * c->H * 8, c->st));
+    CU(cudaMemsetAsync(c->job_s, 0, (size_t)J * 4, c->st));
     return BM_OK;
 }
 
@@ -230,7 +331,31 @@ bm_status check_shape(long long m, int n, int k) {
 bm_status read_globals(bm_fit_ctx* c, Globals* h) {
     CU(cudaMemcpyAsync(h, c->glob, sizeof(Globals), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
+    collect_spans(c);
     return BM_OK;
+}
+
+void fill_report(const bm_fit_ctx* c, const Globals& h, bm_report* rep) {
+    memset(rep, 0, sizeof *rep);
+    rep->f_full = h.f_full;
+    rep->f_incumbent = std::min(h.f_incumbent, h.f_full);
+    rep->s_opt = h.s_opt;
+    rep->best_worker = h.best_worker;
+    rep->rounds_done = c->rounds_run;
+    rep->passes_done = (int64_t)h.passes;
+    rep->lloyd_iters = (int64_t)h.lloyd_iters;
+    rep->assign_rows = (int64_t)h.assign_rows;
+    rep->accepts = (int64_t)h.accepts;
+    rep->L_sum = (int64_t)h.L_sum;
+    rep->rescored_rows = (int64_t)h.rescored;
+    rep->inexact_terms = (int64_t)h.inexact;
+    rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
+    rep->t_worker_s = c->t_worker;
+    rep->t_fullpass_s = c->t_full;
+    rep->kernel_launches = c->n_kernels;
+    rep->fullpass_launches = c->n_full;
+    rep->reseeded = (int64_t)h.reseeded;
+    for (int i = 0; i < 8; ++i) rep->trace_cycles[i] = (int64_t)h.trace[i];
 }
 
 bm_status status_from_flags(const Globals& h) {
@@ -245,21 +370,71 @@ bm_status status_from_flags(const Globals& h) {
     return BM_OK;
 }
 
+long long size_of(const bm_fit_ctx* c, int w, int t) {
+    const uint64_t k1 = stream_k1(kPurposeSize, w, t, 0);
+    if (c->pol.set_len > 0) return c->pol.set[host_draw_below(c->seed, k1, 0, 0, (uint64_t)c->pol.set_len)];
+    return c->pol.s_min + (long long)host_draw_below(c->seed, k1, 0, 0, (uint64_t)(c->s_hi - c->pol.s_min + 1));
+}
+
+bm_status ensure_streams(bm_fit_ctx* c) {
+    if (!c->wst.empty()) return BM_OK;
+    const int ns = std::min(c->pol.workers, 16);
+    CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    for (int i = 0; i < ns; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        c->wst.push_back(s);
+        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        c->ev_join.push_back(e);
+    }
+    return BM_OK;
+}
+
+// Rounds [r0, r1) for every worker: one launch per worker on the worker
+// streams, each with a cluster sized for that worker's largest s_w, so the
+// rows per CTA (and the time per Lloyd iteration) stay balanced.
 bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
-    WorkerArgs a = make_args(c, kModeRounds);
-    a.round_begin = r0;
-    a.round_end = r1;
-    a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
+    bm_status s;
+    if ((s = ensure_streams(c))) return s;
+    if (r1 != r0 + 1) return fail(BM_EINTERNAL, "one round per launch");
     const int big = 0x7fffffff;
     CU(cudaMemcpyAsync(&c->glob->rounds_done, &big, sizeof(int), cudaMemcpyHostToDevice, c->st));
-    CU(launch_worker(c->np, a, c->pol.workers, c->st));
+    const size_t sp = span_begin(c, 0);
+    SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs);
+    sa.rnd = r0;
+    CU(launch_sample(c->np, sa, c->jobs, c->st));
+    c->n_kernels++;
+    CU(cudaEventRecord(c->ev_fork, c->st));
+    const int ns = (int)c->wst.size();
+    for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(c->wst[i], c->ev_fork, 0));
+    for (int w = 0; w < c->pol.workers; ++w) {
+        long long smax = 0;
+        for (int t = r0; t < r1; ++t) smax = std::max(smax, size_of(c, w, t));
+        WorkerArgs a = make_args(c, kModeRounds);
+        a.round_begin = r0;
+        a.round_end = r1;
+        a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
+        a.worker_base = w;
+        a.cs = cluster_size(smax, c->max_cs);
+        CU(launch_worker(c->np, a, 1, c->wst[w % ns]));
+        c->n_kernels++;
+    }
+    for (int i = 0; i < ns; ++i) {
+        CU(cudaEventRecord(c->ev_join[i], c->wst[i]));
+        CU(cudaStreamWaitEvent(c->st, c->ev_join[i], 0));
+    }
+    span_end(c, sp);
     return BM_OK;
 }
 
 bm_status run_fullpass(bm_fit_ctx* c, const double* sel, int* labels, int incumbent) {
     const int grid = sm_count();
+    const size_t sp = span_begin(c, 1);
     CU(launch_fullpass(c->np, c->X, c->m, c->n, c->Cw, c->k, sel, c->pol.workers, labels, c->glob, c->gB,
                        c->gp2, incumbent, grid, c->st));
+    c->n_kernels++;
+    span_end(c, sp);
     return BM_OK;
 }
 
@@ -312,7 +487,12 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, con
     c->X = X_dev; c->m = m; c->n = n; c->k = k; c->np = padded_dim(n);
     c->pol = pol; c->bud = bud; c->seed = seed;
     c->s_lo = s_lo; c->s_hi = s_hi; c->s_cap = s_hi;
-    c->cs = (int)std::min<long long>(8, std::max<long long>(1, (s_hi + kRowsPerCta - 1) / kRowsPerCta));
+    c->max_cs = worker_max_cluster(c->np, k);
+    c->cs = cluster_size(s_hi, c->max_cs);
+    if (c->cs == 0) {
+        delete c;
+        return fail(BM_EINVAL, "s_max = %lld above %lld", s_hi, (long long)c->max_cs * kMaxRowsPerCta);
+    }
     c->Tcap = draw_cap(m, s_hi);
     if (c->Tcap >= (1ll << 32) - 1) { delete c; return fail(BM_EINVAL, "sample size too close to m"); }
     c->H = next_pow2(2 * c->Tcap);
@@ -345,22 +525,19 @@ bm_status bm_fit_rounds(bm_fit_ctx* c, int32_t rounds) {
     if (rounds < 0) return fail(BM_EINVAL, "rounds < 0");
     if (rounds == 0) return BM_OK;
     bm_status s;
-    const bool per_round = c->bud.eval_full_each_round || c->bud.seconds > 0;
-    if (!per_round) {
-        if ((s = run_round_launch(c, c->rounds_run, c->rounds_run + rounds))) return s;
-        c->rounds_run += rounds;
-    } else {
-        for (int r = 0; r < rounds; ++r) {
-            if (c->bud.seconds > 0) {
-                const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
-                if (el >= c->bud.seconds) break;
-            }
-            if ((s = run_round_launch(c, c->rounds_run, c->rounds_run + 1))) return s;
-            c->rounds_run += 1;
-            if (c->bud.eval_full_each_round)
-                if ((s = run_fullpass(c, c->fhat, nullptr, 1))) return s;
-            if (c->bud.seconds > 0) CU(cudaStreamSynchronize(c->st));
+    // one sampling launch plus one launch per worker for every round; with a
+    // wall-clock budget the host checks the clock between rounds and the
+    // kernels check it between passes
+    for (int r = 0; r < rounds; ++r) {
+        if (c->bud.seconds > 0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
+            if (el >= c->bud.seconds) break;
         }
+        if ((s = run_round_launch(c, c->rounds_run, c->rounds_run + 1))) return s;
+        c->rounds_run += 1;
+        if (c->bud.eval_full_each_round)
+            if ((s = run_fullpass(c, c->fhat, nullptr, 1))) return s;
+        if (c->bud.seconds > 0) CU(cudaStreamSynchronize(c->st));
     }
     Globals h;
     if ((s = read_globals(c, &h))) return s;
@@ -372,29 +549,29 @@ bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev
     bm_status s = check_ptr(C_out_dev, "C_out_dev");
     if (s) return s;
     WorkerArgs a = make_args(c, kModeFinalEval);
+    const size_t sp = span_begin(c, 0);
+    SampleArgs sa = make_sample_args(c, kSampleFinal, 1);
+    CU(launch_sample(c->np, sa, 1, c->st));
     CU(launch_worker(c->np, a, c->pol.workers, c->st));
+    c->n_kernels += 2;
+    span_end(c, sp);
     if ((s = run_fullpass(c, c->f_final, labels_out_dev, 1))) return s;
     CU(launch_select_unpad(c->Cw, c->f_final, c->pol.workers, c->k, c->n, c->np, C_out_dev, c->st));
     Globals h;
     if ((s = read_globals(c, &h))) return s;
     if ((s = status_from_flags(h))) return s;
-    if (rep) {
-        memset(rep, 0, sizeof *rep);
-        rep->f_full = h.f_full;
-        rep->f_incumbent = std::min(h.f_incumbent, h.f_full);
-        rep->s_opt = h.s_opt;
-        rep->best_worker = h.best_worker;
-        rep->rounds_done = c->rounds_run;
-        rep->passes_done = (int64_t)h.passes;
-        rep->lloyd_iters = (int64_t)h.lloyd_iters;
-        rep->assign_rows = (int64_t)h.assign_rows;
-        rep->accepts = (int64_t)h.accepts;
-        rep->L_sum = (int64_t)h.L_sum;
-        rep->rescored_rows = (int64_t)h.rescored;
-        rep->inexact_terms = (int64_t)h.inexact;
-        rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - c->t0).count();
-    }
+    if (rep) fill_report(c, h, rep);
     return BM_OK;
+}
+
+bm_status bm_fit_report(bm_fit_ctx* c, bm_report* rep) {
+    if (!c || !rep) return fail(BM_EINVAL, "ctx and report are required");
+    Globals h;
+    bm_status s = read_globals(c, &h);
+    if (s) return s;
+    fill_report(c, h, rep);
+    if (!c->bud.eval_full_each_round) { rep->f_full = 0.0; rep->f_incumbent = INFINITY; }
+    return status_from_flags(h);
 }
 
 void bm_fit_destroy(bm_fit_ctx* c) {
@@ -403,6 +580,11 @@ void bm_fit_destroy(bm_fit_ctx* c) {
         cudaFreeAsync(c->base, c->st);
         cudaStreamSynchronize(c->st);
     }
+    collect_spans(c);
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    for (cudaStream_t s : c->wst) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->ev_join) cudaEventDestroy(e);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
 }
 
@@ -469,7 +651,10 @@ static bm_status step_ctx(bm_fit_ctx* c, const float* X, long long m, int n, int
     c->bud.rounds = 1; c->bud.max_lloyd = 300; c->bud.tol = 1e-4; c->bud.kpp_candidates = 3;
     c->seed = seed;
     c->s_lo = c->s_hi = c->s_cap = std::max<long long>(s_cap, 1);
-    c->cs = (int)std::min<long long>(8, std::max<long long>(1, (c->s_cap + kRowsPerCta - 1) / kRowsPerCta));
+    c->max_cs = worker_max_cluster(c->np, k);
+    c->cs = cluster_size(c->s_cap, c->max_cs);
+    if (c->cs == 0)
+        return fail(BM_EINVAL, "sample of %lld rows above %lld", c->s_cap, (long long)c->max_cs * kMaxRowsPerCta);
     c->Tcap = m > 0 ? draw_cap(m, std::min<long long>(c->s_cap, m)) : 1024;
     c->H = next_pow2(2 * c->Tcap);
     c->L_cap = 1;
@@ -494,10 +679,10 @@ bm_status bm_sample(uint64_t seed, int32_t purpose, int32_t worker, int32_t roun
     CtxGuard guard{c};
     bm_status st = step_ctx(c, nullptr, m, 1, 1, s, seed, stream);
     if (st) return st;
-    WorkerArgs a = make_args(c, kModeStepSample);
+    SampleArgs a = make_sample_args(c, kSampleStep, 1);
     a.idx = reinterpret_cast<long long*>(idx_out_dev); a.idx_stride = 0;
-    a.step_s = s; a.step_purpose = purpose; a.step_worker = worker; a.step_round = round; a.step_pass = pass;
-    CU(launch_worker(c->np, a, 1, c->st));
+    a.step_s = s; a.purpose = purpose; a.worker = worker; a.rnd = round; a.pss = pass;
+    CU(launch_sample(c->np, a, 1, c->st));
     Globals h;
     if ((st = read_globals(c, &h))) return st;
     return status_from_flags(h);
@@ -513,11 +698,11 @@ bm_status bm_gather(const float* X_dev, int64_t m, int32_t n, const int64_t* idx
     bm_fit_ctx* c = new bm_fit_ctx();
     CtxGuard guard{c};
     if ((st = step_ctx(c, X_dev, m, n, 1, s, 0, stream))) return st;
-    WorkerArgs a = make_args(c, kModeStepGather);
+    SampleArgs a = make_sample_args(c, kSampleGather, 1);
     a.idx = const_cast<long long*>(reinterpret_cast<const long long*>(idx_dev));
     a.idx_stride = 0;
     a.step_s = s;
-    CU(launch_worker(c->np, a, 1, c->st));
+    CU(launch_sample(c->np, a, 1, c->st));
     CU(launch_unpad(c->S, s, n, c->np, S_out_dev, c->st));
     Globals h;
     if ((st = read_globals(c, &h))) return st;

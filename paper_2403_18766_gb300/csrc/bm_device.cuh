@@ -18,6 +18,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kThreads = 512;          // threads per CTA of every kernel here
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxCluster = 16;        // CTAs per worker cluster (non-portable above 8)
 
 // ------------------------------------------------------------------ globals
 // Per-call device state written by the kernels and read back by the host.
@@ -27,7 +28,12 @@ struct Globals {
     unsigned int err;                  // error flags (kErr*)
     unsigned int done_ctas;            // last-CTA-done counter (full pass)
     unsigned long long lloyd_iters, assign_rows, passes, rescored, inexact;
-    unsigned long long accepts, L_sum, eval_rows;
+    unsigned long long accepts, L_sum, eval_rows, reseeded;
+    // device phase trace (SM cycles on rank 0 of each worker cluster):
+    // 0 K-means++, 1 Lloyd assignment, 2 Lloyd exchange (barriers, DSMEM
+    // reduction, centroid update), 3 f_hat recompute, 4 sum of worker kernel
+    // times, 5 longest worker kernel, 6 Lloyd assignments, 7 worker kernels
+    unsigned long long trace[8];
     unsigned long long obj_words[4];   // full-pass objective, 32-bit chunks
     double f_full;                     // last full-pass objective
     double f_incumbent;                // least full objective seen
@@ -124,9 +130,13 @@ __device__ __forceinline__ void acc_obj(unsigned __int128& acc, float d, int gf,
     }
 }
 
-// Add a signed float to three int64 words of 32-bit chunks (unit 2^gx) with
-// shared-memory atomics.  Returns false if the value exceeded the range.
-__device__ __forceinline__ bool acc_digits(long long* w, float x, int gx, unsigned int& inexact) {
+// Add a signed float to six int32 words of 16-bit chunks (unit 2^gx):
+// value = sum_i w[i] * 2^(16 i).  Native 32-bit shared-memory atomics; a word
+// absorbs up to 2^15 additions, so a CTA adds at most kMaxRowsPerCta rows
+// between flushes.  Returns false if the value exceeded the 96-bit range.
+constexpr int kDigits = 6;
+constexpr long long kMaxRowsPerCta = 32767;
+__device__ __forceinline__ bool acc_digits(int* w, float x, int gx, unsigned int& inexact) {
     const uint32_t bits = __float_as_uint(x);
     const uint32_t mag = bits & 0x7fffffffu;
     if (mag == 0) return true;
@@ -141,13 +151,14 @@ __device__ __forceinline__ bool acc_digits(long long* w, float x, int gx, unsign
         sh = 0;
         if (!mant) return true;
     }
-    const int i = sh >> 5, intra = sh & 31;
-    const uint64_t v = (uint64_t)mant << intra;
-    long long lo = (long long)(uint32_t)v, hi = (long long)(v >> 32);
-    if (i > 2 || (i == 2 && hi != 0)) return false;
-    if (bits >> 31) { lo = -lo; hi = -hi; }
-    atomicAdd(reinterpret_cast<unsigned long long*>(&w[i]), (unsigned long long)lo);
-    if (hi) atomicAdd(reinterpret_cast<unsigned long long*>(&w[i + 1]), (unsigned long long)hi);
+    const int i = sh >> 4, intra = sh & 15;
+    const uint64_t v = (uint64_t)mant << intra;                 // < 2^39
+    int c0 = (int)(v & 0xffffu), c1 = (int)((v >> 16) & 0xffffu), c2 = (int)(v >> 32);
+    if (i + (c2 ? 2 : (c1 ? 1 : 0)) >= kDigits) return false;
+    if (bits >> 31) { c0 = -c0; c1 = -c1; c2 = -c2; }
+    if (c0) atomicAdd(&w[i], c0);
+    if (c1) atomicAdd(&w[i + 1], c1);
+    if (c2) atomicAdd(&w[i + 2], c2);
     return true;
 }
 

@@ -1,0 +1,200 @@
+// Sampling and gather (a1, a2) for all workers of a round in one launch.
+//
+// Algorithm 1 draws, for every worker and round, one sample to recompute
+// f_hat_w and one sample per pass (Sec. 4.1: "a new uniformly random sample
+// ... in each iteration").  None of them depends on clustering results, so
+// they are all drawn up front, one CTA per (worker, sample) job, and gathered
+// into contiguous padded rows that the worker kernel then reuses.
+//
+// A sample of size s is the first s distinct values among the bounded draws
+// r_0, r_1, ... of its Philox stream, in order of first occurrence.  Each job
+// inserts its draws into an open-addressing table whose slots hold
+// (generation << 32 | t): the generation of the job marks a slot as used, so
+// the table never needs clearing, and the value of a slot is draws[t].  A
+// draw t is kept when the slot of its value holds t itself (the least t).
+#include <cstdint>
+
+#include "bm_device.cuh"
+#include "bm_sample.cuh"
+
+namespace bm {
+
+__device__ __forceinline__ unsigned int tab_hash(unsigned int r) { return r * 0x9E3779B1u; }
+
+// Insert draw (r, t); the slot keeps the least t of value r.  Returns false
+// only if the bounded retry or probe limits ran out (reported as an error).
+__device__ bool tab_insert(unsigned long long* tab, unsigned int mask, unsigned int gen, unsigned int r,
+                           unsigned int t, const unsigned int* draws) {
+    unsigned int h = tab_hash(r) & mask;
+    const unsigned long long mine = ((unsigned long long)gen << 32) | t;
+    for (unsigned int probe = 0; probe <= mask; ++probe) {
+        unsigned long long cur = atomicAdd(&tab[h], 0ull);
+        bool next = false;
+        for (int spin = 0; spin < 1024 && !next; ++spin) {   // each retry sees a newer slot value
+            if ((unsigned int)(cur >> 32) != gen) {          // free in this generation
+                const unsigned long long prev = atomicCAS(&tab[h], cur, mine);
+                if (prev == cur) return true;
+                cur = prev;
+                continue;
+            }
+            const unsigned int tt = (unsigned int)cur;
+            if (draws[tt] != r) { next = true; break; }      // another value: next slot
+            if (tt <= t) return true;                        // an earlier draw holds it
+            const unsigned long long prev = atomicCAS(&tab[h], cur, mine);
+            if (prev == cur) return true;
+            cur = prev;
+        }
+        if (!next) return false;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
+__device__ bool tab_is_first(const unsigned long long* tab, unsigned int mask, unsigned int gen,
+                             unsigned int r, unsigned int t, const unsigned int* draws) {
+    unsigned int h = tab_hash(r) & mask;
+    for (unsigned int probe = 0; probe <= mask; ++probe) {
+        const unsigned long long cur = tab[h];
+        if ((unsigned int)(cur >> 32) != gen) return false;
+        const unsigned int tt = (unsigned int)cur;
+        if (draws[tt] == r) return tt == t;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ long long pow2_at_least(long long v) {
+    long long p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
+    __shared__ long long red64[kWarps + 1];
+    __shared__ int fail;
+    const int job = blockIdx.x;
+    int purpose = a.purpose, worker = a.worker, rnd = a.rnd, pss = a.pss;
+    long long s = a.step_s;
+    if (a.mode == kSampleRound) {
+        const int slots = a.P + 1;
+        worker = a.worker_base + job / slots;
+        const int q = job % slots;
+        rnd = a.rnd;
+        purpose = (q < a.P) ? kPurposePass : kPurposeEval;
+        pss = (q < a.P) ? q : 0;
+        const unsigned long long k1 = stream_k1(kPurposeSize, worker, rnd, 0);
+        if (a.set_len > 0) s = a.set[draw_below(a.seed, k1, 0, 0, (unsigned long long)a.set_len)];
+        else s = a.s_min + (long long)draw_below(a.seed, k1, 0, 0, (unsigned long long)(a.s_max - a.s_min + 1));
+    } else if (a.mode == kSampleFinal) {
+        long long s_lo = a.s_min, s_hi = a.s_max;
+        if (a.set_len > 0) {
+            s_lo = a.set[0]; s_hi = a.set[0];
+            for (int i = 1; i < a.set_len; ++i) { s_lo = min(s_lo, a.set[i]); s_hi = max(s_hi, a.set[i]); }
+        }
+        const long long acc = (long long)a.glob->accepts, Ls = (long long)a.glob->L_sum;
+        s = s_hi;
+        if (acc > 0) s = min(max((2 * Ls + acc) / (2 * acc), s_lo), s_hi);
+        purpose = kPurposeFinal; worker = 0; rnd = 0; pss = 0;
+        if (threadIdx.x == 0) a.glob->s_opt = (int)s;
+    }
+    long long* idx = a.idx + (long long)job * a.idx_stride;
+    float* S = a.S + (long long)job * a.S_stride;
+    if (a.mode != kSampleGather) {
+        const long long m = a.m;
+        unsigned int* draws = a.draws + (long long)job * a.draws_stride;
+        unsigned long long* tab = a.table + (long long)job * a.table_stride;
+        // table size for this job: small samples need only about 2 s draws
+        const long long H = (2 * s <= m) ? min(a.H, pow2_at_least(4 * s + 2048)) : a.H;
+        const unsigned int mask = (unsigned int)(H - 1);
+        const long long cap = min(a.Tcap, H / 2);
+        const unsigned int gen = a.gen_base + (unsigned int)job;
+        const unsigned long long k1 = stream_k1(purpose, worker, rnd, pss);
+        const unsigned long long thr = lemire_thr((unsigned long long)m);
+        long long T_done = 0, T = min(cap, s + (s * s) / m + 64);
+        if (threadIdx.x == 0) fail = 1;
+        __syncthreads();
+        for (int batch = 0; batch < 64 && s > 0; ++batch) {
+            for (long long t = T_done + threadIdx.x; t < T; t += kThreads) {
+                const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
+                draws[t] = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
+            }
+            __threadfence_block();
+            __syncthreads();
+            bool ok = true;
+            for (long long t = T_done + threadIdx.x; t < T; t += kThreads)
+                ok &= tab_insert(tab, mask, gen, draws[t], (unsigned int)t, draws);
+            if (!ok) atomicOr(&a.glob->err, kErrSample);
+            __threadfence_block();
+            __syncthreads();
+            const long long ch = (T + kThreads - 1) / kThreads;
+            const long long c0 = ch * threadIdx.x, c1 = min(T, c0 + ch);
+            long long mine = 0;
+            for (long long t = c0; t < c1; ++t) mine += tab_is_first(tab, mask, gen, draws[t], (unsigned int)t, draws);
+            long long total;
+            const long long excl = block_exscan(mine, red64, &total);
+            if (total >= s) {
+                long long pos = excl;
+                for (long long t = c0; t < c1 && pos < s; ++t) {
+                    const unsigned int r = draws[t];
+                    if (tab_is_first(tab, mask, gen, r, (unsigned int)t, draws)) idx[pos++] = (long long)r;
+                }
+                if (threadIdx.x == 0) fail = 0;
+                break;
+            }
+            if (T >= cap) break;
+            T_done = T;
+            T = min(cap, 2 * T);
+        }
+        __syncthreads();
+        if (s > 0 && fail) {
+            if (threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
+            s = 0;
+        }
+        __threadfence_block();
+        __syncthreads();
+    }
+    if (a.mode == kSampleStep) {
+        if (threadIdx.x == 0 && a.job_s) a.job_s[job] = (int)s;
+        return;
+    }
+    // gather (padded rows, zeros in the padding)
+    const int n = a.n;
+    const long long items = s * (NP / 4);
+    for (long long e = threadIdx.x; e < items; e += kThreads) {
+        const long long i = e / (NP / 4);
+        const int q = (int)(e % (NP / 4));
+        const long long row = idx[i];
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row >= 0 && row < a.m) {
+            const float* xr = a.X + row * (long long)n;
+            v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
+            v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
+            v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
+            v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+        } else if (q == 0) {
+            atomicOr(&a.glob->err, kErrArgs);
+        }
+        reinterpret_cast<float4*>(S + i * NP)[q] = v;
+    }
+    if (threadIdx.x == 0 && a.job_s) a.job_s[job] = (int)s;
+}
+
+template <int NP>
+static cudaError_t launch_sample_t(const SampleArgs& a, int jobs, cudaStream_t st) {
+    sample_kernel<NP><<<jobs, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample(int np, const SampleArgs& a, int jobs, cudaStream_t st) {
+    switch (np) {
+        case 4: return launch_sample_t<4>(a, jobs, st);
+        case 8: return launch_sample_t<8>(a, jobs, st);
+        case 16: return launch_sample_t<16>(a, jobs, st);
+        case 32: return launch_sample_t<32>(a, jobs, st);
+        case 64: return launch_sample_t<64>(a, jobs, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bm

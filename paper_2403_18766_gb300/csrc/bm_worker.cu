@@ -5,6 +5,19 @@ namespace bm {
 
 template <int NP>
 cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st);
+template <int NP>
+int worker_max_cluster_t(int k);
+
+int worker_max_cluster(int np, int k) {
+    switch (np) {
+        case 4: return worker_max_cluster_t<4>(k);
+        case 8: return worker_max_cluster_t<8>(k);
+        case 16: return worker_max_cluster_t<16>(k);
+        case 32: return worker_max_cluster_t<32>(k);
+        case 64: return worker_max_cluster_t<64>(k);
+    }
+    return 8;
+}
 
 size_t worker_smem(int np, int k) {
     switch (np) {

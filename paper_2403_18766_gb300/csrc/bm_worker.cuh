@@ -9,8 +9,6 @@ namespace bm {
 enum WorkerMode : int {
     kModeRounds = 0,      // Algorithm 1 rounds [round_begin, round_end)
     kModeFinalEval = 1,   // common recheck on the FINAL sample of size s_opt
-    kModeStepSample = 2,  // a1 only
-    kModeStepGather = 3,  // a1 indices given -> a2
     kModeStepKpp = 4,     // a3 on a given sample
     kModeStepLloyd = 5,   // a4-a6 on a given sample
 };
@@ -25,6 +23,7 @@ struct WorkerArgs {
     long long set[16];
     int set_len;
     int W, P;
+    int worker_base;                  // worker index of cluster 0 of this launch
     int max_lloyd, trials;
     double tol;
     unsigned long long seed;
@@ -33,13 +32,10 @@ struct WorkerArgs {
     int mode;
     int cs;                           // CTAs per cluster
     Globals* glob;
-    // per-worker workspace
-    float* S; long long S_stride;                 // s_cap * NP floats
-    long long* idx; long long idx_stride;         // s_cap
-    unsigned int* draws; long long draws_stride;  // Tcap
-    long long Tcap;
-    unsigned int* hkey; unsigned int* htmin; long long H; long long hash_stride;
-    float* D2; long long D2_stride;               // s_cap
+    // samples drawn by the sampling kernel: job (w, slot) = w * (P + 1) + slot
+    float* S; long long S_stride;                 // s_cap * NP floats per job
+    const int* job_s;                             // sample size of each job
+    float* D2; long long D2_stride;               // s_cap per worker (K-means++ D^2)
     // worker state
     float* Cw;               // W * k * NP (canonical, read at launch start)
     float* Cw_cta;           // W * cs * k * NP (per-CTA working copies)
@@ -60,7 +56,6 @@ struct Xch {
     unsigned long long inexact, rescored;
     long long wsum;                    // CTA sum of K-means++ weights
     long long pot[4];                  // CTA partial candidate potentials
-    long long nkeep;                   // CTA count of first-occurrence draws
     unsigned int maxbits;              // CTA max of D^2 bits
     int cand[4];                       // candidate row found by this CTA, -1 if none
     int stop;                          // rank-0 decision broadcast
@@ -70,13 +65,18 @@ struct Xch {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
+// Words per cluster in the shared accumulator: odd, so that lanes adding to
+// the same (dimension, digit) of different clusters fall in different banks.
+template <int NP>
+__host__ __device__ constexpr int acc_stride() { return NP * kDigits + 1; }
+
 template <int NP>
 __host__ __device__ inline size_t worker_smem_bytes(int k) {
     size_t b = 0;
     b += align16((size_t)k * NP * 4);           // Ccur
     b += align16((size_t)k * NP * 4);           // Cnew
     b += align16((size_t)k * 4);                // CC
-    b += align16((size_t)k * NP * 3 * 8);       // ACC
+    b += align16((size_t)k * acc_stride<NP>() * 4);  // ACC
     b += align16((size_t)k * 4);                // cnt
     b += align16((size_t)k) * 3;                // deg, empty, emptyall
     b += align16(sizeof(Xch));
@@ -90,5 +90,6 @@ __host__ __device__ inline size_t worker_smem_bytes(int k) {
 
 cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
 size_t worker_smem(int np, int k);
+int worker_max_cluster(int np, int k);   // 16 if 16-CTA clusters fit, else 8
 
 }  // namespace bm

@@ -3,15 +3,16 @@
 // width NP in bm_worker_np*.cu): one thread-block cluster per competing
 // worker of Algorithm 1 (arXiv 2403.18766, Sec. 4.2-4.3).
 //
-// A worker's sample is split into contiguous row slices, one per CTA of its
-// cluster.  Per pass the cluster draws the sample (a1), gathers it (a2),
-// re-seeds degenerate centroids with greedy K-means++ (a3), runs Lloyd's
-// iterations (a4-a6) and applies the incumbent rule.  Cross-CTA exchange goes
-// through distributed shared memory; every cross-CTA dependency is separated
-// by a hardware cluster barrier (barrier.cluster, no spinning in this code).
-// All control flow that reaches a cluster barrier is cluster-uniform: it only
-// depends on kernel arguments and on values every CTA reads after a barrier
-// from the same place, so all CTAs execute the same sequence of barriers.
+// The samples of a round are drawn and gathered beforehand by the sampling
+// kernel.  A worker's sample is split into contiguous row slices, one per CTA
+// of its cluster.  Per pass the cluster re-seeds degenerate centroids with
+// greedy K-means++ (a3), runs Lloyd's iterations (a4-a6) and applies the
+// incumbent rule.  Cross-CTA exchange goes through distributed shared memory;
+// every cross-CTA dependency is separated by a hardware cluster barrier
+// (barrier.cluster, no spinning in this code).  All control flow that reaches
+// a cluster barrier is cluster-uniform: it only depends on kernel arguments
+// and on values every CTA reads after a barrier from the same place, so all
+// CTAs execute the same sequence of barriers.
 #include <cstdint>
 
 #include "bm_device.cuh"
@@ -24,7 +25,7 @@ struct Sm {
     float* Ccur;          // k * NP  centroids of the current step
     float* Cnew;          // k * NP  owner-computed updates
     float* CC;            // k       fl(||c||^2) FMA chain
-    long long* ACC;       // k * NP * 3 fixed-point coordinate sums
+    int* ACC;             // k * acc_stride fixed-point coordinate sums
     int* cnt;             // k
     unsigned char* deg;   // k       worker's degenerate flags (identical copies)
     unsigned char* empty; // k       owner-computed empties of the last assignment
@@ -46,7 +47,7 @@ __device__ inline Sm<NP> carve(int k) {
     s.Ccur = (float*)p;            p += align16((size_t)k * NP * 4);
     s.Cnew = (float*)p;            p += align16((size_t)k * NP * 4);
     s.CC = (float*)p;              p += align16((size_t)k * 4);
-    s.ACC = (long long*)p;         p += align16((size_t)k * NP * 3 * 8);
+    s.ACC = (int*)p;               p += align16((size_t)k * acc_stride<NP>() * 4);
     s.cnt = (int*)p;               p += align16((size_t)k * 4);
     s.deg = p;                     p += align16((size_t)k);
     s.empty = p;                   p += align16((size_t)k);
@@ -71,27 +72,36 @@ struct Worker {
     Sm<NP> sm;
     int rank, cs, w, k, n;
     Grids g;
-    float* S; long long* idx; unsigned int* draws; unsigned int* hkey; unsigned int* htmin;
+    float* S;               // current sample (padded rows), set per pass
     float* D2; float* Cw_mine;
 
     __device__ Worker(const WorkerArgs& args, cg::cluster_group c) : a(args), cl(c) {
         cs = a.cs;
         rank = (int)cl.block_rank();
-        w = blockIdx.x / cs;
+        w = a.worker_base + blockIdx.x / cs;
         k = a.k;
         n = a.n;
         sm = carve<NP>(k);
         g = grids_from_maxbits(a.glob->maxbits);
-        S = a.S + (long long)w * a.S_stride;
-        idx = a.idx + (long long)w * a.idx_stride;
-        draws = a.draws + (long long)w * a.draws_stride;
-        hkey = a.hkey + (long long)w * a.hash_stride;
-        htmin = a.htmin + (long long)w * a.hash_stride;
+        S = a.S;
         D2 = a.D2 + (long long)w * a.D2_stride;
-        Cw_mine = a.Cw_cta + ((long long)w * cs + rank) * (long long)k * NP;
+        Cw_mine = a.Cw_cta + ((long long)w * kMaxCluster + rank) * (long long)k * NP;
     }
 
     __device__ Xch* rx(int q) { return cl.map_shared_rank(sm.x, q); }
+
+    // Phase trace: rank 0, thread 0 adds elapsed SM cycles to glob->trace[i].
+    __device__ bool tracer() const { return rank == 0 && threadIdx.x == 0; }
+    __device__ void trace_add(int i, long long t0) const {
+        if (tracer()) atomicAdd(&a.glob->trace[i], (unsigned long long)(clock64() - t0));
+    }
+
+    // Sample of job (worker, slot) drawn by the sampling kernel; returns its size.
+    __device__ long long use_sample(int slot) {
+        const long long job = (long long)w * (a.P + 1) + slot;
+        S = a.S + job * a.S_stride;
+        return a.job_s[job];
+    }
 
     __device__ void slice(long long s, long long& lo, long long& hi) const {
         lo = s * rank / cs;
@@ -135,116 +145,6 @@ struct Worker {
         __syncthreads();
     }
 
-    // ------------------------------------------------------------ a1: sample
-    __device__ unsigned int hash_slot(unsigned int r) const {
-        return (unsigned int)((r * 0x9E3779B1u) & (unsigned int)(a.H - 1));
-    }
-    __device__ void hash_insert(unsigned int r, unsigned int t) {
-        const unsigned int key = r + 1u, mask = (unsigned int)(a.H - 1);
-        unsigned int h = hash_slot(r);
-        for (long long probe = 0; probe < a.H; ++probe) {
-            const unsigned int prev = atomicCAS(&hkey[h], 0u, key);
-            if (prev == 0u || prev == key) { atomicMin(&htmin[h], t); return; }
-            h = (h + 1u) & mask;
-        }
-    }
-    __device__ bool is_first(unsigned int r, unsigned int t) const {
-        const unsigned int key = r + 1u, mask = (unsigned int)(a.H - 1);
-        unsigned int h = hash_slot(r);
-        for (long long probe = 0; probe < a.H; ++probe) {
-            const unsigned int kk = hkey[h];
-            if (kk == key) return htmin[h] == t;
-            if (kk == 0u) return false;
-            h = (h + 1u) & mask;
-        }
-        return false;
-    }
-
-    // First s distinct Lemire draws in [0, m) of stream k1, in order of first
-    // occurrence, written to idx[0..s).  Returns false (uniformly) if more
-    // than Tcap draws would be needed.
-    __device__ bool sample(unsigned long long k1, long long s, long long* out) {
-        const long long m = a.m;
-        {
-            const long long per = (a.H + cs - 1) / cs;
-            const long long b0 = per * rank, b1 = min(a.H, b0 + per);
-            for (long long i = b0 + threadIdx.x; i < b1; i += kThreads) { hkey[i] = 0u; htmin[i] = 0xffffffffu; }
-        }
-        csync_global();
-        if (s == 0) return true;
-        const unsigned long long thr = lemire_thr((unsigned long long)m);
-        long long T_done = 0;
-        long long T = min(a.Tcap, s + (s * s) / m + 64);
-        bool ok = false;
-        for (int batch = 0; batch < 64; ++batch) {
-            {   // draws [T_done, T)
-                const long long span = T - T_done;
-                const long long b0 = T_done + span * rank / cs, b1 = T_done + span * (rank + 1) / cs;
-                for (long long t = b0 + threadIdx.x; t < b1; t += kThreads) {
-                    const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
-                    const unsigned int r = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
-                    draws[t] = r;
-                    hash_insert(r, (unsigned int)t);
-                }
-            }
-            csync_global();
-            // first occurrences over [0, T): contiguous chunk per thread
-            const long long b0 = T * rank / cs, b1 = T * (rank + 1) / cs;
-            const long long ch = (b1 - b0 + kThreads - 1) / kThreads;
-            const long long c0 = b0 + ch * threadIdx.x, c1 = min(b1, c0 + ch);
-            long long mine = 0;
-            for (long long t = c0; t < c1; ++t) mine += is_first(draws[t], (unsigned int)t) ? 1 : 0;
-            long long ctaTot;
-            const long long excl = block_exscan(mine, sm.red64, &ctaTot);
-            if (threadIdx.x == 0) sm.x->nkeep = ctaTot;
-            cl.sync();
-            long long base = 0, total = 0;
-            for (int q = 0; q < cs; ++q) {
-                const long long v = rx(q)->nkeep;
-                if (q < rank) base += v;
-                total += v;
-            }
-            if (total >= s) {
-                long long pos = base + excl;
-                for (long long t = c0; t < c1 && pos < s; ++t) {
-                    const unsigned int r = draws[t];
-                    if (is_first(r, (unsigned int)t)) out[pos++] = (long long)r;
-                }
-                ok = true;
-                break;
-            }
-            if (T >= a.Tcap) break;
-            T_done = T;
-            T = min(a.Tcap, 2 * T);
-        }
-        csync_global();
-        return ok;
-    }
-
-    // ------------------------------------------------------------ a2: gather
-    __device__ void gather(long long s, const long long* ix) {
-        long long lo, hi;
-        slice(s, lo, hi);
-        constexpr int Q = NP / 4;
-        const long long items = (hi - lo) * Q;
-        for (long long e = threadIdx.x; e < items; e += kThreads) {
-            const long long i = lo + e / Q;
-            const int q = (int)(e % Q);
-            const long long row = ix[i];
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row >= 0 && row < a.m) {
-                const float* xr = a.X + row * (long long)n;
-                v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
-                v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
-                v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
-                v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
-            } else if (q == 0) {
-                atomicOr(&a.glob->err, kErrArgs);          // index outside [0, m)
-            }
-            reinterpret_cast<float4*>(S + i * NP)[q] = v;
-        }
-    }
-
     // --------------------------------------------- a4/a5: assign + accumulate
     // Assign the CTA's rows against Ccur; accumulate exact sums and counts
     // when `acc` is set; leave the CTA partial objective in sm.x.
@@ -253,7 +153,7 @@ struct Worker {
         long long lo, hi;
         slice(s, lo, hi);
         if (acc) {
-            for (int e = threadIdx.x; e < k * NP * 3; e += kThreads) sm.ACC[e] = 0;
+            for (int e = threadIdx.x; e < k * acc_stride<NP>(); e += kThreads) sm.ACC[e] = 0;
             for (int e = threadIdx.x; e < k; e += kThreads) sm.cnt[e] = 0;
         }
         __syncthreads();
@@ -340,10 +240,10 @@ struct Worker {
                 acc_obj(facc, dv, gf, inex);
                 if (acc) {
                     atomicAdd(&sm.cnt[lab], 1);
-                    long long* wb = sm.ACC + (size_t)lab * NP * 3;
+                    int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
 #pragma unroll
                     for (int d = 0; d < NP; ++d)
-                        if (d < n) ok &= acc_digits(wb + d * 3, x[d], gx, inex);
+                        if (d < n) ok &= acc_digits(wb + d * kDigits, x[d], gx, inex);
                 }
             }
         }
@@ -360,20 +260,26 @@ struct Worker {
         __syncthreads();
     }
 
-    // After a barrier: rank 0 combines the CTA partials into f (exact sum,
-    // rounded once) and records the counters.
-    __device__ double combine_objective() {
+    // After a barrier: warp 0 of rank 0 combines the CTA partials into f
+    // (exact sum, rounded once) and records the counters.  Call from warp 0.
+    __device__ double combine_objective_warp() {
+        const int lane = threadIdx.x & 31;
         unsigned __int128 F = 0;
         unsigned long long I = 0, R = 0;
-        for (int q = 0; q < cs; ++q) {
+        for (int q = lane; q < cs; q += 32) {
             const Xch* p = rx(q);
             F += ((unsigned __int128)p->f_hi << 64) | (unsigned __int128)p->f_lo;
             I += p->inexact;
             R += p->rescored;
         }
-        if (I) atomicAdd(&a.glob->inexact, I);
-        if (R) atomicAdd(&a.glob->rescored, R);
-        return u128_to_double(F, g.gf);
+        F = warp_sum_u128(F);
+        I = warp_sum(I);
+        R = warp_sum(R);
+        if (lane == 0) {
+            if (I) atomicAdd(&a.glob->inexact, I);
+            if (R) atomicAdd(&a.glob->rescored, R);
+        }
+        return u128_to_double(F, g.gf);       // valid in lane 0
     }
 
     // a6 (owner part): new centroid of each owned cluster j (j % cs == rank):
@@ -385,10 +291,12 @@ struct Worker {
             const int d = e % NP;
             long long cntj = 0;
             __int128 V = 0;
+#pragma unroll 4
             for (int q = 0; q < cs; ++q) {
                 cntj += cl.map_shared_rank(sm.cnt, q)[j];
-                const long long* wq = cl.map_shared_rank(sm.ACC, q) + ((size_t)j * NP + d) * 3;
-                V += (__int128)wq[0] + (__int128)wq[1] * ((__int128)1 << 32) + (__int128)wq[2] * ((__int128)1 << 64);
+                const int* wq = cl.map_shared_rank(sm.ACC, q) + (size_t)j * acc_stride<NP>() + d * kDigits;
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i) V += (__int128)wq[i] * ((__int128)1 << (16 * i));
             }
             float c = sm.Ccur[(size_t)j * NP + d];
             if (cntj > 0 && d < n) {
@@ -430,9 +338,12 @@ struct Worker {
     __device__ double eval(long long s) {
         assign_slice(s, false);
         cl.sync();
-        if (rank == 0 && threadIdx.x == 0) {
-            sm.x->fval = combine_objective();
-            sm.x->stop = 1;
+        if (rank == 0 && threadIdx.x < 32) {
+            const double f = combine_objective_warp();
+            if (threadIdx.x == 0) {
+                sm.x->fval = f;
+                sm.x->stop = 1;
+            }
         }
         cl.sync();
         double f; int stop;
@@ -447,11 +358,17 @@ struct Worker {
         double f_prev = 0.0;
         int it = 0;
         for (;;) {
+            const long long t_a = clock64();
             assign_slice(s, true);
+            trace_add(1, t_a);
+            if (tracer()) atomicAdd(&a.glob->trace[6], 1ull);
+            const long long t_x = clock64();
             cl.sync();                                       // partials ready
             owner_update();
+            double fw = 0.0;
+            if (rank == 0 && threadIdx.x < 32) fw = combine_objective_warp();
             if (rank == 0 && threadIdx.x == 0) {
-                const double f = combine_objective();
+                const double f = fw;
                 int stop;
                 if (it == 0) stop = (a.max_lloyd <= 0);
                 else stop = (__dsub_rn(f_prev, f) <= __dmul_rn(a.tol, f_prev)) || (it >= a.max_lloyd);
@@ -463,11 +380,13 @@ struct Worker {
             read_decision(f, stop);
             if (stop) {
                 pull_empty();
+                trace_add(2, t_x);
                 iters = it;
                 return f;
             }
             pull_new_centroids();
             prep_centroids();
+            trace_add(2, t_x);
             f_prev = f;
             ++it;
         }
@@ -625,6 +544,7 @@ struct Worker {
                 }
             }
             // centroid j = S[pick]
+            if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->reseeded, 1ull);
             for (int d = threadIdx.x; d < NP; d += kThreads) sm.Ccur[(size_t)j * NP + d] = S[pick * NP + d];
             __syncthreads();
             mloc = 0;
@@ -650,16 +570,6 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
     if (a.glob->nonfinite) return;            // uniform: read before any barrier
     const int w = W.w;
 
-    if (a.mode == kModeStepSample) {
-        W.sample(stream_k1(a.step_purpose, a.step_worker, a.step_round, a.step_pass), a.step_s, a.idx);
-        W.cl.sync();
-        return;
-    }
-    if (a.mode == kModeStepGather) {
-        W.gather(a.step_s, a.idx);
-        W.csync_global();
-        return;
-    }
     if (a.mode == kModeStepKpp || a.mode == kModeStepLloyd) {
         // S (padded) and C (padded, in a.Cw) were staged by the host.
         W.load_centroids(a.Cw);
@@ -682,6 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
     }
 
     // worker state for this launch
+    const long long t_kernel = clock64();
     for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = a.deg[(long long)w * W.k + j];
     for (int e = threadIdx.x; e < W.k * NP; e += kThreads)
         W.Cw_mine[e] = a.Cw[(long long)w * W.k * NP + e];
@@ -689,23 +600,9 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
     double fhat = a.fhat[w];
 
     if (a.mode == kModeFinalEval) {
-        long long s_lo = a.s_min, s_hi = a.s_max;
-        if (a.set_len > 0) {
-            s_lo = a.set[0]; s_hi = a.set[0];
-            for (int i = 1; i < a.set_len; ++i) { s_lo = min(s_lo, a.set[i]); s_hi = max(s_hi, a.set[i]); }
-        }
-        const long long acc = (long long)a.glob->accepts, Ls = (long long)a.glob->L_sum;
-        long long s_opt = s_hi;
-        if (acc > 0) s_opt = min(max((2 * Ls + acc) / (2 * acc), s_lo), s_hi);
-        if (w == 0 && W.rank == 0 && threadIdx.x == 0) a.glob->s_opt = (int)s_opt;
-        const bool ok = W.sample(stream_k1(kPurposeFinal, 0, 0, 0), s_opt, W.idx);
-        if (!ok) {
-            if (threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
-            W.cl.sync();
-            return;
-        }
-        W.gather(s_opt, W.idx);
-        __syncthreads();
+        // the common sample S (job 0 of the final sampling launch)
+        W.S = a.S;
+        const long long s_opt = a.job_s[0];
         W.load_centroids(W.Cw_mine);
         W.prep_centroids();
         const double f = W.eval(s_opt);
@@ -714,25 +611,22 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
         return;
     }
 
-    // ---------------------------------------------------- Algorithm 1 rounds
+    // ---------------------------------------------------- Algorithm 1 round
+    // Samples of this round were drawn and gathered by the sampling kernel:
+    // slots 0..P-1 are the passes, slot P the f_hat recompute sample.
     bool failed = false, out_of_time = false;
     int rounds_completed = 0;
     for (int t = a.round_begin; t < a.round_end && !failed && !out_of_time; ++t) {
-        long long s_w;
-        {
-            const unsigned long long k1 = stream_k1(kPurposeSize, w, t, 0);
-            if (a.set_len > 0) s_w = a.set[draw_below(a.seed, k1, 0, 0, (unsigned long long)a.set_len)];
-            else s_w = a.s_min + (long long)draw_below(a.seed, k1, 0, 0, (unsigned long long)(a.s_max - a.s_min + 1));
-        }
+        const long long s_w = W.use_sample(a.P);
+        if (s_w <= 0) { failed = true; break; }
         bool all_deg = true;
         for (int j = 0; j < W.k; ++j) all_deg &= (W.sm.deg[j] != 0);
         if (!all_deg) {                                  // recompute f_hat_w with the new s_w
-            if (!W.sample(stream_k1(kPurposeEval, w, t, 0), s_w, W.idx)) { failed = true; break; }
-            W.gather(s_w, W.idx);
-            __syncthreads();
+            const long long t_e = clock64();
             W.load_centroids(W.Cw_mine);
             W.prep_centroids();
             fhat = W.eval(s_w);
+            W.trace_add(3, t_e);
         }
         for (int p = 0; p < a.P; ++p) {
             if (a.deadline_ns) {
@@ -748,15 +642,15 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
                 W.cl.sync();
                 if (late) { out_of_time = true; break; }
             }
-            if (!W.sample(stream_k1(kPurposePass, w, t, p), s_w, W.idx)) { failed = true; break; }
-            W.gather(s_w, W.idx);
-            W.csync_global();                            // whole sample visible to the cluster
+            W.use_sample(p);
             W.load_centroids(W.Cw_mine);
             bool any_deg = false;
             for (int j = 0; j < W.k; ++j) any_deg |= (W.sm.deg[j] != 0);
             if (any_deg) {
+                const long long t_k = clock64();
                 W.kmeanspp(s_w, stream_k1(kPurposeKpp, w, t, p));
                 W.store_centroids(W.Cw_mine);            // re-seeding is in place (Alg. 1)
+                W.trace_add(0, t_k);
             }
             W.prep_centroids();
             int iters = 0;
@@ -789,9 +683,40 @@ __global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a)
         if (threadIdx.x == 0) {
             a.fhat[w] = fhat;
             atomicMin(&a.glob->rounds_done, a.round_begin + rounds_completed);
+            const unsigned long long dt = (unsigned long long)(clock64() - t_kernel);
+            atomicAdd(&a.glob->trace[4], dt);
+            atomicMax(&a.glob->trace[5], dt);
+            atomicAdd(&a.glob->trace[7], 1ull);
         }
     }
     W.csync_global();
+}
+
+template <int NP>
+int worker_max_cluster_t(int k) {
+    const size_t smem = worker_smem_bytes<NP>(k);
+    if (cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, worker_kernel<NP>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 8;
+    }
+    return nclusters > 0 ? 16 : 8;
 }
 
 template <int NP>

@@ -39,10 +39,15 @@ class Report(ctypes.Structure):
                 ("lloyd_iters", ctypes.c_int64), ("assign_rows", ctypes.c_int64),
                 ("accepts", ctypes.c_int64), ("L_sum", ctypes.c_int64),
                 ("rescored_rows", ctypes.c_int64), ("inexact_terms", ctypes.c_int64),
-                ("t_total_s", ctypes.c_double)]
+                ("t_total_s", ctypes.c_double), ("t_worker_s", ctypes.c_double),
+                ("t_fullpass_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("fullpass_launches", ctypes.c_int64), ("reseeded", ctypes.c_int64),
+                ("trace_cycles", ctypes.c_int64 * 8)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["trace_cycles"] = list(d["trace_cycles"])
+        return d
 
 
 class BigmeansError(RuntimeError):
@@ -68,6 +73,7 @@ SIGNATURES = {
     "bm_fit_rounds": (_i32, [_p, _i32]),
     "bm_fit_finish": (_i32, [_p, _p, _p, _RP]),
     "bm_fit_destroy": (None, [_p]),
+    "bm_fit_report": (_i32, [_p, _RP]),
     "bm_sample": (_i32, [_u64, _i32, _i32, _i32, _i32, _i64, _i64, _p, _p]),
     "bm_gather": (_i32, [_p, _i64, _i32, _p, _i64, _p, _p]),
     "bm_kmeanspp": (_i32, [_p, _i64, _i32, _p, _i32, _p, _i32, _u64, _i32, _i32, _i32, _p]),
@@ -178,6 +184,11 @@ class FitSession:
         rep = Report()
         _check(lib.bm_fit_finish(self.ctx, _ptr(C), _ptr(Y), ctypes.byref(rep)))
         return C, Y, rep.as_dict()
+
+    def report(self):
+        rep = Report()
+        _check(lib.bm_fit_report(self.ctx, ctypes.byref(rep)))
+        return rep.as_dict()
 
     def close(self):
         if self.ctx:
