@@ -213,6 +213,33 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
                     int32_t k, int32_t* labels_out_dev, double* f_out_host,
                     bm_report* report_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * bm_assign_noalloc -- the full-data pass of bm_assign (labels of every row of
+ * X and f(C, X), same numeric definition, same results) without allocating
+ * any device memory.  The paper has no counterpart: this is a deployment
+ * aid.  It is for callers that cannot allocate device memory when they need
+ * the assignment, e.g. services that reserve all of their device memory in
+ * their own pool at start-up, or loops with a fixed memory budget in which an
+ * allocation could fail or wait for the device at an unpredictable moment.
+ *   - Scratch: a fixed array of 65,792 bytes inside the library (a 256-byte
+ *     accumulator record plus 16,384 floats of padded centroids).  Every GPU
+ *     that loads the library holds it until the process exits.
+ *   - Limit: k * round_up(n) <= 16,384, where round_up(n) is n rounded up to
+ *     4, 8, 16, 32 or 64; larger sizes are rejected with BM_EINVAL (use
+ *     bm_assign).  Other limits and arguments are those of bm_assign; the
+ *     report is omitted.
+ *   - The first call on each device looks up the scratch's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the one scratch array and each call clears its
+ *     accumulators first, so calls that overlap on the GPU (different
+ *     streams or threads without ordering) race: order them, e.g. issue them
+ *     on one stream.  The call returns after its work has completed.
+ * ------------------------------------------------------------------------- */
+bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const float* C_dev,
+                            int32_t k, int32_t* labels_out_dev, double* f_out_host,
+                            void* stream);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char* bm_last_error(void);
 

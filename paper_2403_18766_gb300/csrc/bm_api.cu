@@ -45,8 +45,19 @@ cudaError_t launch_globaltimer(unsigned long long* out, cudaStream_t st);
 using namespace bm;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace bm {
+// Record the thread-local message returned by bm_last_error (for other
+// translation units of the library).
+bm_status set_error(bm_status s, const char* msg) {
+    g_err = msg;
+    return s;
+}
+}  // namespace bm
+
+namespace {
 
 bm_status fail(bm_status s, const char* fmt, ...) {
     char buf[512];

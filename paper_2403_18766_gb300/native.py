@@ -80,6 +80,7 @@ SIGNATURES = {
     "bm_lloyd": (_i32, [_p, _i64, _i32, _p, _i32, _i32, _dbl, ctypes.POINTER(_dbl),
                         ctypes.POINTER(_i32), _p, _p]),
     "bm_assign": (_i32, [_p, _i64, _i32, _p, _i32, _p, ctypes.POINTER(_dbl), _RP, _p]),
+    "bm_assign_noalloc": (_i32, [_p, _i64, _i32, _p, _i32, _p, ctypes.POINTER(_dbl), _p]),
     "bm_last_error": (ctypes.c_char_p, []),
     "bm_version": (ctypes.c_char_p, []),
 }
@@ -243,6 +244,18 @@ def assign(X, C, labels=True, stream=None):
     _check(lib.bm_assign(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(Y),
                          ctypes.byref(f), ctypes.byref(rep), _stream(stream)))
     return Y, f.value, rep.as_dict()
+
+
+def assign_noalloc(X, C, labels=True, stream=None):
+    """bm_assign_noalloc: the full-data pass using the library's fixed scratch
+    (no device allocation inside the call); calls must not overlap on the GPU."""
+    X = _dev_f32(X, "X")
+    C = _dev_f32(C, "C")
+    Y = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) if labels else None
+    f = ctypes.c_double(0)
+    _check(lib.bm_assign_noalloc(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(Y),
+                                 ctypes.byref(f), _stream(stream)))
+    return Y, f.value
 
 
 def version():

@@ -1,0 +1,46 @@
+"""bm_assign_noalloc against bm_assign, through the C ABI.
+
+bm_assign_noalloc serves callers that cannot allocate device memory when
+they need a full-data assignment (for instance services that keep all of
+their device memory in their own pool).  It keeps its scratch in a fixed
+array inside the library, so two calls in a row must each start from cleared
+accumulators and reproduce bm_assign exactly.  This file is collected last so
+that a run stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2403_18766_gb300 import native  # noqa: E402
+from paper_2403_18766_gb300.synthetic import gaussian_mixture  # noqa: E402
+
+
+def _case(m, n, k, seed):
+    X = gaussian_mixture(m, n, max(2, k // 2), seed=seed)
+    C = X[np.random.default_rng(seed).integers(0, m, k)].copy()
+    return torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+
+
+def test_noalloc_matches_bm_assign_two_calls_in_a_row():
+    cases = [_case(100_003, 16, 25, 1), _case(40_000, 33, 40, 2)]
+    for _ in range(2):                          # the scratch keeps the previous call's contents
+        for X, C in cases:
+            Y_ref, f_ref, _ = native.assign(X, C)
+            Y, f = native.assign_noalloc(X, C)
+            torch.cuda.synchronize()
+            assert torch.equal(Y, Y_ref)
+            assert f == f_ref                  # exact objective: bit-identical doubles
+
+
+def test_noalloc_rejects_sizes_above_its_scratch():
+    X, _ = _case(1000, 64, 2, 3)
+    C = X[:300].clone()                        # 300 * 64 floats > 16,384
+    with pytest.raises(native.BigmeansError) as e:
+        native.assign_noalloc(X, C)
+    assert e.value.status == native.BM_EINVAL
+    assert "scratch" in str(e.value)
