@@ -286,6 +286,7 @@ def run_ours(args):
                            t_worker / max(n_worker, 1) * 1e3,
                            "rescored_rows": rep1["rescored_rows"],
                            "reseeded": rep1["reseeded"] - rep0["reseeded"],
+                           "sample_ms_per_step": (rep1["t_sample_s"] - rep0["t_sample_s"]) * 1e3 / args.steps,
                            "trace_cycles": [b - a for a, b in zip(rep0["trace_cycles"],
                                                                    rep1["trace_cycles"])],
                            "inexact_terms": rep1["inexact_terms"],
@@ -297,6 +298,35 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_mode(args):
+    """Kernel-level runs on the same workload for profiling (not the headline):
+    --mode fullpass: bm_assign (labels + f) on all of X with the C of a short fit;
+    --mode lloyd:    bm_lloyd on one 64,000-row sample (tol < 0: fixed iterations)."""
+    import torch
+    from paper_2403_18766_gb300 import native
+    from paper_2403_18766_gb300.synthetic import workload
+    X = workload(WORKLOAD)
+    Xd = torch.from_numpy(X).cuda()
+    C = Xd[torch.arange(0, X.shape[0], X.shape[0] // K_CLUSTERS)[:K_CLUSTERS].cuda()].contiguous()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    S = Xd[:POLICY["s_max"]].contiguous()
+    times = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if args.mode == "fullpass":
+            native.assign(Xd, C)
+        else:
+            native.lloyd(S, C, 20, -1.0)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    print(json.dumps({"mode": args.mode, "median_ms": statistics.median(times) * 1e3,
+                      "note": "wall time of the whole call (allocation, staging, prepass included)"}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -304,9 +334,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd"], default="fit",
+                    help="fit: the headline benchmark; fullpass / lloyd: one kernel family, "
+                         "for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.mode != "fit":
+        return run_kernel_mode(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

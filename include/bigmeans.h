@@ -120,13 +120,19 @@ typedef struct {
     int64_t kernel_launches;    /* kernels of this library launched so far    */
     int64_t fullpass_launches;  /* full-pass launches                         */
     int64_t reseeded;       /* centroids (re)seeded by K-means++              */
-    int64_t trace_cycles[8];  /* SM cycles on rank 0 of each worker cluster:
+    int64_t trace_cycles[16]; /* SM cycles on rank 0 of each worker cluster:
                                  [0] K-means++, [1] Lloyd assignment,
                                  [2] Lloyd exchange (barriers, reduction,
                                  update), [3] f_hat recompute, [4] sum of
                                  worker-kernel times, [5] longest worker
                                  kernel, [6] Lloyd assignments (count),
-                                 [7] worker kernels (count)              */
+                                 [7] worker kernels (count), [8] assignment
+                                 main loop, [9] its block reductions,
+                                 [10] first cluster barrier, [11] owner
+                                 update + objective, [12] second cluster
+                                 barrier, [13] centroid pull + prep     */
+    double t_sample_s;      /* device time of the sampling launches (part of
+                               t_worker_s)                                    */
 } bm_report;
 
 /* ---------------------------------------------------------------------------

@@ -28,7 +28,7 @@
 namespace bm {
 size_t worker_smem(int np, int k);
 cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
-size_t fullpass_smem_bytes(int np, int k);
+size_t fullpass_smem_bytes(int np, int k, int n);
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int grid, cudaStream_t st);
@@ -188,9 +188,13 @@ struct bm_fit_ctx {
     void* base = nullptr;
     Globals* glob = nullptr;
     int jobs = 0;                           // sample jobs per round: W * (P + 1)
+    int prefetched = -1;                    // round whose samples were drawn ahead
+    int rounds_planned = 0x7fffffff;        // rounds the caller intends to run (T)
+    cudaStream_t sst = nullptr;             // sampling stream (draws the next round ahead)
+    cudaEvent_t ev_sdone = nullptr;
     unsigned int gen = 1;                   // next sampler-table generation
     float* S = nullptr; long long* idx = nullptr; unsigned int* draws = nullptr;
-    unsigned long long* table = nullptr; int* job_s = nullptr; float* D2 = nullptr;
+    unsigned long long* table = nullptr; int* job_s = nullptr; float* D2 = nullptr; int* lab = nullptr;
     float* Cw = nullptr; float* Cw_cta = nullptr; unsigned char* deg = nullptr;
     double* fhat = nullptr; double* f_final = nullptr; long long* L_buf = nullptr;
     unsigned long long* timer = nullptr;
@@ -199,17 +203,17 @@ struct bm_fit_ctx {
     cudaEvent_t ev_fork = nullptr;
     std::vector<cudaEvent_t> ev_join;
     // phase timing: event pairs around each launch, summed when the stream syncs
-    struct Span { cudaEvent_t a, b; int kind; };
+    struct Span { cudaEvent_t a, b; int kind; cudaStream_t st; };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> pool;
-    double t_worker = 0, t_full = 0;
+    double t_worker = 0, t_full = 0, t_sample = 0;
     long long n_worker = 0, n_full = 0;
     long long n_kernels = 0;                // kernels of this library launched so far
 };
 
 namespace {
 
-WorkerArgs make_args(const bm_fit_ctx* c, int mode) {
+WorkerArgs make_args(const bm_fit_ctx* c, int mode, int parity = 0) {
     WorkerArgs a;
     memset(&a, 0, sizeof a);
     a.X = c->X; a.m = c->m; a.n = c->n; a.k = c->k;
@@ -220,15 +224,17 @@ WorkerArgs make_args(const bm_fit_ctx* c, int mode) {
     a.max_lloyd = c->bud.max_lloyd; a.trials = c->bud.kpp_candidates; a.tol = c->bud.tol;
     a.seed = c->seed;
     a.mode = mode; a.cs = c->cs; a.glob = c->glob;
-    a.S = c->S; a.S_stride = c->s_cap * c->np; a.job_s = c->job_s;
-    a.D2 = c->D2; a.D2_stride = c->s_cap;
+    a.S_stride = c->s_cap * c->np;
+    a.S = c->S + (long long)parity * c->jobs * a.S_stride;
+    a.job_s = c->job_s + (long long)parity * c->jobs;
+    a.D2 = c->D2; a.D2_stride = c->s_cap; a.lab = c->lab;
     a.Cw = c->Cw; a.Cw_cta = c->Cw_cta; a.deg = c->deg; a.fhat = c->fhat;
     a.L_buf = c->L_buf; a.L_cap = c->L_cap; a.f_final = c->f_final;
     a.gB = c->gB; a.gp2 = c->gp2;
     return a;
 }
 
-SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs) {
+SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs, int parity = 0) {
     SampleArgs a;
     memset(&a, 0, sizeof a);
     a.X = c->X; a.m = c->m; a.n = c->n; a.mode = mode; a.seed = c->seed;
@@ -236,13 +242,14 @@ SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs) {
     a.s_min = c->pol.s_min; a.s_max = c->s_hi;
     for (int i = 0; i < 16; ++i) a.set[i] = c->pol.set[i];
     a.set_len = c->pol.set_len;
-    a.S = c->S; a.S_stride = c->s_cap * c->np;
-    a.idx = c->idx; a.idx_stride = c->s_cap;
-    a.draws = c->draws; a.draws_stride = c->Tcap; a.Tcap = c->Tcap;
-    a.table = c->table; a.H = c->H; a.table_stride = c->H;
+    const long long J = (long long)parity * c->jobs;         // first job of this buffer half
+    a.S_stride = c->s_cap * c->np; a.S = c->S + J * a.S_stride;
+    a.idx_stride = c->s_cap; a.idx = c->idx + J * a.idx_stride;
+    a.draws_stride = c->Tcap; a.draws = c->draws + J * a.draws_stride; a.Tcap = c->Tcap;
+    a.H = c->H; a.table_stride = c->H; a.table = c->table + J * a.table_stride;
     a.gen_base = c->gen;
     c->gen += (unsigned int)jobs;
-    a.job_s = c->job_s; a.glob = c->glob;
+    a.job_s = c->job_s + J; a.glob = c->glob;
     return a;
 }
 
@@ -257,19 +264,21 @@ cudaEvent_t take_event(bm_fit_ctx* c) {
     return e;
 }
 // Record the start of a timed launch; returns the span index.
-size_t span_begin(bm_fit_ctx* c, int kind) {
-    bm_fit_ctx::Span sp{take_event(c), take_event(c), kind};
-    cudaEventRecord(sp.a, c->st);
+size_t span_begin(bm_fit_ctx* c, int kind, cudaStream_t st = nullptr) {
+    if (!st) st = c->st;
+    bm_fit_ctx::Span sp{take_event(c), take_event(c), kind, st};
+    cudaEventRecord(sp.a, st);
     c->spans.push_back(sp);
     return c->spans.size() - 1;
 }
-void span_end(bm_fit_ctx* c, size_t i) { cudaEventRecord(c->spans[i].b, c->st); }
+void span_end(bm_fit_ctx* c, size_t i) { cudaEventRecord(c->spans[i].b, c->spans[i].st); }
 // After a stream sync: fold the finished spans into the phase totals.
 void collect_spans(bm_fit_ctx* c) {
     for (auto& sp : c->spans) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
             if (sp.kind == 0) { c->t_worker += ms * 1e-3; c->n_worker++; }
+            else if (sp.kind == 2) { c->t_sample += ms * 1e-3; }
             else { c->t_full += ms * 1e-3; c->n_full++; }
         }
         c->pool.push_back(sp.a);
@@ -279,12 +288,13 @@ void collect_spans(bm_fit_ctx* c) {
 }
 
 // Carve one device allocation into the workspace: per sample job (W * (P+1)
-// per round) the padded sample, its indices, draws and sampler table; per
-// worker the K-means++ D^2, centroids and state.
+// per round, two rounds' worth so the next round is drawn while this one
+// runs) the padded sample, its indices, draws and sampler table; per worker
+// the K-means++ D^2, labels, centroids and state.
 bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const long long k = c->k, np = c->np;
-    const long long J = (long long)W * (c->pol.passes + 1);
-    c->jobs = (int)J;
+    c->jobs = W * (c->pol.passes + 1);
+    const long long J = 2ll * c->jobs;                  // two halves: this round, next round
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
     const size_t o_glob = take(sizeof(Globals));
@@ -294,6 +304,7 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const size_t o_tab = take((size_t)J * c->H * 8);
     const size_t o_js = take((size_t)J * 4);
     const size_t o_D2 = take((size_t)W * c->s_cap * 4);
+    const size_t o_lab = take((size_t)W * c->s_cap * 4);
     const size_t o_Cw = take((size_t)W * k * np * 4);
     const size_t o_Cwc = take((size_t)W * kMaxCluster * k * np * 4);
     const size_t o_deg = take((size_t)W * k);
@@ -311,7 +322,7 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     c->glob = (Globals*)(b + o_glob);
     c->S = (float*)(b + o_S); c->idx = (long long*)(b + o_idx); c->draws = (unsigned int*)(b + o_draws);
     c->table = (unsigned long long*)(b + o_tab); c->job_s = (int*)(b + o_js);
-    c->D2 = (float*)(b + o_D2); c->Cw = (float*)(b + o_Cw); c->Cw_cta = (float*)(b + o_Cwc);
+    c->D2 = (float*)(b + o_D2); c->lab = (int*)(b + o_lab); c->Cw = (float*)(b + o_Cw); c->Cw_cta = (float*)(b + o_Cwc);
     c->deg = (unsigned char*)(b + o_deg); c->fhat = (double*)(b + o_fhat); c->f_final = (double*)(b + o_ff);
     c->L_buf = (long long*)(b + o_L); c->timer = (unsigned long long*)(b + o_t);
     CU(cudaMemsetAsync(c->glob, 0, sizeof(Globals), c->st));
@@ -366,7 +377,8 @@ void fill_report(const bm_fit_ctx* c, const Globals& h, bm_report* rep) {
     rep->kernel_launches = c->n_kernels;
     rep->fullpass_launches = c->n_full;
     rep->reseeded = (int64_t)h.reseeded;
-    for (int i = 0; i < 8; ++i) rep->trace_cycles[i] = (int64_t)h.trace[i];
+    for (int i = 0; i < 16; ++i) rep->trace_cycles[i] = (int64_t)h.trace[i];
+    rep->t_sample_s = c->t_sample;
 }
 
 bm_status status_from_flags(const Globals& h) {
@@ -390,6 +402,10 @@ long long size_of(const bm_fit_ctx* c, int w, int t) {
 bm_status ensure_streams(bm_fit_ctx* c) {
     if (!c->wst.empty()) return BM_OK;
     const int ns = std::min(c->pol.workers, 16);
+    int lo_prio = 0, hi_prio = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+    CU(cudaStreamCreateWithPriority(&c->sst, cudaStreamNonBlocking, lo_prio));
+    CU(cudaEventCreateWithFlags(&c->ev_sdone, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     for (int i = 0; i < ns; ++i) {
         cudaStream_t s = nullptr;
@@ -411,18 +427,27 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     if (r1 != r0 + 1) return fail(BM_EINTERNAL, "one round per launch");
     const int big = 0x7fffffff;
     CU(cudaMemcpyAsync(&c->glob->rounds_done, &big, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    const int parity = r0 & 1;
     const size_t sp = span_begin(c, 0);
-    SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs);
-    sa.rnd = r0;
-    CU(launch_sample(c->np, sa, c->jobs, c->st));
-    c->n_kernels++;
+    if (c->prefetched == r0) {
+        CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));           // drawn ahead on the sampling stream
+    } else {
+        if (c->prefetched >= 0) CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));
+        SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, parity);
+        sa.rnd = r0;
+        const size_t sp_s = span_begin(c, 2);
+        CU(launch_sample(c->np, sa, c->jobs, c->st));
+        span_end(c, sp_s);
+        c->n_kernels++;
+    }
+    c->prefetched = -1;
     CU(cudaEventRecord(c->ev_fork, c->st));
     const int ns = (int)c->wst.size();
     for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(c->wst[i], c->ev_fork, 0));
     for (int w = 0; w < c->pol.workers; ++w) {
         long long smax = 0;
         for (int t = r0; t < r1; ++t) smax = std::max(smax, size_of(c, w, t));
-        WorkerArgs a = make_args(c, kModeRounds);
+        WorkerArgs a = make_args(c, kModeRounds, parity);
         a.round_begin = r0;
         a.round_end = r1;
         a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
@@ -430,6 +455,20 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         a.cs = cluster_size(smax, c->max_cs);
         CU(launch_worker(c->np, a, 1, c->wst[w % ns]));
         c->n_kernels++;
+    }
+    // Draw the next round's samples into the other half while the workers
+    // run; that half was last read by the previous round, which finished
+    // before ev_fork.
+    if (r0 + 1 < c->rounds_planned) {
+        CU(cudaStreamWaitEvent(c->sst, c->ev_fork, 0));
+        SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, parity ^ 1);
+        sa.rnd = r0 + 1;
+        const size_t sp_s = span_begin(c, 2, c->sst);
+        CU(launch_sample(c->np, sa, c->jobs, c->sst));
+        span_end(c, sp_s);
+        CU(cudaEventRecord(c->ev_sdone, c->sst));
+        c->n_kernels++;
+        c->prefetched = r0 + 1;
     }
     for (int i = 0; i < ns; ++i) {
         CU(cudaEventRecord(c->ev_join[i], c->wst[i]));
@@ -511,6 +550,7 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, con
     c->L_cap = (bud.rounds > 0 ? (long long)bud.rounds : 4096ll) * pol.workers * pol.passes;
     c->L_cap = std::min<long long>(c->L_cap, 1ll << 24);
     c->smem = worker_smem(c->np, k);
+    c->rounds_planned = bud.rounds > 0 ? bud.rounds : 0x7fffffff;
     cert_constants(c->np, c->gB, c->gp2);
     if ((s = alloc_workspace(c, pol.workers))) { delete c; return s; }
     cudaError_t e;
@@ -560,6 +600,10 @@ bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev
     bm_status s = check_ptr(C_out_dev, "C_out_dev");
     if (s) return s;
     WorkerArgs a = make_args(c, kModeFinalEval);
+    if (c->prefetched >= 0) {                  // a drawn-ahead round was not run
+        CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));
+        c->prefetched = -1;
+    }
     const size_t sp = span_begin(c, 0);
     SampleArgs sa = make_sample_args(c, kSampleFinal, 1);
     CU(launch_sample(c->np, sa, 1, c->st));
@@ -587,6 +631,7 @@ bm_status bm_fit_report(bm_fit_ctx* c, bm_report* rep) {
 
 void bm_fit_destroy(bm_fit_ctx* c) {
     if (!c) return;
+    if (c->prefetched >= 0 && c->ev_sdone) cudaStreamWaitEvent(c->st, c->ev_sdone, 0);
     if (c->base) {
         cudaFreeAsync(c->base, c->st);
         cudaStreamSynchronize(c->st);
@@ -594,6 +639,8 @@ void bm_fit_destroy(bm_fit_ctx* c) {
     collect_spans(c);
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     for (cudaStream_t s : c->wst) cudaStreamDestroy(s);
+    if (c->sst) cudaStreamDestroy(c->sst);
+    if (c->ev_sdone) cudaEventDestroy(c->ev_sdone);
     for (cudaEvent_t e : c->ev_join) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
@@ -788,7 +835,7 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
     if (!C_dev) return fail(BM_EINVAL, "C_dev is NULL");
     cudaStream_t sm = (cudaStream_t)stream;
     const int np = padded_dim(n);
-    const size_t smem = fullpass_smem_bytes(np, k);
+    const size_t smem = fullpass_smem_bytes(np, k, n);
     if (smem > kSmemLimit) return fail(BM_EINVAL, "k too large for the full pass");
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;

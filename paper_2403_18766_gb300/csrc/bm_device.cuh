@@ -32,8 +32,11 @@ struct Globals {
     // device phase trace (SM cycles on rank 0 of each worker cluster):
     // 0 K-means++, 1 Lloyd assignment, 2 Lloyd exchange (barriers, DSMEM
     // reduction, centroid update), 3 f_hat recompute, 4 sum of worker kernel
-    // times, 5 longest worker kernel, 6 Lloyd assignments, 7 worker kernels
-    unsigned long long trace[8];
+    // times, 5 longest worker kernel, 6 Lloyd assignments, 7 worker kernels,
+    // 8 assignment main loop, 9 assignment block reductions, 10 first cluster
+    // barrier, 11 owner update + objective, 12 second cluster barrier,
+    // 13 centroid pull + prep, 14-15 spare
+    unsigned long long trace[16];
     unsigned long long obj_words[4];   // full-pass objective, 32-bit chunks
     double f_full;                     // last full-pass objective
     double f_incumbent;                // least full objective seen

@@ -7,6 +7,7 @@
 // form, stores labels and accumulates the exact objective in 128-bit fixed
 // point.  CTA partials go to global memory as 32-bit chunks added into four
 // 64-bit words; the last CTA to finish rounds the total once to double.
+#include <algorithm>
 #include <cstdint>
 
 #include "bm_device.cuh"
@@ -35,40 +36,111 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(const float* __restri
     }
 }
 
+// ------------------------------------------------------------ TMA helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completing on `bar` (addresses and size
+// multiples of 16 bytes).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after `limit` polls and reports it.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, Globals* g) {
+    for (unsigned i = 0; i < (1u << 24); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(&g->err, kErrTimeout);
+    return false;
+}
+
+constexpr int kFpThreads = 256;      // rows per tile = threads per CTA (one row each)
+template <int NP>
+__host__ __device__ constexpr int fp_stages() { return NP >= 64 ? 2 : 3; }   // tiles in flight
+
 // mode: selection of the centroid set.
 //   sel_f == nullptr: use C directly (k x NP, padded).
 //   otherwise: C = Cw + w* k NP with w* = argmin sel_f[0..W) (lowest index).
 // incumbent: when set, f_incumbent = min(f_incumbent, f) and best_worker = w*.
+//
+// X is consumed in tiles of kFpThreads rows: a persistent CTA walks tiles
+// t0, t0 + grid, ...; thread 0 keeps kFpStages tiles in flight with 1-D bulk
+// copies (TMA) completing on per-stage mbarriers; every thread assigns one
+// row of the current tile from shared memory.  The ragged last tile is read
+// with plain loads.
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kFpThreads)
 fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __restrict__ Cw,
                 int k, const double* sel_f, int W, int* __restrict__ labels, Globals* g,
                 float gB, float gp2, int incumbent) {
-    constexpr int RT = (64 / NP) > 8 ? 8 : ((64 / NP) < 1 ? 1 : 64 / NP);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Cs = reinterpret_cast<float*>(smem_raw);                       // k * NP
-    float* CC = Cs + (size_t)k * NP;                                      // k
-    __shared__ unsigned __int128 red128[kWarps];
-    __shared__ unsigned long long red64[kWarps];
-    __shared__ unsigned int redu[kWarps];
+    constexpr int kW = kFpThreads / 32;
+    constexpr int kFpStages = fp_stages<NP>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const size_t tile_bytes = (size_t)kFpThreads * n * 4;
+    float* stage_buf = reinterpret_cast<float*>(smem_raw);                       // kFpStages tiles
+    float* Cs = reinterpret_cast<float*>(smem_raw + kFpStages * tile_bytes);     // k * NP
+    float* CC = Cs + (size_t)k * NP;                                             // k
+    // per-warp row buffer with an odd stride (n + 1 words): conflict-free
+    // both for the copy out of the stage and for one row per lane
+    float* wbuf = CC + ((k + 3) & ~3) + (size_t)(threadIdx.x >> 5) * 32 * (n + 1);
+    __shared__ __align__(8) unsigned long long bar[kFpStages];
+    __shared__ unsigned __int128 red128[kW];
+    __shared__ unsigned long long red64[kW];
+    __shared__ unsigned int redu[kW];
     __shared__ CertC cert;
     __shared__ int wsel;
     __shared__ bool last;
 
     if (g->nonfinite) return;
-    if (threadIdx.x == 0) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
         int best = 0;
         if (sel_f)
             for (int w = 1; w < W; ++w)
                 if (sel_f[w] < sel_f[best]) best = w;
         wsel = best;
+        for (int st = 0; st < kFpStages; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+
+    const long long ntiles = (m + kFpThreads - 1) / kFpThreads;
+    const long long full_tiles = m / kFpThreads;              // tiles copied with TMA
+    const long long grid = gridDim.x;
+    auto issue = [&](long long tile, int st) {
+        if (tile < full_tiles) {
+            mbar_expect_tx(&bar[st], (unsigned)tile_bytes);
+            bulk_g2s(stage_buf + (size_t)st * kFpThreads * n, X + tile * kFpThreads * (long long)n,
+                     (unsigned)tile_bytes, &bar[st]);
+        }
+    };
+    if (tid == 0)
+        for (int st = 0; st < kFpStages; ++st) issue(blockIdx.x + st * grid, st);
+
     const float* C = Cw + (sel_f ? (long long)wsel * k * NP : 0ll);
-    for (int e = threadIdx.x; e < k * NP; e += kThreads) Cs[e] = C[e];
+    for (int e = tid; e < k * NP; e += kFpThreads) Cs[e] = C[e];
     __syncthreads();
     unsigned int mx = 0;
-    for (int j = threadIdx.x; j < k; j += kThreads) {
+    for (int j = tid; j < k; j += kFpThreads) {
         float acc = 0.f, up = 0.f;
 #pragma unroll
         for (int d = 0; d < NP; ++d) {
@@ -79,70 +151,83 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
         CC[j] = acc;
         mx = max(mx, __float_as_uint(up));
     }
-    const unsigned int mm = block_max_u32(mx, redu);
-    if (threadIdx.x == 0) { cert.cmax2 = __uint_as_float(mm); cert.cmax = __fsqrt_ru(cert.cmax2); }
-    __syncthreads();
+    {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if ((tid & 31) == 0) redu[tid >> 5] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int mm = 0;
+            for (int i = 0; i < kW; ++i) mm = max(mm, redu[i]);
+            cert.cmax2 = __uint_as_float(mm);
+            cert.cmax = __fsqrt_ru(cert.cmax2);
+        }
+        __syncthreads();
+    }
     const CertC cc = cert;
     const Grids gr = grids_from_maxbits(g->maxbits);
 
     unsigned __int128 facc = 0;
     unsigned int inex = 0, resc = 0;
-    const long long rows_per_cta_iter = (long long)kThreads * RT;
-    for (long long base0 = (long long)blockIdx.x * rows_per_cta_iter; base0 < m;
-         base0 += (long long)gridDim.x * rows_per_cta_iter) {
-        const long long base = base0 + (long long)threadIdx.x;     // rows base + r*kThreads
-        float m2x[RT][NP];
+    for (long long it = 0;; ++it) {
+        const long long tile = blockIdx.x + it * grid;
+        if (tile >= ntiles) break;
+        const int st = (int)(it % kFpStages);
+        const unsigned parity = (unsigned)((it / kFpStages) & 1);
+        const long long row = tile * kFpThreads + tid;
+        float m2x[NP];
+        if (tile < full_tiles) {
+            mbar_wait(&bar[st], parity, g);
+            const int lane = tid & 31;
+            const float* src = stage_buf + (size_t)st * kFpThreads * n + (size_t)(tid & ~31) * n;
+            __syncwarp();
+            for (int r = 0; r < 32; ++r)
+                for (int d = lane; d < n; d += 32) wbuf[r * (n + 1) + d] = src[r * n + d];
+            __syncwarp();
+            const float* xr = wbuf + lane * (n + 1);
 #pragma unroll
-        for (int r = 0; r < RT; ++r) {
-            const long long row = base + (long long)r * kThreads;
+            for (int d = 0; d < NP; ++d) m2x[d] = (d < n) ? -2.f * xr[d] : 0.f;
+        } else {
             const float* xr = X + row * (long long)n;
 #pragma unroll
-            for (int d = 0; d < NP; ++d) m2x[r][d] = (row < m && d < n) ? -2.f * __ldg(xr + d) : 0.f;
+            for (int d = 0; d < NP; ++d) m2x[d] = (row < m && d < n) ? -2.f * __ldg(xr + d) : 0.f;
         }
-        float g1[RT], g2[RT];
-        int j1[RT];
-#pragma unroll
-        for (int r = 0; r < RT; ++r) { g1[r] = __int_as_float(0x7f800000); g2[r] = g1[r]; j1[r] = 0; }
+        // the stage is free once every thread has its row in registers
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(tile + kFpStages * grid, st);
+        }
+        float g1 = __int_as_float(0x7f800000), g2 = g1;
+        int j1 = 0;
         for (int j = 0; j < k; ++j) {
             const float* cj = Cs + (size_t)j * NP;
-            const float ccj = CC[j];
-            float e[RT];
-#pragma unroll
-            for (int r = 0; r < RT; ++r) e[r] = ccj;
+            float e = CC[j];
 #pragma unroll
             for (int q = 0; q < NP / 4; ++q) {
                 const float4 cv = reinterpret_cast<const float4*>(cj)[q];
-#pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    e[r] = __fmaf_rn(m2x[r][4 * q + 0], cv.x, e[r]);
-                    e[r] = __fmaf_rn(m2x[r][4 * q + 1], cv.y, e[r]);
-                    e[r] = __fmaf_rn(m2x[r][4 * q + 2], cv.z, e[r]);
-                    e[r] = __fmaf_rn(m2x[r][4 * q + 3], cv.w, e[r]);
-                }
+                e = __fmaf_rn(m2x[4 * q + 0], cv.x, e);
+                e = __fmaf_rn(m2x[4 * q + 1], cv.y, e);
+                e = __fmaf_rn(m2x[4 * q + 2], cv.z, e);
+                e = __fmaf_rn(m2x[4 * q + 3], cv.w, e);
             }
-#pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                g2[r] = fminf(g2[r], fmaxf(g1[r], e[r]));
-                j1[r] = (e[r] < g1[r]) ? j : j1[r];
-                g1[r] = fminf(g1[r], e[r]);
-            }
+            g2 = fminf(g2, fmaxf(g1, e));
+            j1 = (e < g1) ? j : j1;
+            g1 = fminf(g1, e);
         }
-#pragma unroll
-        for (int r = 0; r < RT; ++r) {
-            const long long row = base + (long long)r * kThreads;
-            if (row >= m) continue;
+        if (row < m) {
             float x[NP];
             float xn2 = 0.f;
 #pragma unroll
             for (int d = 0; d < NP; ++d) {
-                x[d] = -0.5f * m2x[r][d];
+                x[d] = -0.5f * m2x[d];
                 xn2 = __fmaf_ru(x[d], x[d], xn2);
             }
             const float xn = __fsqrt_ru(xn2);
             int lab;
             float dv;
-            if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
-                lab = j1[r];
+            if (certified(g1, g2, xn2, xn, cc, gB, gp2)) {
+                lab = j1;
                 dv = d32<NP>(x, Cs + (size_t)lab * NP);
             } else {
                 resc++;
@@ -157,22 +242,28 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
             if (labels) labels[row] = lab;
         }
     }
-    const unsigned __int128 F = block_sum_u128(facc, red128);
-    const unsigned long long I = block_sum<unsigned long long>(inex, red64);
-    const unsigned long long R = block_sum<unsigned long long>(resc, red64);
-    if (threadIdx.x == 0) {
+    // CTA reduction (one pass) and the grid-wide total
+    unsigned __int128 F = warp_sum_u128(facc);
+    const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) { red128[wid] = F; red64[wid] = IR; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned __int128 T = 0;
+        unsigned long long ir = 0;
+        for (int i = 0; i < kW; ++i) { T += red128[i]; ir += red64[i]; }
         for (int i = 0; i < 4; ++i) {
-            const unsigned long long chunk = (unsigned long long)((F >> (32 * i)) & 0xffffffffu);
+            const unsigned long long chunk = (unsigned long long)((T >> (32 * i)) & 0xffffffffu);
             if (chunk) atomicAdd(&g->obj_words[i], chunk);
         }
-        if (I) atomicAdd(&g->inexact, I);
-        if (R) atomicAdd(&g->rescored, R);
+        if (ir >> 32) atomicAdd(&g->inexact, ir >> 32);
+        if (ir & 0xffffffffull) atomicAdd(&g->rescored, ir & 0xffffffffull);
         __threadfence();
         const unsigned int prev = atomicAdd(&g->done_ctas, 1u);
         last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last && tid == 0) {
         __threadfence();
         unsigned __int128 T = 0;
         for (int i = 0; i < 4; ++i) {
@@ -238,29 +329,39 @@ __global__ void globaltimer_kernel(unsigned long long* out) {
 }
 
 // ------------------------------------------------------------ host launchers
-size_t fullpass_smem_bytes(int np, int k) { return (size_t)k * np * 4 + (size_t)k * 4; }
+size_t fullpass_smem_bytes(int np, int k, int n) {
+    const int stages = np >= 64 ? 2 : 3;
+    return (size_t)stages * kFpThreads * n * 4 + (size_t)k * np * 4 + (size_t)((k + 3) & ~3) * 4 +
+           (size_t)(kFpThreads / 32) * 32 * (n + 1) * 4;
+}
 
 template <int NP>
 static cudaError_t launch_fullpass_t(const float* X, long long m, int n, const float* C, int k,
                                      const double* sel_f, int W, int* labels, Globals* g, float gB,
-                                     float gp2, int incumbent, int grid, cudaStream_t st) {
-    const size_t smem = fullpass_smem_bytes(NP, k);
+                                     float gp2, int incumbent, int sms, cudaStream_t st) {
+    const size_t smem = fullpass_smem_bytes(NP, k, n);
     cudaError_t e = cudaFuncSetAttribute(fullpass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    fullpass_kernel<NP><<<grid, kThreads, smem, st>>>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fullpass_kernel<NP>, kFpThreads, smem);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (m + kFpThreads - 1) / kFpThreads;
+    const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
+    fullpass_kernel<NP><<<(unsigned)grid, kFpThreads, smem, st>>>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2,
+                                                                   incumbent);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
-                            int incumbent, int grid, cudaStream_t st) {
+                            int incumbent, int sms, cudaStream_t st) {
     switch (np) {
-        case 4: return launch_fullpass_t<4>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, grid, st);
-        case 8: return launch_fullpass_t<8>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, grid, st);
-        case 16: return launch_fullpass_t<16>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, grid, st);
-        case 32: return launch_fullpass_t<32>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, grid, st);
-        case 64: return launch_fullpass_t<64>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, grid, st);
+        case 4: return launch_fullpass_t<4>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
+        case 8: return launch_fullpass_t<8>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
+        case 16: return launch_fullpass_t<16>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
+        case 32: return launch_fullpass_t<32>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
+        case 64: return launch_fullpass_t<64>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
     }
     return cudaErrorInvalidValue;
 }

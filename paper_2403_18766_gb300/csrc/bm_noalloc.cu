@@ -20,7 +20,7 @@
 
 namespace bm {
 bm_status set_error(bm_status s, const char* msg);
-size_t fullpass_smem_bytes(int np, int k);
+size_t fullpass_smem_bytes(int np, int k, int n);
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int grid, cudaStream_t st);
@@ -71,6 +71,8 @@ extern "C" bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n,
     if ((long long)k * np > kMaxCentroidFloats)
         return err(BM_EINVAL, "k * padded n = %lld exceeds the fixed scratch of %lld floats "
                               "(bm_assign has no such limit)", (long long)k * np, kMaxCentroidFloats);
+    if (bm::fullpass_smem_bytes(np, k, n) > 227 * 1024)
+        return err(BM_EINVAL, "k = %d with n = %d needs more shared memory than the full pass has", k, n);
     if (!X_dev || ((uintptr_t)X_dev & 15)) return err(BM_EINVAL, "X_dev is NULL or not 16-byte aligned");
     if (!C_dev) return err(BM_EINVAL, "C_dev is NULL");
     int dev = 0;

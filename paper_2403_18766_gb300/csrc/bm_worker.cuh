@@ -36,6 +36,7 @@ struct WorkerArgs {
     float* S; long long S_stride;                 // s_cap * NP floats per job
     const int* job_s;                             // sample size of each job
     float* D2; long long D2_stride;               // s_cap per worker (K-means++ D^2)
+    int* lab;                                     // s_cap per worker (labels, same stride)
     // worker state
     float* Cw;               // W * k * NP (canonical, read at launch start)
     float* Cw_cta;           // W * cs * k * NP (per-CTA working copies)

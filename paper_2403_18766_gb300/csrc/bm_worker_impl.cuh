@@ -74,6 +74,7 @@ struct Worker {
     Grids g;
     float* S;               // current sample (padded rows), set per pass
     float* D2; float* Cw_mine;
+    int* lab_prev;          // label of each sample row in the previous assignment
 
     __device__ Worker(const WorkerArgs& args, cg::cluster_group c) : a(args), cl(c) {
         cs = a.cs;
@@ -85,6 +86,7 @@ struct Worker {
         g = grids_from_maxbits(a.glob->maxbits);
         S = a.S;
         D2 = a.D2 + (long long)w * a.D2_stride;
+        lab_prev = a.lab + (long long)w * a.D2_stride;
         Cw_mine = a.Cw_cta + ((long long)w * kMaxCluster + rank) * (long long)k * NP;
     }
 
@@ -146,17 +148,22 @@ struct Worker {
     }
 
     // --------------------------------------------- a4/a5: assign + accumulate
-    // Assign the CTA's rows against Ccur; accumulate exact sums and counts
-    // when `acc` is set; leave the CTA partial objective in sm.x.
-    __device__ void assign_slice(long long s, bool acc) {
+    // Assign the CTA's rows against Ccur and leave the CTA partial objective
+    // in sm.x.  mode 0: no sums (objective only); mode 1: first assignment of
+    // a Lloyd run, sums and counts rebuilt from zero; mode 2: incremental --
+    // the sums are exact integers, so only rows whose label changed since the
+    // previous assignment move from their old cluster to the new one.
+    __device__ void assign_slice(long long s, int mode) {
         constexpr int RT = RowsPerThread<NP>::v;
+        const bool acc = mode != 0;
         long long lo, hi;
         slice(s, lo, hi);
-        if (acc) {
+        if (mode == 1) {
             for (int e = threadIdx.x; e < k * acc_stride<NP>(); e += kThreads) sm.ACC[e] = 0;
             for (int e = threadIdx.x; e < k; e += kThreads) sm.cnt[e] = 0;
         }
         __syncthreads();
+        const long long t_loop = clock64();
         const CertC cc = *sm.cert;
         const float gB = a.gB, gp2 = a.gp2;
         const int gx = g.gx, gf = g.gf;
@@ -183,6 +190,10 @@ struct Worker {
                     for (int d = 0; d < NP; ++d) m2x[r][d] = 0.f;
                 }
             }
+            int oldlab[RT];
+#pragma unroll
+            for (int r = 0; r < RT; ++r)
+                oldlab[r] = (mode == 2 && base + r < hi) ? lab_prev[base + r] : -1;
             float g1[RT], g2[RT];
             int j1[RT];
 #pragma unroll
@@ -238,26 +249,47 @@ struct Worker {
                     }
                 }
                 acc_obj(facc, dv, gf, inex);
-                if (acc) {
+                if (acc && oldlab[r] != lab) {
+                    // Move the row between clusters (rolled loop over the row
+                    // re-read from L1: keeps the hot code small).
+                    const float* xr = S + row * NP;
                     atomicAdd(&sm.cnt[lab], 1);
                     int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
-#pragma unroll
-                    for (int d = 0; d < NP; ++d)
-                        if (d < n) ok &= acc_digits(wb + d * kDigits, x[d], gx, inex);
+#pragma unroll 1
+                    for (int d = 0; d < n; ++d) ok &= acc_digits(wb + d * kDigits, xr[d], gx, inex);
+                    if (oldlab[r] >= 0) {
+                        atomicSub(&sm.cnt[oldlab[r]], 1);
+                        int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
+#pragma unroll 1
+                        for (int d = 0; d < n; ++d) ok &= acc_digits(wo + d * kDigits, -xr[d], gx, inex);
+                    }
+                    lab_prev[row] = lab;
                 }
             }
         }
         if (!ok) atomicOr(&a.glob->err, kErrDigits);
-        const unsigned __int128 F = block_sum_u128(facc, sm.red128);
-        const unsigned long long I = block_sum<unsigned long long>(inex, reinterpret_cast<unsigned long long*>(sm.red64));
-        const unsigned long long R = block_sum<unsigned long long>(resc, reinterpret_cast<unsigned long long*>(sm.red64));
-        if (threadIdx.x == 0) {
-            sm.x->f_lo = (unsigned long long)F;
-            sm.x->f_hi = (unsigned long long)(F >> 64);
-            sm.x->inexact = I;
-            sm.x->rescored = R;
+        const long long t_red = clock64();
+        if (acc) trace_add(8, t_loop);
+        // one fused CTA reduction: objective (128-bit) and the two counters
+        unsigned __int128 F = warp_sum_u128(facc);
+        const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { sm.red128[wid] = F; sm.red64[wid] = (long long)IR; }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            F = (lane < kWarps) ? sm.red128[lane] : (unsigned __int128)0;
+            unsigned long long ir = (lane < kWarps) ? (unsigned long long)sm.red64[lane] : 0ull;
+            F = warp_sum_u128(F);
+            ir = warp_sum(ir);
+            if (lane == 0) {
+                sm.x->f_lo = (unsigned long long)F;
+                sm.x->f_hi = (unsigned long long)(F >> 64);
+                sm.x->inexact = ir >> 32;
+                sm.x->rescored = ir & 0xffffffffull;
+            }
         }
         __syncthreads();
+        if (acc) trace_add(9, t_red);
     }
 
     // After a barrier: warp 0 of rank 0 combines the CTA partials into f
@@ -284,27 +316,48 @@ struct Worker {
 
     // a6 (owner part): new centroid of each owned cluster j (j % cs == rank):
     // float(double(exact sum) / count); an empty cluster keeps its centroid.
+    // A group of G >= cs lanes handles one owned (cluster, dimension)
+    // element: lane q of the group reads CTA q's digits and count, a
+    // segmented shuffle reduction combines them, and the group leader does
+    // the double conversion and division (many elements in parallel).
     __device__ void owner_update() {
         const int nOwned = (k - rank + cs - 1) / cs;
-        for (int e = threadIdx.x; e < nOwned * NP; e += kThreads) {
-            const int j = rank + (e / NP) * cs;
-            const int d = e % NP;
-            long long cntj = 0;
+        const int G = cs <= 1 ? 1 : cs <= 2 ? 2 : cs <= 4 ? 4 : cs <= 8 ? 8 : 16;
+        const int q = threadIdx.x % G;
+        const int groups = kThreads / G;
+        const int total = nOwned * NP;
+        // all threads run the same trip count so the shuffles stay converged
+        for (int base = 0; base < total; base += groups) {
+            const int e = base + (int)threadIdx.x / G;
+            const bool valid = e < total;
+            const int j = rank + (valid ? e / NP : 0) * cs;
+            const int d = valid ? e % NP : 0;
             __int128 V = 0;
-#pragma unroll 4
-            for (int q = 0; q < cs; ++q) {
-                cntj += cl.map_shared_rank(sm.cnt, q)[j];
+            long long cntj = 0;
+            if (valid && q < cs) {
                 const int* wq = cl.map_shared_rank(sm.ACC, q) + (size_t)j * acc_stride<NP>() + d * kDigits;
+                int dg[kDigits];
 #pragma unroll
-                for (int i = 0; i < kDigits; ++i) V += (__int128)wq[i] * ((__int128)1 << (16 * i));
+                for (int i = 0; i < kDigits; ++i) dg[i] = wq[i];
+                cntj = cl.map_shared_rank(sm.cnt, q)[j];
+#pragma unroll
+                for (int i = 0; i < kDigits; ++i) V += (__int128)dg[i] * ((__int128)1 << (16 * i));
             }
-            float c = sm.Ccur[(size_t)j * NP + d];
-            if (cntj > 0 && d < n) {
-                const double sum = i128_to_double(V, g.gx);
-                c = __double2float_rn(__ddiv_rn(sum, (double)cntj));
+            for (int o = G >> 1; o > 0; o >>= 1) {
+                const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)V, o, G);
+                const long long hi = __shfl_down_sync(0xffffffffu, (long long)(V >> 64), o, G);
+                V += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+                cntj += __shfl_down_sync(0xffffffffu, cntj, o, G);
             }
-            sm.Cnew[(size_t)j * NP + d] = c;
-            if (d == 0) sm.empty[j] = (cntj == 0) ? 1 : 0;
+            if (valid && q == 0) {
+                float c = sm.Ccur[(size_t)j * NP + d];
+                if (cntj > 0 && d < n) {
+                    const double sum = i128_to_double(V, g.gx);
+                    c = __double2float_rn(__ddiv_rn(sum, (double)cntj));
+                }
+                sm.Cnew[(size_t)j * NP + d] = c;
+                if (d == 0) sm.empty[j] = (cntj == 0) ? 1 : 0;
+            }
         }
     }
 
@@ -336,7 +389,7 @@ struct Worker {
 
     // f(Ccur, S) without updating centroids (recompute of f_hat_w, recheck).
     __device__ double eval(long long s) {
-        assign_slice(s, false);
+        assign_slice(s, 0);
         cl.sync();
         if (rank == 0 && threadIdx.x < 32) {
             const double f = combine_objective_warp();
@@ -359,11 +412,13 @@ struct Worker {
         int it = 0;
         for (;;) {
             const long long t_a = clock64();
-            assign_slice(s, true);
+            assign_slice(s, it == 0 ? 1 : 2);
             trace_add(1, t_a);
             if (tracer()) atomicAdd(&a.glob->trace[6], 1ull);
             const long long t_x = clock64();
             cl.sync();                                       // partials ready
+            trace_add(10, t_x);
+            const long long t_o = clock64();
             owner_update();
             double fw = 0.0;
             if (rank == 0 && threadIdx.x < 32) fw = combine_objective_warp();
@@ -375,7 +430,11 @@ struct Worker {
                 sm.x->fval = f;
                 sm.x->stop = stop;
             }
+            trace_add(11, t_o);
+            const long long t_b2 = clock64();
             cl.sync();                                       // updates + decision ready
+            trace_add(12, t_b2);
+            const long long t_p = clock64();
             double f; int stop;
             read_decision(f, stop);
             if (stop) {
@@ -386,6 +445,7 @@ struct Worker {
             }
             pull_new_centroids();
             prep_centroids();
+            trace_add(13, t_p);
             trace_add(2, t_x);
             f_prev = f;
             ++it;

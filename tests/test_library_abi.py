@@ -48,7 +48,7 @@ def test_struct_layouts_match_c():
     # offsets follow C's natural alignment rules for these field lists
     assert ctypes.sizeof(native.SamplePolicy) == 8 + 8 + 16 * 8 + 4 + 4 + 4 + 4
     assert native.Budget.seconds.offset == 8 and native.Budget.tol.offset == 24
-    assert ctypes.sizeof(native.Report) == 8 * 3 + 4 + 4 + 8 * 7 + 8 * 3 + 8 * 3 + 8 * 8
+    assert ctypes.sizeof(native.Report) == 8 * 3 + 4 + 4 + 8 * 7 + 8 * 3 + 8 * 3 + 8 * 16 + 8
 
 
 def test_errors_without_gpu_are_status_codes(lib):
