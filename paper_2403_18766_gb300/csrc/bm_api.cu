@@ -78,7 +78,7 @@ bm_status fail(bm_status s, const char* fmt, ...) {
     } while (0)
 
 constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kRowsPerCta = 4096;
+constexpr int kRowsPerCta = 2048;
 
 int padded_dim(int n) {
     if (n <= 4) return 4;
@@ -273,10 +273,19 @@ size_t span_begin(bm_fit_ctx* c, int kind, cudaStream_t st = nullptr) {
 }
 void span_end(bm_fit_ctx* c, size_t i) { cudaEventRecord(c->spans[i].b, c->spans[i].st); }
 // After a stream sync: fold the finished spans into the phase totals.
+// Spans on other streams (the sampling stream) may still be running: those
+// stay queued until they complete.
 void collect_spans(bm_fit_ctx* c) {
+    std::vector<bm_fit_ctx::Span> pending;
     for (auto& sp : c->spans) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) {
+        const cudaError_t e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+        if (e == cudaErrorNotReady) {
+            cudaGetLastError();
+            pending.push_back(sp);
+            continue;
+        }
+        if (e == cudaSuccess) {
             if (sp.kind == 0) { c->t_worker += ms * 1e-3; c->n_worker++; }
             else if (sp.kind == 2) { c->t_sample += ms * 1e-3; }
             else { c->t_full += ms * 1e-3; c->n_full++; }
@@ -284,7 +293,7 @@ void collect_spans(bm_fit_ctx* c) {
         c->pool.push_back(sp.a);
         c->pool.push_back(sp.b);
     }
-    c->spans.clear();
+    c->spans.swap(pending);
 }
 
 // Carve one device allocation into the workspace: per sample job (W * (P+1)
@@ -636,7 +645,9 @@ void bm_fit_destroy(bm_fit_ctx* c) {
         cudaFreeAsync(c->base, c->st);
         cudaStreamSynchronize(c->st);
     }
+    if (c->sst) cudaStreamSynchronize(c->sst);
     collect_spans(c);
+    for (auto& sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
     for (cudaStream_t s : c->wst) cudaStreamDestroy(s);
     if (c->sst) cudaStreamDestroy(c->sst);

@@ -16,7 +16,7 @@
 namespace bm {
 namespace cg = cooperative_groups;
 
-constexpr int kThreads = 512;          // threads per CTA of every kernel here
+constexpr int kThreads = 256;          // threads per CTA of the worker, sampling and prepass kernels
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCluster = 16;        // CTAs per worker cluster (non-portable above 8)
 

@@ -170,7 +170,11 @@ struct Worker {
         unsigned __int128 facc = 0;
         unsigned int inex = 0, resc = 0;
         bool ok = true;
-        for (long long base = lo + (long long)threadIdx.x * RT; base < hi; base += (long long)kThreads * RT) {
+        const int lane = threadIdx.x & 31;
+        // warp-uniform trip count (the move step below uses warp ballots)
+        for (long long base0 = lo + (long long)(threadIdx.x & ~31) * RT; base0 < hi;
+             base0 += (long long)kThreads * RT) {
+            const long long base = base0 + (long long)lane * RT;
             float m2x[RT][NP];
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
@@ -225,7 +229,7 @@ struct Worker {
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
                 const long long row = base + r;
-                if (row >= hi) continue;
+                const bool valid = row < hi;
                 float x[NP];
                 float xn2 = 0.f;
 #pragma unroll
@@ -234,36 +238,68 @@ struct Worker {
                     xn2 = __fmaf_ru(x[d], x[d], xn2);
                 }
                 const float xn = __fsqrt_ru(xn2);
-                int lab;
-                float dv;
-                if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
-                    lab = j1[r];
-                    dv = d32<NP>(x, sm.Ccur + (size_t)lab * NP);
-                } else {
-                    resc++;
-                    lab = 0;
-                    dv = d32<NP>(x, sm.Ccur);
-                    for (int j = 1; j < k; ++j) {
-                        const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
-                        if (dj < dv) { dv = dj; lab = j; }
+                int lab = 0;
+                float dv = 0.f;
+                if (valid) {
+                    if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
+                        lab = j1[r];
+                        dv = d32<NP>(x, sm.Ccur + (size_t)lab * NP);
+                    } else {
+                        resc++;
+                        dv = d32<NP>(x, sm.Ccur);
+                        for (int j = 1; j < k; ++j) {
+                            const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
+                            if (dj < dv) { dv = dj; lab = j; }
+                        }
                     }
+                    acc_obj(facc, dv, gf, inex);
                 }
-                acc_obj(facc, dv, gf, inex);
-                if (acc && oldlab[r] != lab) {
-                    // Move the row between clusters (rolled loop over the row
-                    // re-read from L1: keeps the hot code small).
-                    const float* xr = S + row * NP;
-                    atomicAdd(&sm.cnt[lab], 1);
-                    int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
+                if (acc) {
+                    // Move rows whose label changed between clusters.  Many
+                    // movers (first assignment): each lane moves its own row.
+                    // Few movers (later iterations): the warp moves them one
+                    // at a time, lanes over dimensions, so the warp does not
+                    // walk the move path with one or two lanes active.
+                    const bool moved = valid && oldlab[r] != lab;
+                    const unsigned mv = __ballot_sync(0xffffffffu, moved);
+                    if (__popc(mv) > 8) {
+                        if (moved) {
+                            const float* xr = S + row * NP;
+                            atomicAdd(&sm.cnt[lab], 1);
+                            int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
 #pragma unroll 1
-                    for (int d = 0; d < n; ++d) ok &= acc_digits(wb + d * kDigits, xr[d], gx, inex);
-                    if (oldlab[r] >= 0) {
-                        atomicSub(&sm.cnt[oldlab[r]], 1);
-                        int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
+                            for (int d = 0; d < n; ++d) ok &= acc_digits(wb + d * kDigits, xr[d], gx, inex);
+                            if (oldlab[r] >= 0) {
+                                atomicSub(&sm.cnt[oldlab[r]], 1);
+                                int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
 #pragma unroll 1
-                        for (int d = 0; d < n; ++d) ok &= acc_digits(wo + d * kDigits, -xr[d], gx, inex);
+                                for (int d = 0; d < n; ++d) ok &= acc_digits(wo + d * kDigits, -xr[d], gx, inex);
+                            }
+                            lab_prev[row] = lab;
+                        }
+                    } else {
+                        unsigned rem = mv;
+                        while (rem) {
+                            const int src = __ffs(rem) - 1;
+                            rem &= rem - 1u;
+                            const long long srow = __shfl_sync(0xffffffffu, row, src);
+                            const int snew = __shfl_sync(0xffffffffu, lab, src);
+                            const int sold = __shfl_sync(0xffffffffu, oldlab[r], src);
+                            if (lane == src) {
+                                atomicAdd(&sm.cnt[snew], 1);
+                                if (sold >= 0) atomicSub(&sm.cnt[sold], 1);
+                                lab_prev[srow] = snew;
+                            }
+                            const float* xr = S + srow * NP;
+                            int* wb = sm.ACC + (size_t)snew * acc_stride<NP>();
+                            int* wo = sm.ACC + (size_t)(sold >= 0 ? sold : 0) * acc_stride<NP>();
+                            for (int d = lane; d < n; d += 32) {
+                                const float xv = xr[d];
+                                ok &= acc_digits(wb + d * kDigits, xv, gx, inex);
+                                if (sold >= 0) ok &= acc_digits(wo + d * kDigits, -xv, gx, inex);
+                            }
+                        }
                     }
-                    lab_prev[row] = lab;
                 }
             }
         }
@@ -273,7 +309,7 @@ struct Worker {
         // one fused CTA reduction: objective (128-bit) and the two counters
         unsigned __int128 F = warp_sum_u128(facc);
         const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int wid = threadIdx.x >> 5;
         if (lane == 0) { sm.red128[wid] = F; sm.red64[wid] = (long long)IR; }
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -625,7 +661,7 @@ struct Worker {
 // trials > 3 would need more broadcast slots; the host caps it at 3.
 
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 1) worker_kernel(const WorkerArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a) {
     Worker<NP> W(a, cg::this_cluster());
     if (a.glob->nonfinite) return;            // uniform: read before any barrier
     const int w = W.w;
