@@ -327,6 +327,66 @@ def run_kernel_mode(args):
     return 0
 
 
+def run_precision(args):
+    """Precision form of the full-data pass on the 10^7 x 64, k = 100 workload:
+    X packed once to BF16 (resident), then bm_assign_bf16 timed with CUDA
+    events (L2 flushed between calls) against the HBM roofline; the exact FP32
+    pass (bm_assign) on the same C is timed beside it, and the label
+    agreement and objective error of the precision form are reported."""
+    import torch
+    from paper_2403_18766_gb300 import native
+    from paper_2403_18766_gb300.synthetic import workload
+    X = workload("gmm_10m_n64_k100z")
+    m, n = X.shape
+    k = 100
+    Xd = torch.from_numpy(X).cuda()
+    # centroids as the pass meets them after a fit: one short Big-means fit
+    C, _, _ = native.fit(Xd, k, native.make_policy(s_min=20000, s_max=60000, workers=8, passes=4),
+                         native.make_budget(rounds=1), seed=3, labels=False)
+    P = native.PackedBF16(Xd)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = fn()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                ts.append(a.elapsed_time(b) / 1e3)
+        return statistics.median(ts), out
+
+    t_bf, (Yb, fb, rb) = timed(lambda: native.assign_bf16(P, C, tau=1e-3))
+    t_tc0, _ = timed(lambda: native.assign_bf16(P, C, tau=0.0))
+    t_ex, (Ye, fe, re_) = timed(lambda: native.assign(Xd, C))
+    peaks, src = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_bf = m * (128 + 4 + 4)                 # packed row + norm + label
+    line = {"metric": "precision-form full pass (labels + f)", "value": bytes_bf / t_bf / 1e9,
+            "unit": "GB/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "gmm_10m_n64_k100z: m=1e7, n=64, 100 Gaussians (Zipf 1.2), k=100",
+                       "dtype": "bf16 distance tiles, FP32 accumulate (tcgen05), FP32 re-score",
+                       "tau": 1e-3, "l2": "flushed between calls"},
+            "roofline": {"bound": "hbm", "achieved": bytes_bf / t_bf / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": bytes_bf / t_bf / 1e9 / hbm, "traffic": None,
+                         "kernel": "tc_fullpass_kernel (tcgen05.mma kind::f16, 1-D TMA tiles)",
+                         "algorithmic": "136 bytes per row (128 B packed row, 4 B norm, 4 B label)",
+                         "peak_source": src},
+            "ms_per_call": t_bf * 1e3, "exact_fp32_ms_per_call": t_ex * 1e3,
+            "tau0_ms_per_call": t_tc0 * 1e3, "tau0_GBps": bytes_bf / t_tc0 / 1e9,
+            "speedup_vs_exact_pass": t_ex / t_bf,
+            "rescored_rows": rb["rescored_rows"],
+            "label_mismatch_vs_exact": int((Yb != Ye).sum().item()),
+            "f_rel_err_vs_exact": abs(fb - fe) / fe, "f_precision": fb, "f_exact": fe}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,12 +394,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd"], default="fit",
+    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision"], default="fit",
                     help="fit: the headline benchmark; fullpass / lloyd: one kernel family, "
                          "for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.mode == "precision":
+        return run_precision(args)
     if args.mode != "fit":
         return run_kernel_mode(args)
     if args.impl == "reference":

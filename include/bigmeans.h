@@ -220,6 +220,38 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
                     bm_report* report_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Precision form of the full-data pass (a9 with the distance contraction on
+ * the tensor cores).
+ *
+ * bm_pack_bf16 -- pack X (m x n float32, n <= 64) into the layout the
+ * tensor-core pass reads: m_pad = round_up(m, 128) rows of 64 bfloat16
+ * (round to nearest, zero padded), 128 bytes per row, with the 16-byte
+ * chunks of row r stored at chunk index (c XOR (r mod 8)); and
+ * norms[r] = float(sum_d bf16(x_rd)^2), norms[m_pad] = max |x| (the
+ * fixed-point grid of the objective).  Xb_out_dev: m_pad * 128 bytes,
+ * 1024-byte aligned; norms_out_dev: m_pad + 1 floats.  Caller owns both;
+ * they stay valid for any number of bm_assign_bf16 calls.  Non-finite X is
+ * rejected with BM_EINVAL.
+ *
+ * bm_assign_bf16 -- labels of every row of X and the objective, with
+ * g_j = ||c_j||^2 - 2 x.c_j formed from bfloat16 x and c with FP32
+ * accumulation (tcgen05, kind::f16).  A row whose two least g differ by less
+ * than tau * ||x||^2 is re-scored from the FP32 master X_dev with the exact
+ * definition (FP32 direct form, lowest index on ties); otherwise its label is
+ * the least g and its distance ||x||^2 + g (both in FP32).  f is the exact
+ * sum of those distances rounded once to double; report->rescored_rows
+ * counts re-scored rows.  1 <= k <= 256.  Labels of rows that are not
+ * re-scored can differ from bm_assign where two centroids are within the
+ * BF16 error; the difference in f is reported by the tests and the bench.
+ * ------------------------------------------------------------------------- */
+bm_status bm_pack_bf16(const float* X_dev, int64_t m, int32_t n, void* Xb_out_dev,
+                       float* norms_out_dev, void* stream);
+bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev,
+                         int64_t m, int32_t n, const float* C_dev, int32_t k, float tau,
+                         int32_t* labels_out_dev, double* f_out_host, bm_report* report_out,
+                         void* stream);
+
+/* ---------------------------------------------------------------------------
  * bm_assign_noalloc -- the full-data pass of bm_assign (labels of every row of
  * X and f(C, X), same numeric definition, same results) without allocating
  * any device memory.  The paper has no counterpart: this is a deployment

@@ -40,6 +40,12 @@ cudaError_t launch_select_unpad(const float* Cw, const double* sel_f, int W, int
 cudaError_t launch_init_state(double* fhat, int W, unsigned char* deg, long long kdeg, Globals* g,
                               cudaStream_t st);
 cudaError_t launch_globaltimer(unsigned long long* out, cudaStream_t st);
+size_t tc_smem_bytes(int k, int Npad);
+cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad, void* Xb, float* norms,
+                             cudaStream_t st);
+cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
+                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, int sms,
+                               cudaStream_t st);
 }  // namespace bm
 
 using namespace bm;
@@ -347,11 +353,13 @@ bm_status check_ptr(const void* p, const char* what) {
     return BM_OK;
 }
 
-// Size checks shared by the fit and the step entry points.
-bm_status check_shape(long long m, int n, int k) {
+// Size checks shared by the fit and the step entry points (the worker's
+// shared-memory accumulators bound k * n unless only the full pass runs).
+bm_status check_shape(long long m, int n, int k, bool worker = true) {
     if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range [1, 2^31)", m);
     if (n < 1 || n > 64) return fail(BM_EINVAL, "n = %d out of range [1, 64]", n);
     if (k < 1) return fail(BM_EINVAL, "k = %d must be >= 1", k);
+    if (!worker) return BM_OK;
     const size_t smem = worker_smem(padded_dim(n), k);
     if (smem > kSmemLimit)
         return fail(BM_EINVAL, "k = %d with n = %d needs %zu bytes of shared memory (limit %zu)", k, n,
@@ -840,7 +848,7 @@ bm_status bm_lloyd(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev,
 
 bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev, int32_t k,
                     int32_t* labels_out_dev, double* f_out_host, bm_report* rep, void* stream) {
-    bm_status st = check_shape(m, n, k);
+    bm_status st = check_shape(m, n, k, false);
     if (st) return st;
     if ((st = check_ptr(X_dev, "X_dev"))) return st;
     if (!C_dev) return fail(BM_EINVAL, "C_dev is NULL");
@@ -871,6 +879,67 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
     const cudaError_t e2 = cudaStreamSynchronize(sm);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return fail(BM_ECUDA, "full pass: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if ((st = status_from_flags(h))) return st;
+    if (f_out_host) *f_out_host = h.f_full;
+    if (rep) {
+        memset(rep, 0, sizeof *rep);
+        rep->f_full = h.f_full;
+        rep->f_incumbent = h.f_full;
+        rep->rescored_rows = (int64_t)h.rescored;
+        rep->inexact_terms = (int64_t)h.inexact;
+    }
+    return BM_OK;
+}
+
+// --------------------------------------------------- precision form (BF16)
+bm_status bm_pack_bf16(const float* X_dev, int64_t m, int32_t n, void* Xb_out_dev, float* norms_out_dev,
+                       void* stream) {
+    if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range", (long long)m);
+    if (n < 1 || n > 64) return fail(BM_EINVAL, "n = %d out of range [1, 64]", n);
+    if (!X_dev || !Xb_out_dev || !norms_out_dev) return fail(BM_EINVAL, "NULL pointer");
+    if (((uintptr_t)Xb_out_dev) & 1023) return fail(BM_EINVAL, "Xb_out_dev must be 1024-byte aligned");
+    const long long m_pad = (m + 127) / 128 * 128;
+    CU(launch_pack_bf16(X_dev, m, n, m_pad, Xb_out_dev, norms_out_dev, (cudaStream_t)stream));
+    float mx = 0.f;
+    CU(cudaMemcpyAsync(&mx, norms_out_dev + m_pad, sizeof mx, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!(mx < INFINITY)) return fail(BM_EINVAL, "X contains non-finite values");
+    if (mx >= 0x1p126f) return fail(BM_EINVAL, "max |x| must be below 2^126");
+    return BM_OK;
+}
+
+bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m, int32_t n,
+                         const float* C_dev, int32_t k, float tau, int32_t* labels_out_dev, double* f_out_host,
+                         bm_report* rep, void* stream) {
+    if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range", (long long)m);
+    if (n < 1 || n > 64) return fail(BM_EINVAL, "n = %d out of range [1, 64]", n);
+    if (k < 1 || k > 256) return fail(BM_EINVAL, "k = %d out of range [1, 256] for the tensor-core pass", k);
+    if (!Xb_dev || !norms_dev || !X_dev || !C_dev) return fail(BM_EINVAL, "NULL pointer");
+    if (((uintptr_t)Xb_dev) & 1023) return fail(BM_EINVAL, "Xb_dev must be 1024-byte aligned");
+    if (!(tau >= 0.f)) return fail(BM_EINVAL, "tau must be >= 0");
+    if (tc_smem_bytes(k, (k + 15) & ~15) > kSmemLimit) return fail(BM_EINVAL, "k too large");
+    cudaStream_t sm = (cudaStream_t)stream;
+    void* base = nullptr;
+    const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
+    CU(cudaMallocAsync(&base, gb + (size_t)m * 4, sm));
+    Globals* g = (Globals*)base;
+    int* queue = (int*)((char*)base + gb);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
+        (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
+        (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, labels_out_dev, queue, g,
+                                sm_count(), sm))) {
+        cudaFreeAsync(base, sm);
+        cudaStreamSynchronize(sm);
+        return fail(BM_ECUDA, "tensor-core pass launch: %s", cudaGetErrorString(e));
+    }
+    Globals h;
+    e = cudaMemcpyAsync(&h, g, sizeof(Globals), cudaMemcpyDeviceToHost, sm);
+    cudaFreeAsync(base, sm);
+    const cudaError_t e2 = cudaStreamSynchronize(sm);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(BM_ECUDA, "tensor-core pass: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    bm_status st;
     if ((st = status_from_flags(h))) return st;
     if (f_out_host) *f_out_host = h.f_full;
     if (rep) {

@@ -43,7 +43,7 @@ struct Globals {
     int best_worker;                   // worker whose centroids were assessed
     int s_opt;
     int rounds_done;
-    int pad_;
+    unsigned int queue_len;            // rows queued for exact re-scoring (tensor-core pass)
 };
 constexpr unsigned kErrSample = 1u;    // sampler ran out of draws
 constexpr unsigned kErrDigits = 2u;    // fixed-point range exceeded

@@ -1,0 +1,422 @@
+// Precision form of the full-data pass (Alg. 1 last step, Eq. 1) on the
+// fifth-generation tensor cores of sm_103a.
+//
+// X is packed once into BF16 rows of 64 elements (128 bytes, zero padded),
+// with the 16-byte chunks of every row XOR-swizzled by (row mod 8): exactly
+// the 128-byte-swizzle K-major layout the tensor core reads from shared
+// memory, so a plain 1-D bulk copy (TMA) of 128 consecutive rows lands in
+// shared memory ready to use.  The pack also stores fl(||x_bf16||^2).
+//
+// Per tile of 128 rows one thread issues four tcgen05.mma (M = 128, N =
+// k rounded up to 16, K = 16 each) of X_bf16 x C_bf16^T into a tensor-memory
+// accumulator (FP32); four warps then read their 32 rows with tcgen05.ld,
+// form g_j = ||c_j||^2 - 2 x.c_j, keep the two least, and
+//  * if g2 - g1 >= tau * ||x||^2: label = j1, distance = ||x||^2 + g1;
+//  * otherwise the row index is appended to a queue, and a second kernel
+//    re-scores the queued rows from the FP32 master copy with the exact
+//    definition (FP32 direct form, lowest index on ties).
+// The objective is the exact sum of the per-row distances (integer fixed
+// point), rounded once.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
+#include "bm_device.cuh"
+
+namespace bm {
+
+constexpr int kTcRows = 128;           // rows per tile (MMA M)
+constexpr int kTcK = 64;               // packed row width (BF16 elements)
+constexpr int kTcStages = 3;           // X tiles in flight
+constexpr int kTcThreads = 128;        // 4 warps: TMEM lane quarters
+constexpr int kTcTmemCols = 256;       // tensor-memory columns per CTA
+
+// ------------------------------------------------------------------ pack
+// Xb[r][chunk c ^ (r & 7)] holds elements 8c .. 8c+7 of row r (BF16, RN);
+// rows m .. m_pad-1 and elements n .. 63 are zero.  norms[r] = fl(sum x_b^2).
+__global__ void pack_bf16_kernel(const float* __restrict__ X, long long m, int n, long long m_pad,
+                                 __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms) {
+    const long long total = m_pad * (kTcK / 8);                 // 16-byte chunks
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / (kTcK / 8);
+        const int c = (int)(e % (kTcK / 8));
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int d = 8 * c + i;
+            v[i] = __float2bfloat16_rn((r < m && d < n) ? X[r * n + d] : 0.f);
+        }
+        const int pc = c ^ (int)(r & 7);
+        *reinterpret_cast<uint4*>(Xb + r * kTcK + 8 * pc) = *reinterpret_cast<const uint4*>(v);
+    }
+    unsigned int mx = 0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < m_pad;
+         r += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int d = 0; d < n && r < m; ++d) {
+            const float x = X[r * n + d];
+            mx = max(mx, __float_as_uint(x) & 0x7fffffffu);
+            const float b = __bfloat162float(__float2bfloat16_rn(x));
+            acc = __fmaf_rn(b, b, acc);
+        }
+        norms[r] = acc;
+    }
+    // norms[m_pad] = max |x| (bits; non-finite values compare above all finite ones)
+    if (mx) atomicMax(reinterpret_cast<unsigned int*>(norms + m_pad), mx);
+}
+
+// ------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ unsigned s_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mbar_init(unsigned long long* b, unsigned cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void tc_expect_tx(unsigned long long* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tc_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(s_addr(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool tc_try_wait(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(s_addr(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Bounded wait; on timeout the error flag is set and the caller carries on.
+__device__ __forceinline__ bool tc_wait(unsigned long long* b, unsigned parity, Globals* g) {
+    for (unsigned i = 0; i < (1u << 24); ++i)
+        if (tc_try_wait(b, parity)) return true;
+    atomicOr(&g->err, kErrTimeout);
+    return false;
+}
+
+// 64-bit shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
+// groups 1024 bytes apart, descriptor version 1.
+__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr >> 4) & 0x3FFFu);          // start address
+    d |= (unsigned long long)1u << 16;                          // leading byte offset (unused here)
+    d |= (unsigned long long)(1024u >> 4) << 32;                // stride byte offset
+    d |= (unsigned long long)1u << 46;                          // version
+    d |= (unsigned long long)2u << 61;                          // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, N and M as given.
+__host__ __device__ constexpr unsigned idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long adesc, unsigned long long bdesc,
+                                       unsigned idesc, unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 columns of 32-bit tensor-memory cells -> 16 registers per thread.
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------ the full pass
+// Shared memory: [X stages 3 x 16 KB][B: Npad x 128 B][ccb: Npad] (X stages
+// and B 1024-byte aligned).
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict__ xnorm,
+                   const float* __restrict__ Xf, long long m, int n, const float* __restrict__ C, int k,
+                   int Npad, float tau, int* __restrict__ labels, int* __restrict__ queue, Globals* g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (s_addr(smem_raw) & 1023)) & 1023);
+    unsigned char* xs = base;                                             // stages
+    unsigned char* bs = base + kTcStages * kTcRows * 128;                 // B operand
+    float* ccb = reinterpret_cast<float*>(bs + (size_t)Npad * 128);       // Npad
+    __shared__ __align__(8) unsigned long long bar_x[kTcStages];
+    __shared__ __align__(8) unsigned long long bar_mma;
+    __shared__ unsigned tmem_slot;
+    __shared__ unsigned __int128 red128[kTcThreads / 32];
+    __shared__ unsigned long long red64[kTcThreads / 32];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (g->nonfinite) return;
+
+    // tensor memory: warp 0 allocates and later frees
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) tc_mbar_init(&bar_x[s], 1);
+        tc_mbar_init(&bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // centroids: BF16 B operand (swizzled) and ||c_bf16||^2
+    for (int e = tid; e < Npad * (kTcK / 8); e += kTcThreads) {
+        const int j = e / (kTcK / 8), c = e % (kTcK / 8);
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int d = 8 * c + i;
+            v[i] = __float2bfloat16_rn((j < k && d < n) ? C[(size_t)j * n + d] : 0.f);
+        }
+        const int pc = c ^ (j & 7);
+        *reinterpret_cast<uint4*>(bs + (size_t)j * 128 + 16 * pc) = *reinterpret_cast<const uint4*>(v);
+    }
+    for (int j = tid; j < Npad; j += kTcThreads) {
+        float acc = 0.f;
+        for (int d = 0; d < n && j < k; ++d) {
+            const float b = __bfloat162float(__float2bfloat16_rn(C[(size_t)j * n + d]));
+            acc = __fmaf_rn(b, b, acc);
+        }
+        ccb[j] = (j < k) ? acc : __int_as_float(0x7f800000);   // padded columns never win
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B visible to the tensor core
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_slot;
+
+    const long long ntiles = (m + kTcRows - 1) / kTcRows;
+    const long long grid = gridDim.x;
+    const unsigned tile_bytes = kTcRows * 128;
+    if (tid == 0)
+        for (int s = 0; s < kTcStages; ++s) {
+            const long long t = blockIdx.x + (long long)s * grid;
+            if (t < ntiles) {
+                tc_expect_tx(&bar_x[s], tile_bytes);
+                tc_bulk_g2s(xs + (size_t)s * tile_bytes, Xb + t * kTcRows * kTcK, tile_bytes, &bar_x[s]);
+            }
+        }
+    const unsigned idesc = idesc_bf16_f32(kTcRows, Npad);
+    const long long m_pad = (m + kTcRows - 1) / kTcRows * kTcRows;
+    const Grids gr = grids_from_maxbits(max(g->maxbits, __float_as_uint(xnorm[m_pad])));
+    unsigned __int128 facc = 0;
+    unsigned int inex = 0;
+    bool ok = true;
+    for (long long it = 0;; ++it) {
+        const long long tile = blockIdx.x + it * grid;
+        if (tile >= ntiles) break;
+        const int st = (int)(it % kTcStages);
+        if (tid == 0) {
+            ok &= tc_wait(&bar_x[st], (unsigned)((it / kTcStages) & 1), g);
+            tc_fence_after();
+            const unsigned a0 = s_addr(xs + (size_t)st * tile_bytes), b0 = s_addr(bs);
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 16; ++kk)
+                tc_mma(tmem, smem_desc_sw128(a0 + 32 * kk), smem_desc_sw128(b0 + 32 * kk), idesc, kk > 0);
+            tc_commit(&bar_mma);
+        }
+        // every thread waits for the accumulator of this tile
+        ok &= tc_wait(&bar_mma, (unsigned)(it & 1), g);
+        tc_fence_after();
+        const long long row = tile * kTcRows + warp * 32 + lane;
+        const float xx = row < m ? xnorm[row] : 0.f;
+        float g1 = __int_as_float(0x7f800000), g2 = g1;
+        int j1 = 0;
+        for (int c0 = 0; c0 < Npad; c0 += 16) {
+            float v[16];
+            tc_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float e = __fmaf_rn(-2.f, v[i], ccb[c0 + i]);
+                g2 = fminf(g2, fmaxf(g1, e));
+                j1 = (e < g1) ? (c0 + i) : j1;
+                g1 = fminf(g1, e);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();                    // accumulator read, X stage consumed
+        if (tid == 0) {
+            const long long nt = tile + (long long)kTcStages * grid;
+            if (nt < ntiles) {
+                tc_expect_tx(&bar_x[st], tile_bytes);
+                tc_bulk_g2s(xs + (size_t)st * tile_bytes, Xb + nt * kTcRows * kTcK, tile_bytes, &bar_x[st]);
+            }
+        }
+        // Close calls go to a queue re-scored by rescore_kernel with the
+        // exact definition; the others are final here.
+        const bool close = row < m && !(g2 - g1 >= tau * xx);
+        const unsigned cq = __ballot_sync(0xffffffffu, close);
+        if (cq) {
+            unsigned qbase = 0;
+            if (lane == __ffs(cq) - 1) qbase = atomicAdd(&g->queue_len, (unsigned)__popc(cq));
+            qbase = __shfl_sync(0xffffffffu, qbase, __ffs(cq) - 1);
+            if (close) queue[qbase + __popc(cq & ((1u << lane) - 1u))] = (int)row;
+        }
+        if (row < m && !close) {
+            acc_obj(facc, fmaxf(0.f, xx + g1), gr.gf, inex);
+            if (labels) labels[row] = j1;
+        }
+    }
+    // free tensor memory (every MMA of this CTA completed before its last wait)
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    }
+    // objective: CTA reduction, then the grid-wide total (last CTA rounds it)
+    unsigned __int128 F = warp_sum_u128(facc);
+    const unsigned long long I = warp_sum((unsigned long long)inex);
+    if (lane == 0) { red128[warp] = F; red64[warp] = I; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned __int128 T = 0;
+        unsigned long long in = 0;
+        for (int i = 0; i < kTcThreads / 32; ++i) { T += red128[i]; in += red64[i]; }
+        for (int i = 0; i < 4; ++i) {
+            const unsigned long long chunk = (unsigned long long)((T >> (32 * i)) & 0xffffffffu);
+            if (chunk) atomicAdd(&g->obj_words[i], chunk);
+        }
+        if (in) atomicAdd(&g->inexact, in);
+        if (!ok) atomicOr(&g->err, kErrTimeout);
+    }
+}
+
+// Exact re-score of the queued close calls (FP32 direct form over all k,
+// lowest index on ties), thread per row with the row in registers; adds the
+// rows' distances to the objective words and, in its last CTA, rounds the
+// objective of both kernels once.
+__global__ void __launch_bounds__(256)
+rescore_kernel(const float* __restrict__ Xf, const float* __restrict__ xnorm, long long m, int n,
+               const float* __restrict__ C, int k, const int* __restrict__ queue, int* __restrict__ labels,
+               Globals* g) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float* Cs = reinterpret_cast<float*>(smem_raw);                 // k x 64
+    __shared__ unsigned __int128 red128[8];
+    __shared__ unsigned long long red64[8];
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (g->nonfinite) return;
+    for (int e = tid; e < k * kTcK; e += 256) {
+        const int j = e / kTcK, d = e % kTcK;
+        Cs[e] = d < n ? C[(size_t)j * n + d] : 0.f;
+    }
+    __syncthreads();
+    const long long m_pad = (m + kTcRows - 1) / kTcRows * kTcRows;
+    const Grids gr = grids_from_maxbits(max(g->maxbits, __float_as_uint(xnorm[m_pad])));
+    const long long q = g->queue_len;
+    unsigned __int128 facc = 0;
+    unsigned int inex = 0;
+    for (long long i = (long long)blockIdx.x * 256 + tid; i < q; i += (long long)gridDim.x * 256) {
+        const long long row = queue[i];
+        float x[kTcK];
+        const float* xr = Xf + row * (long long)n;
+#pragma unroll
+        for (int d = 0; d < kTcK; ++d) x[d] = d < n ? xr[d] : 0.f;
+        float best = __int_as_float(0x7f800000);
+        int bj = 0;
+        for (int j = 0; j < k; ++j) {
+            const float* cj = Cs + (size_t)j * kTcK;
+            float acc = 0.f;
+#pragma unroll
+            for (int d = 0; d < kTcK; ++d) {
+                if (d < n) {
+                    const float t = __fsub_rn(x[d], cj[d]);
+                    acc = __fadd_rn(acc, __fmul_rn(t, t));
+                }
+            }
+            if (acc < best) { best = acc; bj = j; }
+        }
+        acc_obj(facc, best, gr.gf, inex);
+        if (labels) labels[row] = bj;
+    }
+    unsigned __int128 F = warp_sum_u128(facc);
+    const unsigned long long I = warp_sum((unsigned long long)inex);
+    if (lane == 0) { red128[warp] = F; red64[warp] = I; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned __int128 T = 0;
+        unsigned long long in = 0;
+        for (int i = 0; i < 8; ++i) { T += red128[i]; in += red64[i]; }
+        for (int i = 0; i < 4; ++i) {
+            const unsigned long long chunk = (unsigned long long)((T >> (32 * i)) & 0xffffffffu);
+            if (chunk) atomicAdd(&g->obj_words[i], chunk);
+        }
+        if (in) atomicAdd(&g->inexact, in);
+        __threadfence();
+        last = (atomicAdd(&g->done_ctas, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        unsigned __int128 T = 0;
+        for (int i = 0; i < 4; ++i) {
+            T += (unsigned __int128)atomicAdd(&g->obj_words[i], 0ull) << (32 * i);
+            g->obj_words[i] = 0;
+        }
+        g->f_full = u128_to_double(T, gr.gf);
+        g->rescored += (unsigned long long)q;
+        g->done_ctas = 0;
+    }
+}
+
+// ------------------------------------------------------------ launchers
+size_t tc_smem_bytes(int k, int Npad) {
+    return 1024 + (size_t)kTcStages * kTcRows * 128 + (size_t)Npad * 128 + (size_t)Npad * 4;
+}
+
+cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad, void* Xb, float* norms,
+                             cudaStream_t st) {
+    const long long total = m_pad * (kTcK / 8);
+    const int grid = (int)std::min<long long>(8192, (total + 255) / 256);
+    cudaError_t e = cudaMemsetAsync(norms + m_pad, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    pack_bf16_kernel<<<grid, 256, 0, st>>>(X, m, n, m_pad, (__nv_bfloat16*)Xb, norms);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
+                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, int sms,
+                               cudaStream_t st) {
+    const int Npad = (k + 15) & ~15;
+    // at least 80 KB so that at most two CTAs (2 x 256 tensor-memory
+    // columns = all 512) share an SM and no allocation has to wait
+    const size_t smem = std::max<size_t>(tc_smem_bytes(k, Npad), 80 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(tc_fullpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fullpass_kernel, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, 512 / kTcTmemCols));     // tensor-memory columns per SM
+    const long long tiles = (m + kTcRows - 1) / kTcRows;
+    const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * per_sm, tiles));
+    tc_fullpass_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>((const __nv_bfloat16*)Xb, xnorm, Xf, m, n, C, k,
+                                                                 Npad, tau, labels, queue, g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t rs = (size_t)k * kTcK * 4;
+    e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+    if (e != cudaSuccess) return e;
+    rescore_kernel<<<sms * 4, 256, rs, st>>>(Xf, xnorm, m, n, C, k, queue, labels, g);
+    return cudaGetLastError();
+}
+
+}  // namespace bm

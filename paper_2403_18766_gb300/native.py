@@ -81,6 +81,9 @@ SIGNATURES = {
                         ctypes.POINTER(_i32), _p, _p]),
     "bm_assign": (_i32, [_p, _i64, _i32, _p, _i32, _p, ctypes.POINTER(_dbl), _RP, _p]),
     "bm_assign_noalloc": (_i32, [_p, _i64, _i32, _p, _i32, _p, ctypes.POINTER(_dbl), _p]),
+    "bm_pack_bf16": (_i32, [_p, _i64, _i32, _p, _p, _p]),
+    "bm_assign_bf16": (_i32, [_p, _p, _p, _i64, _i32, _p, _i32, ctypes.c_float, _p,
+                              ctypes.POINTER(_dbl), _RP, _p]),
     "bm_last_error": (ctypes.c_char_p, []),
     "bm_version": (ctypes.c_char_p, []),
 }
@@ -256,6 +259,34 @@ def assign_noalloc(X, C, labels=True, stream=None):
     _check(lib.bm_assign_noalloc(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(Y),
                                  ctypes.byref(f), _stream(stream)))
     return Y, f.value
+
+
+class PackedBF16:
+    """X packed for the tensor-core full pass (bm_pack_bf16); keeps the FP32 master."""
+
+    def __init__(self, X, stream=None):
+        self.X = _dev_f32(X, "X")
+        m, n = self.X.shape
+        m_pad = (m + 127) // 128 * 128
+        # 1024-byte aligned buffer carved from a larger allocation
+        self._raw = torch.empty(m_pad * 128 + 1024, dtype=torch.uint8, device=self.X.device)
+        off = (-self._raw.data_ptr()) % 1024
+        self.Xb = self._raw[off:off + m_pad * 128]
+        self.norms = torch.empty(m_pad + 1, dtype=torch.float32, device=self.X.device)
+        _check(lib.bm_pack_bf16(_ptr(self.X), m, n, _ptr(self.Xb), _ptr(self.norms), _stream(stream)))
+
+
+def assign_bf16(packed, C, tau=1e-3, labels=True, stream=None):
+    """bm_assign_bf16: precision-form full pass on tensor cores."""
+    C = _dev_f32(C, "C")
+    X = packed.X
+    Y = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) if labels else None
+    f = ctypes.c_double(0)
+    rep = Report()
+    _check(lib.bm_assign_bf16(_ptr(packed.Xb), _ptr(packed.norms), _ptr(X), X.shape[0], X.shape[1],
+                              _ptr(C), C.shape[0], float(tau), _ptr(Y), ctypes.byref(f),
+                              ctypes.byref(rep), _stream(stream)))
+    return Y, f.value, rep.as_dict()
 
 
 def version():

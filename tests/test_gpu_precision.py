@@ -1,0 +1,111 @@
+"""GPU tests of the precision form: BF16 pack and the tensor-core full pass.
+
+* the packed rows are torch's round-to-nearest bfloat16 of X, in the
+  documented swizzled layout, and the norms are fl(sum bf16(x)^2);
+* tau = inf re-scores every row with the exact FP32 definition, so labels and
+  f equal bm_assign bit for bit (checks the bookkeeping of the kernel);
+* tau = 0 takes every label from the tensor cores: they must equal the argmin
+  of a bfloat16 / FP32-accumulate reference except where two centroids are
+  within the accumulation error (checks descriptors, swizzle, TMEM reads);
+* the default tau = 1e-3 agrees with the exact pass on all but near ties and
+  reports how far its objective is from the exact one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import kmeans as okm  # noqa: E402
+from paper_2403_18766_gb300 import native  # noqa: E402
+from paper_2403_18766_gb300.synthetic import gaussian_mixture  # noqa: E402
+
+
+def _case(m, n, k, seed, components=None):
+    X = gaussian_mixture(m, n, components or max(2, k // 2), seed=seed)
+    C = X[np.random.default_rng(seed).integers(0, m, k)].copy()
+    return torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+
+
+def _unswizzle(Xb_bytes, m):
+    rows = Xb_bytes.view(torch.int16).view(-1, 64).cpu().numpy()
+    out = np.empty_like(rows)
+    r = np.arange(rows.shape[0])[:, None]
+    for c in range(8):
+        pc = c ^ (r & 7)
+        out[:, 8 * c:8 * c + 8] = np.take_along_axis(rows, (8 * pc + np.arange(8)[None, :]), axis=1)
+    return out[:m]
+
+
+@pytest.mark.parametrize("m,n", [(1000, 64), (333, 17), (129, 8), (5000, 3)])
+def test_pack_bf16_layout_and_norms(m, n):
+    X, _ = _case(m, n, 2, m + n)
+    P = native.PackedBF16(X)
+    ref = torch.zeros(m, 64, dtype=torch.bfloat16)
+    ref[:, :n] = X.cpu().to(torch.bfloat16)
+    got = _unswizzle(P.Xb, m)
+    assert np.array_equal(got, ref.view(torch.int16).numpy())
+    b = X.cpu().to(torch.bfloat16).float().numpy()
+    norms = np.zeros(m, np.float32)
+    for d in range(n):                                   # FMA chain in FP32, ascending d
+        norms = (norms.astype(np.float64) + b[:, d].astype(np.float64) ** 2).astype(np.float32)
+    np.testing.assert_allclose(P.norms[:m].cpu().numpy(), norms, rtol=2e-6, atol=1e-6)
+    m_pad = (m + 127) // 128 * 128
+    assert torch.all(P.norms[m:m_pad] == 0)
+    assert P.norms[m_pad].item() == X.abs().max().item()
+
+
+CASES = [(100_003, 64, 100), (5000, 40, 17), (384, 16, 256), (1000, 8, 3), (70_001, 16, 25)]
+
+
+@pytest.mark.parametrize("m,n,k", CASES)
+def test_tau_inf_is_the_exact_pass(m, n, k):
+    X, C = _case(m, n, k, 7 * m + k)
+    P = native.PackedBF16(X)
+    Y, f, rep = native.assign_bf16(P, C, tau=math.inf)
+    Yr, fr, _ = native.assign(X, C)
+    assert torch.equal(Y, Yr)
+    assert f == fr
+    assert rep["rescored_rows"] == m
+
+
+@pytest.mark.parametrize("m,n,k", CASES)
+def test_tau0_labels_come_from_the_tensor_cores(m, n, k):
+    X, C = _case(m, n, k, 11 * m + k)
+    P = native.PackedBF16(X)
+    Y, f, rep = native.assign_bf16(P, C, tau=0.0)
+    assert rep["rescored_rows"] == 0
+    xb = X.to(torch.bfloat16).float()
+    cb = C.to(torch.bfloat16).float()
+    dot = xb.double() @ cb.double().T                    # exact products, FP64 sum
+    g = (cb.double() ** 2).sum(1)[None, :] - 2 * dot
+    top2 = torch.topk(g, 2, dim=1, largest=False)
+    lab = top2.indices[:, 0].int()
+    gap = top2.values[:, 1] - top2.values[:, 0]
+    scale = (xb.double().abs() @ cb.double().abs().T).max(1).values   # sum |x_d c_d| bound
+    clear = gap > 1e-4 * scale + 1e-6                    # far above FP32 accumulation error
+    assert clear.float().mean() > 0.5
+    assert torch.equal(Y[clear], lab[clear])
+
+
+@pytest.mark.parametrize("m,n,k", CASES)
+def test_default_tau_matches_exact_labels_except_near_ties(m, n, k):
+    X, C = _case(m, n, k, 13 * m + k)
+    P = native.PackedBF16(X)
+    Y, f, rep = native.assign_bf16(P, C, tau=1e-3)
+    Yr, fr, _ = native.assign(X, C)
+    mism = (Y != Yr).nonzero().flatten()
+    assert mism.numel() <= max(3, m // 100)
+    if mism.numel():
+        rows = mism.cpu().numpy()
+        Xn, Cn = X.cpu().numpy(), C.cpu().numpy()
+        D = okm.d32_all(Xn[rows], Cn)
+        srt = np.sort(D, axis=1)
+        xx = (Xn[rows].astype(np.float64) ** 2).sum(1)
+        assert np.all(srt[:, 1] - srt[:, 0] < 0.05 * xx + 1.0)   # only close calls differ
+    assert abs(f - fr) <= 5e-3 * fr
