@@ -278,6 +278,24 @@ bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const floa
                             int32_t k, int32_t* labels_out_dev, double* f_out_host,
                             void* stream);
 
+/* ---------------------------------------------------------------------------
+ * bm_set_fullpass_impl / bm_last_fullpass_impl -- choice of implementation
+ * for the full-data pass of Eq. (1) (bm_assign, bm_assign_noalloc and the
+ * full passes inside a fit).  Both implementations give identical labels and
+ * f (the same FP32 direct-form definition, certified).
+ *   impl 0 (default): the tensor-core pass (tcgen05, TF32 products of the
+ *          expanded form, certified, uncertain rows re-scored in FP32) where
+ *          it applies -- n % 4 == 0, X 16-byte aligned, k <= 256 -- else
+ *          the FP32-ALU pass;
+ *   impl 1: always the FP32-ALU pass.
+ * Any other value is rejected with BM_EINVAL.  The setting is process-wide;
+ * change it only while no call of this library is running.
+ * bm_last_fullpass_impl returns which one the last full pass launched by the
+ * calling thread used: 2 = tensor cores, 1 = FP32 ALU, 0 = none yet.
+ * ------------------------------------------------------------------------- */
+bm_status bm_set_fullpass_impl(int32_t impl);
+int32_t bm_last_fullpass_impl(void);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char* bm_last_error(void);
 

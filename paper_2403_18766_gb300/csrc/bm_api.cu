@@ -43,6 +43,10 @@ cudaError_t launch_globaltimer(unsigned long long* out, cudaStream_t st);
 size_t tc_smem_bytes(int k, int Npad);
 cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad, void* Xb, float* norms,
                              cudaStream_t st);
+void set_fullpass_impl(int impl);
+int last_fullpass_impl();
+int fullpass_impl_setting();
+bool tcx_eligible(const float* X, long long m, int n, int np, int k);
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
                                const float* C, int k, float tau, int* labels, int* queue, Globals* g, int sms,
                                cudaStream_t st);
@@ -510,6 +514,13 @@ bm_status run_fullpass(bm_fit_ctx* c, const double* sel, int* labels, int incumb
 extern "C" {
 
 const char* bm_last_error(void) { return g_err.c_str(); }
+
+bm_status bm_set_fullpass_impl(int32_t impl) {
+    if (impl != 0 && impl != 1) return fail(BM_EINVAL, "fullpass impl = %d must be 0 or 1", impl);
+    set_fullpass_impl(impl);
+    return BM_OK;
+}
+int32_t bm_last_fullpass_impl(void) { return last_fullpass_impl(); }
 const char* bm_version(void) { return "bigmeans-gb300 0.1 (sm_103a)"; }
 
 bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
@@ -855,7 +866,8 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
     cudaStream_t sm = (cudaStream_t)stream;
     const int np = padded_dim(n);
     const size_t smem = fullpass_smem_bytes(np, k, n);
-    if (smem > kSmemLimit) return fail(BM_EINVAL, "k too large for the full pass");
+    if (smem > kSmemLimit && !(fullpass_impl_setting() == 0 && tcx_eligible(X_dev, m, n, np, k)))
+        return fail(BM_EINVAL, "k too large for the full pass");
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
     CU(cudaMallocAsync(&base, gb + (size_t)k * np * 4, sm));

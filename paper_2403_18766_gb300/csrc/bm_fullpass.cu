@@ -8,6 +8,7 @@
 // point.  CTA partials go to global memory as 32-bit chunks added into four
 // 64-bit words; the last CTA to finish rounds the total once to double.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "bm_device.cuh"
@@ -353,9 +354,30 @@ static cudaError_t launch_fullpass_t(const float* X, long long m, int n, const f
     return cudaGetLastError();
 }
 
+cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
+                                const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
+                                int incumbent, int sms, cudaStream_t st);
+
+// Which implementation full passes use: 0 = the tensor-core pass where it
+// applies, else the FP32-ALU pass; 1 = always the FP32-ALU pass.  Both give
+// identical labels and objective (same definition, certified).
+static std::atomic<int> g_fullpass_impl{0};
+static thread_local int g_last_impl = 0;
+void set_fullpass_impl(int impl) { g_fullpass_impl.store(impl); }
+int last_fullpass_impl() { return g_last_impl; }
+int fullpass_impl_setting() { return g_fullpass_impl.load(); }
+
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int sms, cudaStream_t st) {
+    if (g_fullpass_impl.load() == 0) {
+        const cudaError_t e = launch_tcx_fullpass(np, X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
+        if (e != cudaErrorNotSupported) {
+            g_last_impl = 2;
+            return e;
+        }
+    }
+    g_last_impl = 1;
     switch (np) {
         case 4: return launch_fullpass_t<4>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
         case 8: return launch_fullpass_t<8>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);

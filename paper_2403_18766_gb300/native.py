@@ -84,6 +84,8 @@ SIGNATURES = {
     "bm_pack_bf16": (_i32, [_p, _i64, _i32, _p, _p, _p]),
     "bm_assign_bf16": (_i32, [_p, _p, _p, _i64, _i32, _p, _i32, ctypes.c_float, _p,
                               ctypes.POINTER(_dbl), _RP, _p]),
+    "bm_set_fullpass_impl": (_i32, [_i32]),
+    "bm_last_fullpass_impl": (_i32, []),
     "bm_last_error": (ctypes.c_char_p, []),
     "bm_version": (ctypes.c_char_p, []),
 }
@@ -247,6 +249,16 @@ def assign(X, C, labels=True, stream=None):
     _check(lib.bm_assign(_ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(Y),
                          ctypes.byref(f), ctypes.byref(rep), _stream(stream)))
     return Y, f.value, rep.as_dict()
+
+
+def set_fullpass_impl(impl):
+    """bm_set_fullpass_impl: 0 = tensor-core full pass where it applies, 1 = FP32-ALU pass."""
+    _check(lib.bm_set_fullpass_impl(int(impl)))
+
+
+def last_fullpass_impl():
+    """bm_last_fullpass_impl: 2 = tensor cores, 1 = FP32 ALU, 0 = none yet (this thread)."""
+    return int(lib.bm_last_fullpass_impl())
 
 
 def assign_noalloc(X, C, labels=True, stream=None):
