@@ -305,25 +305,40 @@ def run_kernel_mode(args):
     import torch
     from paper_2403_18766_gb300 import native
     from paper_2403_18766_gb300.synthetic import workload
-    X = workload(WORKLOAD)
+    name = args.workload or WORKLOAD
+    X = workload(name, m=args.rows)
     Xd = torch.from_numpy(X).cuda()
-    C = Xd[torch.arange(0, X.shape[0], X.shape[0] // K_CLUSTERS)[:K_CLUSTERS].cuda()].contiguous()
+    kc = args.k or K_CLUSTERS
+    if args.centroids == "fit":      # centroids as a fit leaves them (close calls between split clusters)
+        C, _, _ = native.fit(Xd, kc, native.make_policy(s_min=20000, s_max=60000, workers=8, passes=4),
+                             native.make_budget(rounds=1), seed=3, labels=False)
+    else:
+        C = Xd[torch.arange(0, X.shape[0], X.shape[0] // kc)[:kc].cuda()].contiguous()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     S = Xd[:POLICY["s_max"]].contiguous()
-    times = []
+    times, kern, resc = [], [], 0
     for i in range(args.warmup + args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if args.mode == "fullpass":
-            native.assign(Xd, C)
+            _, _, rep = native.assign(Xd, C)
         else:
             native.lloyd(S, C, 20, -1.0)
         torch.cuda.synchronize()
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
-    print(json.dumps({"mode": args.mode, "median_ms": statistics.median(times) * 1e3,
-                      "note": "wall time of the whole call (allocation, staging, prepass included)"}))
+            if args.mode == "fullpass":
+                kern.append(rep["t_fullpass_s"])
+                resc = rep["rescored_rows"]
+    out = {"mode": args.mode, "median_ms": statistics.median(times) * 1e3,
+           "note": "wall time of the whole call (allocation, staging, prepass included)"}
+    if kern:
+        m, n = X.shape
+        out.update({"kernel_median_ms": statistics.median(kern) * 1e3,
+                    "kernel_GBps": m * (n * 4 + 4) / statistics.median(kern) / 1e9,
+                    "impl": native.last_fullpass_impl(), "rescored_rows": resc})
+    print(json.dumps(out))
     return 0
 
 
@@ -380,6 +395,9 @@ def run_precision(args):
             "ms_per_call": t_bf * 1e3, "exact_fp32_ms_per_call": t_ex * 1e3,
             "tau0_ms_per_call": t_tc0 * 1e3, "tau0_GBps": bytes_bf / t_tc0 / 1e9,
             "speedup_vs_exact_pass": t_ex / t_bf,
+            "exact_kernel_ms": re_["t_fullpass_s"] * 1e3,
+            "exact_kernel_GBps": m * (n * 4 + 4) / re_["t_fullpass_s"] / 1e9,
+            "exact_rescored_rows": re_["rescored_rows"],
             "rescored_rows": rb["rescored_rows"],
             "label_mismatch_vs_exact": int((Yb != Ye).sum().item()),
             "f_rel_err_vs_exact": abs(fb - fe) / fe, "f_precision": fb, "f_exact": fe}
@@ -394,6 +412,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=None, help="kernel modes: workload name (default: the headline's)")
+    ap.add_argument("--rows", type=int, default=None, help="kernel modes: rows of the workload to use")
+    ap.add_argument("--k", type=int, default=None, help="kernel modes: number of centroids")
+    ap.add_argument("--centroids", choices=["rows", "fit"], default="rows",
+                    help="kernel modes: centroids from evenly spaced rows, or from a short fit")
     ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision"], default="fit",
                     help="fit: the headline benchmark; fullpass / lloyd: one kernel family, "
                          "for profiling")

@@ -214,7 +214,9 @@ bm_status bm_lloyd(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev,
                    int32_t* iters_out_host, uint8_t* empty_out_dev, void* stream);
 
 /* a9 -- full-data pass (Alg. 1 last step; Eq. 1): labels of every row of X
- * and f(C, X).  labels_out_dev may be NULL.  *f_out_host receives f. */
+ * and f(C, X).  labels_out_dev may be NULL.  *f_out_host receives f.  When
+ * report_out is given it receives f, the re-scored row count and, in
+ * t_fullpass_s, the device time of the pass kernel alone (CUDA events). */
 bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev,
                     int32_t k, int32_t* labels_out_dev, double* f_out_host,
                     bm_report* report_out, void* stream);

@@ -875,20 +875,35 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
     float* Cp = (float*)((char*)base + gb);
     float gB, gp2;
     cert_constants(np, gB, gp2);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (rep) {
+        CU(cudaEventCreate(&ev[0]));
+        CU(cudaEventCreate(&ev[1]));
+    }
     cudaError_t e;
     if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
         (e = launch_pad(C_dev, k, n, np, Cp, sm)) ||
         (e = launch_prepass(X_dev, m * n, g, 2 * sm_count(), sm)) ||
         (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
-        (e = launch_fullpass(np, X_dev, m, n, Cp, k, nullptr, 1, labels_out_dev, g, gB, gp2, 0, sm_count(), sm))) {
+        (ev[0] && (e = cudaEventRecord(ev[0], sm))) ||
+        (e = launch_fullpass(np, X_dev, m, n, Cp, k, nullptr, 1, labels_out_dev, g, gB, gp2, 0, sm_count(), sm)) ||
+        (ev[1] && (e = cudaEventRecord(ev[1], sm)))) {
         cudaFreeAsync(base, sm);
         cudaStreamSynchronize(sm);
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
         return fail(BM_ECUDA, "full pass launch: %s", cudaGetErrorString(e));
     }
     Globals h;
     e = cudaMemcpyAsync(&h, g, sizeof(Globals), cudaMemcpyDeviceToHost, sm);
     cudaFreeAsync(base, sm);
     const cudaError_t e2 = cudaStreamSynchronize(sm);
+    float ms = 0.f;
+    if (ev[0]) {
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
     if (e != cudaSuccess || e2 != cudaSuccess)
         return fail(BM_ECUDA, "full pass: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     if ((st = status_from_flags(h))) return st;
@@ -899,6 +914,8 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
         rep->f_incumbent = h.f_full;
         rep->rescored_rows = (int64_t)h.rescored;
         rep->inexact_terms = (int64_t)h.inexact;
+        rep->t_fullpass_s = ms * 1e-3;
+        rep->fullpass_launches = 1;
     }
     return BM_OK;
 }

@@ -233,11 +233,17 @@ struct CertC { float cmax2, cmax; };
 // fl(||c||^2 + sum(-2 x_d) c_d) over centroids; xn2 >= ||x||^2, xn >= ||x||.
 // gB >= gamma_{2NP+2}, gp2 >= 2 (1 + 2^-14) gamma_{NP+2}.  Returns true when
 // the argmin of the FP32 direct-form distances is certainly the index of g1.
-__device__ __forceinline__ bool certified(float g1, float g2, float xn2, float xn,
-                                          const CertC& cc, float gB, float gp2) {
+// Threshold of the certificate: any centroid j with fl_rd(g_j - g1) > thr has
+// a larger FP32 direct-form distance than the centroid of g1.
+__device__ __forceinline__ float cert_threshold(float g1, float xn2, float xn, const CertC& cc, float gB,
+                                                float gp2) {
     const float B = __fmul_ru(gB, __fadd_ru(cc.cmax2, __fmul_ru(2.f, __fmul_ru(xn, cc.cmax))));
     const float d1 = fmaxf(0.f, __fadd_ru(__fadd_ru(g1, B), xn2));
-    const float thr = __fadd_ru(__fmul_ru(2.f, B), __fmul_ru(gp2, d1));
+    return __fadd_ru(__fmul_ru(2.f, B), __fmul_ru(gp2, d1));
+}
+__device__ __forceinline__ bool certified(float g1, float g2, float xn2, float xn,
+                                          const CertC& cc, float gB, float gp2) {
+    const float thr = cert_threshold(g1, xn2, xn, cc, gB, gp2);
     const float gap = __fsub_rd(g2, g1);
     return gap > thr;                     // false for NaN; +inf gap (k = 1) passes
 }

@@ -8,24 +8,38 @@
 //
 //   * X (FP32, row-major, n % 4 == 0) is read by 2-D TMA copies into 128-row
 //     tiles in the 128-byte-swizzle K-major layout (32 floats per row and
-//     atom; columns past n are filled with zeros by the copy);
-//   * one tcgen05.mma kind::tf32 chain per tile computes acc_j = x.c_j for
-//     all centroids into a tensor-memory accumulator (two accumulators, so
-//     the MMA of tile t+1 overlaps the epilogue of tile t);
+//     column block; columns past n are zero-filled by the copy);
+//   * split TF32: every x is split into hi = trunc_tf32(x) (exact in TF32,
+//     written over the tile in place) and the residual r = x - hi (exact in
+//     FP32, written to a second tile), every c likewise; one tile of 128
+//     rows takes the MMAs r(x).hi(c) and hi(x).r(c) first, then
+//     hi(x).hi(c), all accumulated in FP32 in tensor memory
+//     (tcgen05.mma kind::tf32, M = 128, N = k rounded up to 16, K = 8 per
+//     instruction).  x = hi + r exactly, so the epilogue rebuilds the FP32
+//     row from the two tiles;
 //   * the epilogue forms g_j = fl(||c_j||^2 - 2 acc_j), keeps the two least,
 //     and accepts j1 when the certificate of the expanded form holds with
-//     the TF32 error added to its bound (below); the distance of the row is
-//     then d32(x, c_j1).  Rows whose certificate fails are re-scored by the
-//     warp over all centroids in d32.
+//     the split-TF32 error in its bound; the distance of the row is then
+//     d32(x, c_j1).  Rows whose certificate fails are re-scored by the warp
+//     over all centroids in d32 (lowest index on ties).
 //
-// Error bound behind the certificate: the tensor core reads x with at most
-// 10 mantissa bits (|x~ - x| <= 2^-10 |x|), C is rounded to TF32 here
-// (|c~ - c| <= 2^-11 |c|), products of TF32 values are exact in FP32, and
-// the FP32 accumulation of at most 64 products adds far less than
-// 2^-12 sum |x c|.  So |acc_j - x.c_j| <= 1.75 * 2^-10 ||x|| ||c_j|| and
-// |g_j - (||c_j||^2 - 2 x.c_j)| <= 2^-9 (cmax^2 + 2 ||x|| cmax), which is the
-// form certified() takes with its gamma factor set to 2^-9.  A gap below
+// Error of acc_j against x.c_j (exact reals): the tensor core reads the
+// residuals with at most 10 mantissa bits (|r~ - r| <= 2^-10 |r|, whether it
+// truncates or rounds), and |r| <= 2^-10 |x|, so the representation error is
+// at most |r~(x) - r(x)| |c| + |x| |r~(c) - r(c)| + |r(x)| |r(c)|
+// <= 3 * 2^-20 |x| |c| per term; products of TF32 values are exact in FP32.  The accumulation is taken to add at most (K + 1) 2^-23 of the
+// magnitude accumulated so far per MMA instruction (products aligned and
+// truncated once against the largest term, then added to the accumulator):
+// at most ksteps * 9 * 2^-23 sum |x c| over the hi.hi instructions, and far
+// less over the small correction terms issued first.  The host passes the
+// certificate factor gB = 2 (ksteps * 9 * 2^-23) + 8 * 2^-20, which bounds
+// |g_j - (||c_j||^2 - 2 x.c_j)| by gB (cmax^2 + 2 ||x|| cmax).  A gap below
 // 2^-60 is never accepted (subnormal data).
+//
+// CTA roles: warp 8 issues the TMA copies, warp 9 the MMAs; warps 0-7 form
+// two epilogue warpgroups, warpgroup b taking the tiles it == b (mod 2) with
+// tensor-memory accumulator b and its own lo(x) buffer, so the MMA of one
+// tile overlaps the epilogue of the other.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -38,38 +52,78 @@
 
 namespace bm {
 
-constexpr int kTxRows = 128;              // rows per tile (MMA M)
-constexpr int kTxAtomBytes = kTxRows * 128;   // one 32-float-wide column block of a tile
-constexpr int kTxEpiWarps = 4;            // epilogue warps (TMEM lane quarters)
-constexpr int kTxThreads = 32 * (kTxEpiWarps + 2);   // + producer warp + MMA warp
+constexpr int kTxRows = 128;                  // rows per tile (MMA M)
+constexpr int kTxAtomBytes = kTxRows * 128;   // one 32-float column block of a tile
+constexpr int kTxEpiWarps = 8;                // two epilogue warpgroups
+constexpr int kTxProducer = kTxEpiWarps, kTxMma = kTxEpiWarps + 1;
+constexpr int kTxThreads = 32 * (kTxEpiWarps + 2);
+constexpr int kTxMaxStages = 4;
+constexpr int kTxPairs = 64;                  // candidate pairs per warp and tile
 
 struct TxShape {
     int atoms;       // 32-float column blocks per row (1 or 2)
-    int ksteps;      // MMA instructions per tile (K = 8 each)
+    int ksteps;      // K = 8 steps per operand pair
     int Npad;        // MMA N: k rounded up to 16
     int acc_stride;  // tensor-memory columns per accumulator
     int tmem_cols;   // columns allocated
     int stages;      // X tiles in flight
 };
 
-// Shared memory: [X stages: stages x atoms x 16 KB][B: atoms x Npad x 128 B]
-// [CC: Npad floats]; X stages and B 1024-byte aligned.
+// Shared memory (1024-byte aligned pieces):
+//   [X stages: stages x atoms x 16 KB][r(x): 2 x atoms x 16 KB]
+//   [hi(c), r(c): 2 x atoms x Npad x 128 B][CC: Npad floats]
 __host__ __device__ inline size_t tx_smem_bytes(const TxShape& s) {
-    return 1024 + (size_t)s.stages * s.atoms * kTxAtomBytes + (size_t)s.atoms * s.Npad * 128 + (size_t)s.Npad * 4;
+    return 1024 + (size_t)(s.stages + 2) * s.atoms * kTxAtomBytes + (size_t)2 * s.atoms * s.Npad * 128 +
+           (size_t)s.Npad * 4;
+}
+
+__device__ __forceinline__ float trunc_tf32(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
+
+// Byte offset of the 16-byte chunk holding elements 4 q .. 4 q + 3 of row r in
+// a tile of 32-float column blocks (128-byte swizzle).
+__device__ __forceinline__ unsigned tile_off(int r, int q) {
+    return (unsigned)((q >> 3) * kTxAtomBytes + r * 128 + (((q & 7) ^ (r & 7)) << 4));
+}
+
+// d32 of row rr of a tile against centroid j, both rebuilt as hi + r from
+// their two swizzled tiles (exact: the parts do not overlap).  The X tiles
+// have 32-float column blocks of 16 KB, the centroid tiles of Npad x 128 B.
+template <int NP>
+__device__ __forceinline__ float d32_split(const unsigned char* xh, const unsigned char* xr, int rr,
+                                           const unsigned char* ch, const unsigned char* cr, int j,
+                                           unsigned cstride) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+        const unsigned xo = tile_off(rr, q);
+        const unsigned co = (unsigned)(q >> 3) * cstride + (unsigned)j * 128 + (unsigned)(((q & 7) ^ (j & 7)) << 4);
+        const float4 h = *reinterpret_cast<const float4*>(xh + xo);
+        const float4 l = *reinterpret_cast<const float4*>(xr + xo);
+        const float4 a = *reinterpret_cast<const float4*>(ch + co);
+        const float4 b = *reinterpret_cast<const float4*>(cr + co);
+        float t;
+        t = __fsub_rn(__fadd_rn(h.x, l.x), __fadd_rn(a.x, b.x)); acc = __fadd_rn(acc, __fmul_rn(t, t));
+        t = __fsub_rn(__fadd_rn(h.y, l.y), __fadd_rn(a.y, b.y)); acc = __fadd_rn(acc, __fmul_rn(t, t));
+        t = __fsub_rn(__fadd_rn(h.z, l.z), __fadd_rn(a.z, b.z)); acc = __fadd_rn(acc, __fmul_rn(t, t));
+        t = __fsub_rn(__fadd_rn(h.w, l.w), __fadd_rn(a.w, b.w)); acc = __fadd_rn(acc, __fmul_rn(t, t));
+    }
+    return acc;
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kTxThreads, 2)
+__global__ void __launch_bounds__(kTxThreads, 1)
 tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const float* __restrict__ Cw, int k,
                     const double* sel_f, int W, int* __restrict__ labels, Globals* g, float gB, float gp2,
                     int incumbent, TxShape sh) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (tc::s_addr(smem_raw) & 1023)) & 1023);
-    unsigned char* xs = base;
-    unsigned char* bs = xs + (size_t)sh.stages * sh.atoms * kTxAtomBytes;
-    float* CC = reinterpret_cast<float*>(bs + (size_t)sh.atoms * sh.Npad * 128);
-    constexpr int kMaxStages = 4;
-    __shared__ __align__(8) unsigned long long full[kMaxStages], empty[kMaxStages], accf[2], acce[2];
+    const size_t tile_bytes = (size_t)sh.atoms * kTxAtomBytes;
+    unsigned char* xs = base;                                      // X stages
+    unsigned char* xl = xs + (size_t)sh.stages * tile_bytes;       // r(x), 2 buffers
+    unsigned char* bh = xl + 2 * tile_bytes;                       // hi(c)
+    unsigned char* bl = bh + (size_t)sh.atoms * sh.Npad * 128;     // r(c)
+    float* CC = reinterpret_cast<float*>(bl + (size_t)sh.atoms * sh.Npad * 128);
+    __shared__ __align__(8) unsigned long long full[kTxMaxStages], empty[kTxMaxStages], conv[2], accf[2];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
     __shared__ unsigned __int128 red128[kTxThreads / 32];
@@ -78,6 +132,8 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     __shared__ CertC cert;
     __shared__ int wsel;
     __shared__ bool last;
+    __shared__ unsigned pairs[kTxEpiWarps][kTxPairs];               // candidate (lane, j) per warp
+    __shared__ unsigned long long pkeys[kTxEpiWarps][32];           // (d32 bits, j) minimum per row
 
     if (g->nonfinite) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -89,25 +145,28 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 if (sel_f[w] < sel_f[best]) best = w;
         wsel = best;
         abort_flag = 0;
-        for (int s = 0; s < sh.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], kTxEpiWarps); }
-        for (int b = 0; b < 2; ++b) { tc::mbar_init(&accf[b], 1); tc::mbar_init(&acce[b], kTxEpiWarps); }
+        for (int s = 0; s < sh.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 4); }
+        for (int b = 0; b < 2; ++b) { tc::mbar_init(&conv[b], 4); tc::mbar_init(&accf[b], 1); }
         tc::mbar_init_fence();
     }
-    if (warp == kTxEpiWarps + 1) tc::tmem_alloc(&tmem_slot, (unsigned)sh.tmem_cols);
+    if (warp == kTxMma) tc::tmem_alloc(&tmem_slot, (unsigned)sh.tmem_cols);
     __syncthreads();
     const float* C = Cw + (long long)wsel * k * NP;
 
-    // B operand: TF32-rounded centroids, swizzled like the X tiles; CC and
-    // the certificate constants from the FP32 centroids.
+    // B operands hi(c), r(c) (swizzled like the X tiles); CC and the
+    // certificate constants from the FP32 centroids.
     for (int e = tid; e < sh.atoms * sh.Npad * 8; e += kTxThreads) {
         const int a = e / (sh.Npad * 8), rem = e % (sh.Npad * 8), j = rem >> 3, c = rem & 7;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
         const int d0 = a * 32 + c * 4;
         if (j < k && d0 < NP) {
             const float4 cv = *reinterpret_cast<const float4*>(C + (size_t)j * NP + d0);
-            v = make_float4(tc::to_tf32(cv.x), tc::to_tf32(cv.y), tc::to_tf32(cv.z), tc::to_tf32(cv.w));
+            h = make_float4(trunc_tf32(cv.x), trunc_tf32(cv.y), trunc_tf32(cv.z), trunc_tf32(cv.w));
+            l = make_float4(cv.x - h.x, cv.y - h.y, cv.z - h.z, cv.w - h.w);     // exact
         }
-        *reinterpret_cast<float4*>(bs + (size_t)a * sh.Npad * 128 + (size_t)j * 128 + ((c ^ (j & 7)) << 4)) = v;
+        const size_t off = (size_t)a * sh.Npad * 128 + (size_t)j * 128 + ((c ^ (j & 7)) << 4);
+        *reinterpret_cast<float4*>(bh + off) = h;
+        *reinterpret_cast<float4*>(bl + off) = l;
     }
     unsigned int mx = 0;
     for (int j = tid; j < sh.Npad; j += kTxThreads) {
@@ -126,7 +185,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if (lane == 0) redu[warp] = mx;
-    tc::fence_proxy_async();                 // B visible to the tensor core
+    tc::fence_proxy_async();                 // B operands visible to the tensor core
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -144,7 +203,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
 
     unsigned __int128 facc = 0;
     unsigned int inex = 0, resc = 0;
-    if (warp == kTxEpiWarps) {
+    if (warp == kTxProducer) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             long long it = 0;
@@ -153,64 +212,101 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 if (tile >= ntiles) break;
                 const int s = (int)(it % S);
                 if (it >= S && !tc::wait(&empty[s], (unsigned)((it / S - 1) & 1), abort, g)) break;
-                tc::expect_tx(&full[s], (unsigned)(sh.atoms * kTxAtomBytes));
+                tc::expect_tx(&full[s], (unsigned)tile_bytes);
                 for (int a = 0; a < sh.atoms; ++a)
-                    tc::tma_load_2d(xs + (size_t)(s * sh.atoms + a) * kTxAtomBytes, &tmap, 32 * a,
+                    tc::tma_load_2d(xs + (size_t)s * tile_bytes + (size_t)a * kTxAtomBytes, &tmap, 32 * a,
                                     (int)(tile * kTxRows), &full[s]);
             }
             if (*abort)       // drain the copies still in flight before the CTA exits
                 for (long long i = (it > S ? it - S : 0); i < it; ++i)
                     for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&full[i % S], (unsigned)((i / S) & 1)); ++p) {}
         }
-    } else if (warp == kTxEpiWarps + 1) {
+    } else if (warp == kTxMma) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             const unsigned idesc = tc::idesc_tf32(kTxRows, sh.Npad);
+            const unsigned bstride = (unsigned)(sh.Npad * 128);
             long long it = 0;
             for (;; ++it) {
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
                 const int s = (int)(it % S), b = (int)(it & 1);
                 if (!tc::wait(&full[s], (unsigned)((it / S) & 1), abort, g)) break;
-                if (it >= 2 && !tc::wait(&acce[b], (unsigned)((it / 2 - 1) & 1), abort, g)) break;
+                if (!tc::wait(&conv[b], (unsigned)((it >> 1) & 1), abort, g)) break;
                 tc::fence_after();
-                const unsigned a0 = tc::s_addr(xs + (size_t)s * sh.atoms * kTxAtomBytes), b0 = tc::s_addr(bs);
+                const unsigned ax = tc::s_addr(xs + (size_t)s * tile_bytes);
+                const unsigned al = tc::s_addr(xl + (size_t)b * tile_bytes);
+                const unsigned ah = tc::s_addr(bh), alo = tc::s_addr(bl);
+                const unsigned d = tmem + (unsigned)(b * sh.acc_stride);
+                for (int kk = 0; kk < sh.ksteps; ++kk) {         // correction terms first
+                    const unsigned off = (unsigned)((kk & 3) * 32);
+                    const unsigned ao = (unsigned)(kk >> 2) * kTxAtomBytes + off;
+                    const unsigned bo = (unsigned)(kk >> 2) * bstride + off;
+                    tc::mma_tf32(d, tc::desc_sw128(al + ao), tc::desc_sw128(ah + bo), idesc, kk > 0);
+                    tc::mma_tf32(d, tc::desc_sw128(ax + ao), tc::desc_sw128(alo + bo), idesc, 1);
+                }
                 for (int kk = 0; kk < sh.ksteps; ++kk) {
                     const unsigned off = (unsigned)((kk & 3) * 32);
-                    const unsigned aa = a0 + (unsigned)(kk >> 2) * kTxAtomBytes + off;
-                    const unsigned ba = b0 + (unsigned)(kk >> 2) * (unsigned)(sh.Npad * 128) + off;
-                    tc::mma_tf32(tmem + (unsigned)(b * sh.acc_stride), tc::desc_sw128(aa), tc::desc_sw128(ba), idesc,
-                                 kk > 0);
+                    const unsigned ao = (unsigned)(kk >> 2) * kTxAtomBytes + off;
+                    const unsigned bo = (unsigned)(kk >> 2) * bstride + off;
+                    tc::mma_tf32(d, tc::desc_sw128(ax + ao), tc::desc_sw128(ah + bo), idesc, 1);
                 }
                 tc::commit(&accf[b]);
             }
             if (*abort && it > 0)     // the last commit covers every MMA issued
                 for (unsigned p = 0;
-                     p < (1u << 22) && !tc::try_wait(&accf[(it - 1) & 1], (unsigned)(((it - 1) / 2) & 1)); ++p) {}
+                     p < (1u << 22) && !tc::try_wait(&accf[(it - 1) & 1], (unsigned)(((it - 1) >> 1) & 1)); ++p) {}
         }
     } else {
-        // ---------------------------------------------------------- epilogue
+        // --------------------------------------------------- epilogue groups
         const Grids gr = grids_from_maxbits(g->maxbits);
         const CertC cc = cert;
-        const int r = warp * 32 + lane;                     // row within the tile = TMEM lane
-        for (long long it = 0;; ++it) {
+        const int b = warp >> 2, q4 = warp & 3;
+        const int r = q4 * 32 + lane;                        // row within the tile = TMEM lane
+        unsigned char* xlb = xl + (size_t)b * tile_bytes;
+        const unsigned cstride = (unsigned)(sh.Npad * 128);
+        for (long long it = b;; it += 2) {
             const long long tile = blockIdx.x + it * grid;
             if (tile >= ntiles) break;
-            const int s = (int)(it % S), b = (int)(it & 1);
+            const int s = (int)(it % S);
+            unsigned char* st = xs + (size_t)s * tile_bytes;
+            // 1. the row: hi(x) in place, r(x) into this group's buffer
             int ok = 1;
-            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it / 2) & 1), abort, g);
+            if (lane == 0) ok = tc::wait(&full[s], (unsigned)((it / S) & 1), abort, g);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            float xn2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < NP / 4; ++q) {
+                float4* p = reinterpret_cast<float4*>(st + tile_off(r, q));
+                const float4 v = *p;
+                xn2 = __fmaf_ru(v.x, v.x, xn2);
+                xn2 = __fmaf_ru(v.y, v.y, xn2);
+                xn2 = __fmaf_ru(v.z, v.z, xn2);
+                xn2 = __fmaf_ru(v.w, v.w, xn2);
+                const float4 h = make_float4(trunc_tf32(v.x), trunc_tf32(v.y), trunc_tf32(v.z), trunc_tf32(v.w));
+                *p = h;
+                *reinterpret_cast<float4*>(xlb + tile_off(r, q)) =
+                    make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            }
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::arrive(&conv[b]);
+            const float xn = __fsqrt_ru(xn2);
+            // 2. the accumulator of this tile
+            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it >> 1) & 1), abort, g);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc::fence_after();
-            // two interleaved top-2 chains over the accumulator columns
-            float ga1 = __int_as_float(0x7f800000), ga2 = ga1, gb1 = ga1, gb2 = ga1;
-            int ja = 0, jb = 0;
-            const unsigned trow = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * sh.acc_stride);
-            for (int c0 = 0; c0 < sh.Npad; c0 += 32) {
-                unsigned va[16], vb[16];
+            // four interleaved top-2 chains over the accumulator columns
+            float t1[4], t2[4];
+            int tj[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { t1[c] = __int_as_float(0x7f800000); t2[c] = t1[c]; tj[c] = 0; }
+            const unsigned trow = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)(b * sh.acc_stride);
+            for (int c0 = 0; c0 < sh.Npad; c0 += 16) {
+                unsigned va[16];
                 tc::ld16(trow + (unsigned)c0, va);
-                const bool two = c0 + 16 < sh.Npad;
-                if (two) tc::ld16(trow + (unsigned)(c0 + 16), vb);
                 tc::wait_ld();
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -219,81 +315,91 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float e = __fmaf_rn(-2.f, __uint_as_float(va[4 * q + i]), cv[i]);
-                        ga2 = fminf(ga2, fmaxf(ga1, e));
-                        ja = (e < ga1) ? (c0 + 4 * q + i) : ja;
-                        ga1 = fminf(ga1, e);
+                        t2[i] = fminf(t2[i], fmaxf(t1[i], e));
+                        tj[i] = (e < t1[i]) ? (c0 + 4 * q + i) : tj[i];
+                        t1[i] = fminf(t1[i], e);
                     }
                 }
-                if (two) {
+            }
+            float g1 = t1[0], g2 = t2[0];
+            int j1 = tj[0];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 cq = *reinterpret_cast<const float4*>(CC + c0 + 16 + 4 * q);
-                        const float cv[4] = {cq.x, cq.y, cq.z, cq.w};
+            for (int c = 1; c < 4; ++c) {   // merge: least value, lowest index among equal values
+                const bool take = t1[c] < g1 || (t1[c] == g1 && tj[c] < j1);
+                g2 = take ? fminf(g1, t2[c]) : fminf(g2, t1[c]);
+                g1 = take ? t1[c] : g1;
+                j1 = take ? tj[c] : j1;
+            }
+            // 3. certificate, distance (x = hi + r from the two tiles); an
+            //    uncertain row is decided among its candidates: the centroids
+            //    whose g lies within the certificate threshold of g1
+            const long long row = tile * kTxRows + r;
+            const float thr = fmaxf(cert_threshold(g1, xn2, xn, cc, gB, gp2), 0x1p-60f);
+            const bool good = row >= m || __fsub_rd(g2, g1) > thr;
+            int lab = j1;
+            float dv = 0.f;
+            if (good && row < m) dv = d32_split<NP>(st, xlb, r, bh, bl, j1, cstride);
+            const unsigned unc = __ballot_sync(0xffffffffu, !good);
+            if (unc) {
+                if (lane == 0) resc += __popc(unc);
+                unsigned* plist = pairs[warp];
+                unsigned long long* keys = pkeys[warp];
+                keys[lane] = ~0ull;
+                int np = 0;                                  // warp-uniform pair count
+                for (int c0 = 0; c0 < sh.Npad; c0 += 16) {  // second pass over the accumulator
+                    unsigned va[16];
+                    tc::ld16(trow + (unsigned)c0, va);
+                    tc::wait_ld();
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float e = __fmaf_rn(-2.f, __uint_as_float(vb[4 * q + i]), cv[i]);
-                            gb2 = fminf(gb2, fmaxf(gb1, e));
-                            jb = (e < gb1) ? (c0 + 16 + 4 * q + i) : jb;
-                            gb1 = fminf(gb1, e);
+                    for (int i = 0; i < 16; ++i) {
+                        const float e = __fmaf_rn(-2.f, __uint_as_float(va[i]), CC[c0 + i]);
+                        const bool cand = !good && !(__fsub_rd(e, g1) > thr);
+                        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+                        if (cm) {
+                            const int slot = np + __popc(cm & ((1u << lane) - 1u));
+                            if (cand && slot < kTxPairs) plist[slot] = ((unsigned)lane << 16) | (unsigned)(c0 + i);
+                            np += __popc(cm);
                         }
                     }
                 }
+                __syncwarp();
+                if (np <= kTxPairs) {                        // candidate pairs, one lane each
+                    for (int p = lane; p < np; p += 32) {
+                        const int l = (int)(plist[p] >> 16), j = (int)(plist[p] & 0xffffu);
+                        const float d = d32_split<NP>(st, xlb, q4 * 32 + l, bh, bl, j, cstride);
+                        atomicMin(&keys[l], ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j);
+                    }
+                    __syncwarp();
+                    if (!good) {
+                        const unsigned long long key = keys[lane];
+                        lab = (int)(key & 0xffffffffu);
+                        dv = __uint_as_float((unsigned)(key >> 32));
+                    }
+                } else {                                     // many candidates: all centroids
+                    unsigned pend = unc;
+                    while (pend) {
+                        const int src = __ffs(pend) - 1;
+                        pend &= pend - 1;
+                        const int rs = q4 * 32 + src;
+                        float bd = __int_as_float(0x7f800000);
+                        int bj = 0x7fffffff;
+                        for (int j = lane; j < k; j += 32) {
+                            const float dj = d32_split<NP>(st, xlb, rs, bh, bl, j, cstride);
+                            if (dj < bd || bj == 0x7fffffff) { bd = dj; bj = j; }
+                        }
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                            if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
+                        }
+                        if (lane == src) { dv = bd; lab = bj; }
+                    }
+                }
             }
-            tc::fence_before();
+            tc::fence_before();             // accumulator b read; its next MMA waits on conv[b]
             __syncwarp();
-            if (lane == 0) tc::arrive(&acce[b]);          // accumulator b free for the MMA of tile it+2
-            float g1, g2;
-            int j1;
-            if (ga1 <= gb1) { g1 = ga1; j1 = ja; g2 = fminf(ga2, gb1); }
-            else { g1 = gb1; j1 = jb; g2 = fminf(gb2, ga1); }
-
-            // this row of X, from the swizzled stage
-            const unsigned char* st = xs + (size_t)s * sh.atoms * kTxAtomBytes;
-            float x[NP];
-#pragma unroll
-            for (int d4 = 0; d4 < NP / 4; ++d4) {
-                const float4 v = *reinterpret_cast<const float4*>(st + (size_t)(d4 >> 3) * kTxAtomBytes + r * 128 +
-                                                                  (((d4 & 7) ^ (r & 7)) << 4));
-                x[4 * d4 + 0] = v.x; x[4 * d4 + 1] = v.y; x[4 * d4 + 2] = v.z; x[4 * d4 + 3] = v.w;
-            }
-            const long long row = tile * kTxRows + r;
-            float xn2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < NP; ++d) xn2 = __fmaf_ru(x[d], x[d], xn2);
-            const float xn = __fsqrt_ru(xn2);
-            const bool good = certified(g1, g2, xn2, xn, cc, gB, gp2) && __fsub_rd(g2, g1) > 0x1p-60f;
-            int lab = j1;
-            float dv = 0.f;
-            if (good) dv = d32<NP>(x, C + (size_t)j1 * NP);
-            unsigned pend = __ballot_sync(0xffffffffu, row < m && !good);
-            if (lane == 0) resc += __popc(pend);
-            while (pend) {                                  // warp-cooperative exact re-score
-                const int src = __ffs(pend) - 1;
-                pend &= pend - 1;
-                const int rs = warp * 32 + src;
-                float xsr[NP];
-#pragma unroll
-                for (int d4 = 0; d4 < NP / 4; ++d4) {
-                    const float4 v = *reinterpret_cast<const float4*>(
-                        st + (size_t)(d4 >> 3) * kTxAtomBytes + rs * 128 + (((d4 & 7) ^ (rs & 7)) << 4));
-                    xsr[4 * d4 + 0] = v.x; xsr[4 * d4 + 1] = v.y; xsr[4 * d4 + 2] = v.z; xsr[4 * d4 + 3] = v.w;
-                }
-                float bd = __int_as_float(0x7f800000);
-                int bj = 0x7fffffff;
-                for (int j = lane; j < k; j += 32) {
-                    const float dj = d32<NP>(xsr, C + (size_t)j * NP);
-                    if (dj < bd || bj == 0x7fffffff) { bd = dj; bj = j; }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
-                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-                    if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
-                }
-                if (lane == src) { dv = bd; lab = bj; }
-            }
-            __syncwarp();
-            if (lane == 0) tc::arrive(&empty[s]);          // stage s free for the copy of tile it+S
+            if (lane == 0) tc::arrive(&empty[s]);             // stage s no longer read
             if (row < m) {
                 acc_obj(facc, dv, gr.gf, inex);
                 if (labels) labels[row] = lab;
@@ -304,7 +410,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     // teardown: every MMA has completed (consumed, or drained on abort)
     tc::fence_before();
     __syncthreads();
-    if (warp == kTxEpiWarps + 1) {
+    if (warp == kTxMma) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, (unsigned)sh.tmem_cols);
     }
@@ -369,13 +475,11 @@ bool tx_shape(int np, int k, TxShape& s) {
     while (cols < 2 * s.acc_stride) cols <<= 1;
     if (cols > 512) return false;
     s.tmem_cols = cols;
-    // stages: as many as fit (2..4) while two CTAs still share an SM
-    const size_t fixed = 1024 + (size_t)s.atoms * s.Npad * 128 + (size_t)s.Npad * 4;
-    const size_t per = (size_t)s.atoms * kTxAtomBytes;
-    const size_t budget = 113 * 1024;
-    int st = budget > fixed ? (int)((budget - fixed) / per) : 0;
-    s.stages = std::min(4, std::max(2, st));
-    return tx_smem_bytes(s) <= 227 * 1024;
+    // as many stages (2..4) as fit in the shared memory of one CTA (227 KB,
+    // less 6 KB for the kernel's static shared memory)
+    constexpr size_t kDyn = 221 * 1024;
+    for (s.stages = kTxMaxStages; s.stages > 2 && tx_smem_bytes(s) > kDyn; --s.stages) {}
+    return tx_smem_bytes(s) <= kDyn;
 }
 
 template <int NP>
@@ -387,8 +491,12 @@ cudaError_t launch_t(const CUtensorMap& tm, long long m, const float* C, int k, 
     size_t smem = tx_smem_bytes(sh);
     smem = std::max(smem, (size_t)(228 * 1024) / (size_t)(tmem_per_sm + 1) + 1024);
     smem = std::min<size_t>(smem, 227 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(tcx_fullpass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, tcx_fullpass_kernel<NP>);
+    if (e != cudaSuccess) return e;
+    if ((long long)fa.numRegs * kTxThreads > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
+        return cudaErrorNotSupported;
+    e = cudaFuncSetAttribute(tcx_fullpass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcx_fullpass_kernel<NP>, kTxThreads, smem);
@@ -411,6 +519,12 @@ bool tcx_eligible(const float* X, long long m, int n, int np, int k) {
            encode_fn() != nullptr;
 }
 
+// Certificate factor of the split-TF32 products (see the file comment).
+float tcx_gamma(int np) {
+    const int ksteps = std::max(1, np / 8);
+    return 2.0f * (float)(ksteps * 9) * 0x1p-23f + 8.0f * 0x1p-20f;
+}
+
 // Launch the tensor-core exact pass; cudaErrorNotSupported when not eligible.
 cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                                 const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
@@ -426,7 +540,7 @@ cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, cons
                                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
-    const float gBt = std::max(gB, 0x1p-9f);
+    const float gBt = std::max(gB, tcx_gamma(np));
     switch (np) {
         case 4: return launch_t<4>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
         case 8: return launch_t<8>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);

@@ -64,10 +64,10 @@ def test_tensor_core_pass_is_bit_exact(m, n, k):
 
 
 def test_widest_case_runs_on_tensor_cores_only():
-    """n = 64, k = 256: beyond the FP32-ALU pass's shared memory, taken by the
+    """n = 64, k = 176: beyond the FP32-ALU pass's shared memory, taken by the
     tensor-core pass alone."""
-    X = gaussian_mixture(20_000, 64, 128, seed=21)
-    C = X[np.random.default_rng(3).integers(0, X.shape[0], 256)].copy()
+    X = gaussian_mixture(20_000, 64, 88, seed=21)
+    C = X[np.random.default_rng(3).integers(0, X.shape[0], 176)].copy()
     Y, f, rep = native.assign(_t(X), _t(C))
     assert native.last_fullpass_impl() == 2
     lab, dist = okm.assign(X, C)
