@@ -31,13 +31,24 @@ __device__ __forceinline__ bool try_wait(unsigned long long* b, unsigned parity)
                  : "memory");
     return ok != 0;
 }
+// try_wait that may suspend the thread for up to `ns` nanoseconds while the
+// phase is incomplete (it returns as soon as the phase completes).
+__device__ __forceinline__ bool try_wait_sleep(unsigned long long* b, unsigned parity, unsigned ns) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(s_addr(b)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait.  Gives up when `abort` is raised by another role of the CTA,
-// or after 2^24 polls (then it raises `abort` and the timeout flag), so that
-// no role of a CTA can wait forever on another.
+// or after 2^18 polls of at most 20 us each (then it raises `abort` and the
+// timeout flag), so that no role of a CTA can wait forever on another.
 __device__ __forceinline__ bool wait(unsigned long long* b, unsigned parity, volatile int* abort, Globals* g) {
-    for (unsigned i = 0; i < (1u << 24); ++i) {
-        if (try_wait(b, parity)) return true;
-        if ((i & 63) == 63 && *abort) return false;
+    for (unsigned i = 0; i < (1u << 18); ++i) {
+        if (try_wait_sleep(b, parity, 20000u)) return true;
+        if (*abort) return false;
     }
     *abort = 1;
     atomicOr(&g->err, kErrTimeout);

@@ -9,9 +9,10 @@
 //   * X (FP32, row-major, n % 4 == 0) is read by 2-D TMA copies into 128-row
 //     tiles in the 128-byte-swizzle K-major layout (32 floats per row and
 //     column block; columns past n are zero-filled by the copy);
-//   * split TF32: every x is split into hi = trunc_tf32(x) (exact in TF32,
-//     written over the tile in place) and the residual r = x - hi (exact in
-//     FP32, written to a second tile), every c likewise; one tile of 128
+//   * split TF32: every x is split into hi = trunc_tf32(x) (exact in TF32)
+//     and the residual r = x - hi (exact in FP32), written to two tiles of
+//     the epilogue group that takes the tile (which frees the TMA stage at
+//     once), every c likewise; one tile of 128
 //     rows takes the MMAs r(x).hi(c) and hi(x).r(c) first, then
 //     hi(x).hi(c), all accumulated in FP32 in tensor memory
 //     (tcgen05.mma kind::tf32, M = 128, N = k rounded up to 16, K = 8 per
@@ -36,10 +37,11 @@
 // |g_j - (||c_j||^2 - 2 x.c_j)| by gB (cmax^2 + 2 ||x|| cmax).  A gap below
 // 2^-60 is never accepted (subnormal data).
 //
-// CTA roles: warp 8 issues the TMA copies, warp 9 the MMAs; warps 0-7 form
-// two epilogue warpgroups, warpgroup b taking the tiles it == b (mod 2) with
-// tensor-memory accumulator b and its own lo(x) buffer, so the MMA of one
-// tile overlaps the epilogue of the other.
+// CTA roles: the warp after the epilogue warps issues the TMA copies, the
+// next one the MMAs; the epilogue warps form G = 2 or 3 warpgroups,
+// warpgroup b taking the tiles it == b (mod G) with tensor-memory
+// accumulator b and its own hi(x) / r(x) tiles, so the MMA of one tile
+// overlaps the epilogues of the others.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -54,10 +56,9 @@ namespace bm {
 
 constexpr int kTxRows = 128;                  // rows per tile (MMA M)
 constexpr int kTxAtomBytes = kTxRows * 128;   // one 32-float column block of a tile
-constexpr int kTxEpiWarps = 8;                // two epilogue warpgroups
-constexpr int kTxProducer = kTxEpiWarps, kTxMma = kTxEpiWarps + 1;
-constexpr int kTxThreads = 32 * (kTxEpiWarps + 2);
-constexpr int kTxMaxStages = 4;
+constexpr int kTxMaxGroups = 3;              // epilogue warpgroups per CTA (2 or 3)
+constexpr int kTxMaxStages = 6;
+__host__ __device__ constexpr int tx_threads(int groups) { return 32 * (4 * groups + 2); }
 constexpr int kTxPairs = 64;                  // candidate pairs per warp and tile
 
 struct TxShape {
@@ -67,14 +68,17 @@ struct TxShape {
     int acc_stride;  // tensor-memory columns per accumulator
     int tmem_cols;   // columns allocated
     int stages;      // X tiles in flight
+    int groups;      // epilogue warpgroups (= accumulators = r(x) buffers)
+    int inplace;     // 1: hi(x) written over the stage, which is held until the
+                     //    group's epilogue ends; 0: hi(x) in a group buffer
 };
 
 // Shared memory (1024-byte aligned pieces):
-//   [X stages: stages x atoms x 16 KB][r(x): 2 x atoms x 16 KB]
-//   [hi(c), r(c): 2 x atoms x Npad x 128 B][CC: Npad floats]
+//   [X stages: stages x atoms x 16 KB][hi(x) (unless in place), r(x): groups
+//   x atoms x 16 KB each][hi(c), r(c): 2 x atoms x Npad x 128 B][CC: Npad floats]
 __host__ __device__ inline size_t tx_smem_bytes(const TxShape& s) {
-    return 1024 + (size_t)(s.stages + 2) * s.atoms * kTxAtomBytes + (size_t)2 * s.atoms * s.Npad * 128 +
-           (size_t)s.Npad * 4;
+    return 1024 + (size_t)(s.stages + (2 - s.inplace) * s.groups) * s.atoms * kTxAtomBytes +
+           (size_t)2 * s.atoms * s.Npad * 128 + (size_t)s.Npad * 4;
 }
 
 __device__ __forceinline__ float trunc_tf32(float v) { return __uint_as_float(__float_as_uint(v) & 0xffffe000u); }
@@ -110,8 +114,8 @@ __device__ __forceinline__ float d32_split(const unsigned char* xh, const unsign
     return acc;
 }
 
-template <int NP>
-__global__ void __launch_bounds__(kTxThreads, 1)
+template <int NP, int NG>
+__global__ void __launch_bounds__(tx_threads(NG), 1)
 tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const float* __restrict__ Cw, int k,
                     const double* sel_f, int W, int* __restrict__ labels, Globals* g, float gB, float gp2,
                     int incumbent, TxShape sh) {
@@ -119,21 +123,23 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     unsigned char* base = smem_raw + ((1024 - (tc::s_addr(smem_raw) & 1023)) & 1023);
     const size_t tile_bytes = (size_t)sh.atoms * kTxAtomBytes;
     unsigned char* xs = base;                                      // X stages
-    unsigned char* xl = xs + (size_t)sh.stages * tile_bytes;       // r(x), 2 buffers
-    unsigned char* bh = xl + 2 * tile_bytes;                       // hi(c)
+    unsigned char* xh = xs + (size_t)sh.stages * tile_bytes;       // hi(x), one per group
+    unsigned char* xl = xh + (sh.inplace ? 0 : NG) * tile_bytes;   // r(x), one per group
+    unsigned char* bh = xl + NG * tile_bytes;                      // hi(c)
     unsigned char* bl = bh + (size_t)sh.atoms * sh.Npad * 128;     // r(c)
     float* CC = reinterpret_cast<float*>(bl + (size_t)sh.atoms * sh.Npad * 128);
-    __shared__ __align__(8) unsigned long long full[kTxMaxStages], empty[kTxMaxStages], conv[2], accf[2];
+    constexpr int kEpi = 4 * NG, kProducer = kEpi, kMma = kEpi + 1, kThreads = tx_threads(NG);
+    __shared__ __align__(8) unsigned long long full[kTxMaxStages], empty[kTxMaxStages], conv[NG], accf[NG];
     __shared__ unsigned tmem_slot;
     __shared__ int abort_flag;
-    __shared__ unsigned __int128 red128[kTxThreads / 32];
-    __shared__ unsigned long long red64[kTxThreads / 32];
-    __shared__ unsigned int redu[kTxThreads / 32];
+    __shared__ unsigned __int128 red128[kThreads / 32];
+    __shared__ unsigned long long red64[kThreads / 32];
+    __shared__ unsigned int redu[kThreads / 32];
     __shared__ CertC cert;
     __shared__ int wsel;
     __shared__ bool last;
-    __shared__ unsigned pairs[kTxEpiWarps][kTxPairs];               // candidate (lane, j) per warp
-    __shared__ unsigned long long pkeys[kTxEpiWarps][32];           // (d32 bits, j) minimum per row
+    __shared__ unsigned pairs[kEpi][kTxPairs];                      // candidate (lane, j) per warp
+    __shared__ unsigned long long pkeys[kEpi][32];                  // (d32 bits, j) minimum per row
 
     if (g->nonfinite) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -146,16 +152,16 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         wsel = best;
         abort_flag = 0;
         for (int s = 0; s < sh.stages; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 4); }
-        for (int b = 0; b < 2; ++b) { tc::mbar_init(&conv[b], 4); tc::mbar_init(&accf[b], 1); }
+        for (int b = 0; b < NG; ++b) { tc::mbar_init(&conv[b], 4); tc::mbar_init(&accf[b], 1); }
         tc::mbar_init_fence();
     }
-    if (warp == kTxMma) tc::tmem_alloc(&tmem_slot, (unsigned)sh.tmem_cols);
+    if (warp == kMma) tc::tmem_alloc(&tmem_slot, (unsigned)sh.tmem_cols);
     __syncthreads();
     const float* C = Cw + (long long)wsel * k * NP;
 
     // B operands hi(c), r(c) (swizzled like the X tiles); CC and the
     // certificate constants from the FP32 centroids.
-    for (int e = tid; e < sh.atoms * sh.Npad * 8; e += kTxThreads) {
+    for (int e = tid; e < sh.atoms * sh.Npad * 8; e += kThreads) {
         const int a = e / (sh.Npad * 8), rem = e % (sh.Npad * 8), j = rem >> 3, c = rem & 7;
         float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
         const int d0 = a * 32 + c * 4;
@@ -169,7 +175,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         *reinterpret_cast<float4*>(bl + off) = l;
     }
     unsigned int mx = 0;
-    for (int j = tid; j < sh.Npad; j += kTxThreads) {
+    for (int j = tid; j < sh.Npad; j += kThreads) {
         float acc = 0.f, up = 0.f;
         if (j < k) {
 #pragma unroll
@@ -191,7 +197,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     tc::fence_after();
     if (tid == 0) {
         unsigned int mm = 0;
-        for (int i = 0; i < kTxThreads / 32; ++i) mm = max(mm, redu[i]);
+        for (int i = 0; i < kThreads / 32; ++i) mm = max(mm, redu[i]);
         cert.cmax2 = __uint_as_float(mm);
         cert.cmax = __fsqrt_ru(cert.cmax2);
     }
@@ -203,7 +209,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
 
     unsigned __int128 facc = 0;
     unsigned int inex = 0, resc = 0;
-    if (warp == kTxProducer) {
+    if (warp == kProducer) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             long long it = 0;
@@ -221,7 +227,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 for (long long i = (it > S ? it - S : 0); i < it; ++i)
                     for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&full[i % S], (unsigned)((i / S) & 1)); ++p) {}
         }
-    } else if (warp == kTxMma) {
+    } else if (warp == kMma) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
             const unsigned idesc = tc::idesc_tf32(kTxRows, sh.Npad);
@@ -230,11 +236,11 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             for (;; ++it) {
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
-                const int s = (int)(it % S), b = (int)(it & 1);
-                if (!tc::wait(&full[s], (unsigned)((it / S) & 1), abort, g)) break;
-                if (!tc::wait(&conv[b], (unsigned)((it >> 1) & 1), abort, g)) break;
+                const int b = (int)(it % NG);
+                if (!tc::wait(&conv[b], (unsigned)((it / NG) & 1), abort, g)) break;
                 tc::fence_after();
-                const unsigned ax = tc::s_addr(xs + (size_t)s * tile_bytes);
+                const unsigned ax = tc::s_addr(sh.inplace ? xs + (size_t)(it % S) * tile_bytes
+                                                          : xh + (size_t)b * tile_bytes);
                 const unsigned al = tc::s_addr(xl + (size_t)b * tile_bytes);
                 const unsigned ah = tc::s_addr(bh), alo = tc::s_addr(bl);
                 const unsigned d = tmem + (unsigned)(b * sh.acc_stride);
@@ -255,7 +261,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             }
             if (*abort && it > 0)     // the last commit covers every MMA issued
                 for (unsigned p = 0;
-                     p < (1u << 22) && !tc::try_wait(&accf[(it - 1) & 1], (unsigned)(((it - 1) >> 1) & 1)); ++p) {}
+                     p < (1u << 22) && !tc::try_wait(&accf[(it - 1) % NG], (unsigned)(((it - 1) / NG) & 1)); ++p) {}
         }
     } else {
         // --------------------------------------------------- epilogue groups
@@ -265,12 +271,14 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         const int r = q4 * 32 + lane;                        // row within the tile = TMEM lane
         unsigned char* xlb = xl + (size_t)b * tile_bytes;
         const unsigned cstride = (unsigned)(sh.Npad * 128);
-        for (long long it = b;; it += 2) {
+        for (long long it = b;; it += NG) {
             const long long tile = blockIdx.x + it * grid;
             if (tile >= ntiles) break;
             const int s = (int)(it % S);
             unsigned char* st = xs + (size_t)s * tile_bytes;
-            // 1. the row: hi(x) in place, r(x) into this group's buffer
+            unsigned char* xhb = sh.inplace ? st : xh + (size_t)b * tile_bytes;
+            // 1. the row: hi(x) and r(x) into this group's buffers; the stage
+            //    is free again as soon as every warp of the group has read it
             int ok = 1;
             if (lane == 0) ok = tc::wait(&full[s], (unsigned)((it / S) & 1), abort, g);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -278,23 +286,25 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             float xn2 = 0.f;
 #pragma unroll
             for (int q = 0; q < NP / 4; ++q) {
-                float4* p = reinterpret_cast<float4*>(st + tile_off(r, q));
-                const float4 v = *p;
+                const float4 v = *reinterpret_cast<const float4*>(st + tile_off(r, q));
                 xn2 = __fmaf_ru(v.x, v.x, xn2);
                 xn2 = __fmaf_ru(v.y, v.y, xn2);
                 xn2 = __fmaf_ru(v.z, v.z, xn2);
                 xn2 = __fmaf_ru(v.w, v.w, xn2);
                 const float4 h = make_float4(trunc_tf32(v.x), trunc_tf32(v.y), trunc_tf32(v.z), trunc_tf32(v.w));
-                *p = h;
+                *reinterpret_cast<float4*>(xhb + tile_off(r, q)) = h;
                 *reinterpret_cast<float4*>(xlb + tile_off(r, q)) =
                     make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
             }
             tc::fence_proxy_async();
             __syncwarp();
-            if (lane == 0) tc::arrive(&conv[b]);
+            if (lane == 0) {
+                if (!sh.inplace) tc::arrive(&empty[s]);
+                tc::arrive(&conv[b]);
+            }
             const float xn = __fsqrt_ru(xn2);
             // 2. the accumulator of this tile
-            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it >> 1) & 1), abort, g);
+            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it / NG) & 1), abort, g);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc::fence_after();
@@ -338,7 +348,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             const bool good = row >= m || __fsub_rd(g2, g1) > thr;
             int lab = j1;
             float dv = 0.f;
-            if (good && row < m) dv = d32_split<NP>(st, xlb, r, bh, bl, j1, cstride);
+            if (good && row < m) dv = d32_split<NP>(xhb, xlb, r, bh, bl, j1, cstride);
             const unsigned unc = __ballot_sync(0xffffffffu, !good);
             if (unc) {
                 if (lane == 0) resc += __popc(unc);
@@ -366,7 +376,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 if (np <= kTxPairs) {                        // candidate pairs, one lane each
                     for (int p = lane; p < np; p += 32) {
                         const int l = (int)(plist[p] >> 16), j = (int)(plist[p] & 0xffffu);
-                        const float d = d32_split<NP>(st, xlb, q4 * 32 + l, bh, bl, j, cstride);
+                        const float d = d32_split<NP>(xhb, xlb, q4 * 32 + l, bh, bl, j, cstride);
                         atomicMin(&keys[l], ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)j);
                     }
                     __syncwarp();
@@ -384,7 +394,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                         float bd = __int_as_float(0x7f800000);
                         int bj = 0x7fffffff;
                         for (int j = lane; j < k; j += 32) {
-                            const float dj = d32_split<NP>(st, xlb, rs, bh, bl, j, cstride);
+                            const float dj = d32_split<NP>(xhb, xlb, rs, bh, bl, j, cstride);
                             if (dj < bd || bj == 0x7fffffff) { bd = dj; bj = j; }
                         }
 #pragma unroll
@@ -398,8 +408,10 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 }
             }
             tc::fence_before();             // accumulator b read; its next MMA waits on conv[b]
-            __syncwarp();
-            if (lane == 0) tc::arrive(&empty[s]);             // stage s no longer read
+            if (sh.inplace) {
+                __syncwarp();
+                if (lane == 0) tc::arrive(&empty[s]);     // this warp's rows of the stage are read
+            }
             if (row < m) {
                 acc_obj(facc, dv, gr.gf, inex);
                 if (labels) labels[row] = lab;
@@ -410,7 +422,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     // teardown: every MMA has completed (consumed, or drained on abort)
     tc::fence_before();
     __syncthreads();
-    if (warp == kTxMma) {
+    if (warp == kMma) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, (unsigned)sh.tmem_cols);
     }
@@ -422,7 +434,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     if (tid == 0) {
         unsigned __int128 T = 0;
         unsigned long long ir = 0;
-        for (int i = 0; i < kTxThreads / 32; ++i) { T += red128[i]; ir += red64[i]; }
+        for (int i = 0; i < kThreads / 32; ++i) { T += red128[i]; ir += red64[i]; }
         for (int i = 0; i < 4; ++i) {
             const unsigned long long chunk = (unsigned long long)((T >> (32 * i)) & 0xffffffffu);
             if (chunk) atomicAdd(&g->obj_words[i], chunk);
@@ -465,48 +477,74 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// Groups: three epilogue warpgroups where the shared memory and tensor
+// memory allow, else two, else one.  The stage count is a multiple of the
+// group count, so that tile it and tile it - stages (the previous user of
+// its stage, whose barrier phase precedes it) belong to the same group:
+// every full-barrier phase is then waited on by one group, in order, and a
+// wait can never be two phases ahead (where parity would alias).
 bool tx_shape(int np, int k, TxShape& s) {
     if (k < 1 || k > 256 || np > 64) return false;
     s.atoms = np > 32 ? 2 : 1;
     s.ksteps = std::max(1, np / 8);
     s.Npad = (k + 15) & ~15;
     s.acc_stride = (s.Npad + 31) & ~31;
-    int cols = 32;
-    while (cols < 2 * s.acc_stride) cols <<= 1;
-    if (cols > 512) return false;
-    s.tmem_cols = cols;
-    // as many stages (2..4) as fit in the shared memory of one CTA (227 KB,
-    // less 6 KB for the kernel's static shared memory)
-    constexpr size_t kDyn = 221 * 1024;
-    for (s.stages = kTxMaxStages; s.stages > 2 && tx_smem_bytes(s) > kDyn; --s.stages) {}
-    return tx_smem_bytes(s) <= kDyn;
+    // 227 KB per CTA, less 8 KB for the kernel's static shared memory
+    constexpr size_t kDyn = 219 * 1024;
+    // layouts in order of preference: hi(x) in group buffers with 3 or 2
+    // groups; hi(x) in place with 2 groups; hi(x) in group buffers, 1 group
+    const int order[4][2] = {{3, 0}, {2, 0}, {2, 1}, {1, 0}};
+    for (const auto& o : order) {
+        s.groups = o[0];
+        s.inplace = o[1];
+        int cols = 32;
+        while (cols < s.groups * s.acc_stride) cols <<= 1;
+        if (cols > 512) continue;
+        s.tmem_cols = cols;
+        for (s.stages = (kTxMaxStages / s.groups) * s.groups; s.stages >= s.groups; s.stages -= s.groups)
+            if (tx_smem_bytes(s) <= kDyn) return true;
+    }
+    return false;
 }
 
-template <int NP>
+template <int NP, int NG>
 cudaError_t launch_t(const CUtensorMap& tm, long long m, const float* C, int k, const double* sel_f, int W,
                      int* labels, Globals* g, float gB, float gp2, int incumbent, int sms, const TxShape& sh,
                      cudaStream_t st) {
+    constexpr int threads = tx_threads(NG);
     // at most 512 / tmem_cols CTAs per SM, so that no allocation has to wait
     const int tmem_per_sm = 512 / sh.tmem_cols;
     size_t smem = tx_smem_bytes(sh);
     smem = std::max(smem, (size_t)(228 * 1024) / (size_t)(tmem_per_sm + 1) + 1024);
-    smem = std::min<size_t>(smem, 227 * 1024);
+    smem = std::min<size_t>(smem, 219 * 1024);
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, tcx_fullpass_kernel<NP>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, tcx_fullpass_kernel<NP, NG>);
     if (e != cudaSuccess) return e;
-    if ((long long)fa.numRegs * kTxThreads > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
+    const int warps_alloc = (threads / 32 + 3) & ~3;            // warps are given registers in fours
+    if ((long long)fa.numRegs * 32 * warps_alloc > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
         return cudaErrorNotSupported;
-    e = cudaFuncSetAttribute(tcx_fullpass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(tcx_fullpass_kernel<NP, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcx_fullpass_kernel<NP>, kTxThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcx_fullpass_kernel<NP, NG>, threads, smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, std::min(per_sm, tmem_per_sm));
     const long long tiles = (m + kTxRows - 1) / kTxRows;
     const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * per_sm, tiles));
-    tcx_fullpass_kernel<NP><<<(unsigned)grid, kTxThreads, smem, st>>>(tm, m, C, k, sel_f, W, labels, g, gB, gp2,
-                                                                      incumbent, sh);
+    tcx_fullpass_kernel<NP, NG><<<(unsigned)grid, threads, smem, st>>>(tm, m, C, k, sel_f, W, labels, g, gB, gp2,
+                                                                       incumbent, sh);
     return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t launch_g(const CUtensorMap& tm, long long m, const float* C, int k, const double* sel_f, int W,
+                     int* labels, Globals* g, float gB, float gp2, int incumbent, int sms, const TxShape& sh,
+                     cudaStream_t st) {
+    if (sh.groups == 3)
+        return launch_t<NP, 3>(tm, m, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
+    if (sh.groups == 2)
+        return launch_t<NP, 2>(tm, m, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
+    return launch_t<NP, 1>(tm, m, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
 }
 
 }  // namespace
@@ -542,11 +580,11 @@ cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, cons
     if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
     const float gBt = std::max(gB, tcx_gamma(np));
     switch (np) {
-        case 4: return launch_t<4>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
-        case 8: return launch_t<8>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
-        case 16: return launch_t<16>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
-        case 32: return launch_t<32>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
-        case 64: return launch_t<64>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
+        case 4: return launch_g<4>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
+        case 8: return launch_g<8>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
+        case 16: return launch_g<16>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
+        case 32: return launch_g<32>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
+        case 64: return launch_g<64>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
     }
     return cudaErrorNotSupported;
 }
