@@ -250,7 +250,8 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     roof_full = {"bound": "hbm", "achieved": full_gbs, "peak": hbm_peak, "unit": "GB/s",
                  "frac": full_gbs / hbm_peak, "traffic": None,
-                 "kernel": "fullpass_kernel<16> (labels + f(C, X))",
+                 "kernel": ("tcx_fullpass_kernel<16> (tcgen05 split-TF32, certified, labels + f(C, X))"
+                            if native.last_fullpass_impl() == 2 else "fullpass_kernel<16> (labels + f(C, X))"),
                  "algorithmic": f"m*n*4 = {bytes_full:.4g} bytes per launch (X read once)",
                  "avg_launch_us": t_full / max(n_full, 1) * 1e6, "peak_source": peak_src}
 

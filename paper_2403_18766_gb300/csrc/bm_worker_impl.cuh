@@ -175,7 +175,7 @@ struct Worker {
         for (long long base0 = lo + (long long)(threadIdx.x & ~31) * RT; base0 < hi;
              base0 += (long long)kThreads * RT) {
             const long long base = base0 + (long long)lane * RT;
-            float m2x[RT][NP];
+            float2 m2x[RT][NP / 2];                          // -2 x, dimension pairs
 #pragma unroll
             for (int r = 0; r < RT; ++r) {
                 const long long row = base + r;
@@ -184,14 +184,12 @@ struct Worker {
 #pragma unroll
                     for (int q = 0; q < NP / 4; ++q) {
                         const float4 v = p[q];
-                        m2x[r][4 * q + 0] = -2.f * v.x;
-                        m2x[r][4 * q + 1] = -2.f * v.y;
-                        m2x[r][4 * q + 2] = -2.f * v.z;
-                        m2x[r][4 * q + 3] = -2.f * v.w;
+                        m2x[r][2 * q + 0] = make_float2(-2.f * v.x, -2.f * v.y);
+                        m2x[r][2 * q + 1] = make_float2(-2.f * v.z, -2.f * v.w);
                     }
                 } else {
 #pragma unroll
-                    for (int d = 0; d < NP; ++d) m2x[r][d] = 0.f;
+                    for (int d = 0; d < NP / 2; ++d) m2x[r][d] = make_float2(0.f, 0.f);
                 }
             }
             int oldlab[RT];
@@ -203,22 +201,28 @@ struct Worker {
 #pragma unroll
             for (int r = 0; r < RT; ++r) { g1[r] = __int_as_float(0x7f800000); g2[r] = g1[r]; j1[r] = 0; }
             for (int j = 0; j < k; ++j) {
+                // g_j = ||c_j||^2 - 2 x.c_j as two interleaved partial sums
+                // (even and odd dimensions, packed FP32 FMA), then added:
+                // NP + 1 terms in another order, inside the certificate's
+                // gamma_{2NP+2} bound.
                 const float* cj = sm.Ccur + (size_t)j * NP;
                 const float ccj = sm.CC[j];
-                float e[RT];
+                float2 e2[RT];
 #pragma unroll
-                for (int r = 0; r < RT; ++r) e[r] = ccj;
+                for (int r = 0; r < RT; ++r) e2[r] = make_float2(ccj, 0.f);
 #pragma unroll
                 for (int q = 0; q < NP / 4; ++q) {
                     const float4 cv = reinterpret_cast<const float4*>(cj)[q];
+                    const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
 #pragma unroll
                     for (int r = 0; r < RT; ++r) {
-                        e[r] = __fmaf_rn(m2x[r][4 * q + 0], cv.x, e[r]);
-                        e[r] = __fmaf_rn(m2x[r][4 * q + 1], cv.y, e[r]);
-                        e[r] = __fmaf_rn(m2x[r][4 * q + 2], cv.z, e[r]);
-                        e[r] = __fmaf_rn(m2x[r][4 * q + 3], cv.w, e[r]);
+                        e2[r] = __ffma2_rn(m2x[r][2 * q + 0], c01, e2[r]);
+                        e2[r] = __ffma2_rn(m2x[r][2 * q + 1], c23, e2[r]);
                     }
                 }
+                float e[RT];
+#pragma unroll
+                for (int r = 0; r < RT; ++r) e[r] = __fadd_rn(e2[r].x, e2[r].y);
 #pragma unroll
                 for (int r = 0; r < RT; ++r) {
                     g2[r] = fminf(g2[r], fmaxf(g1[r], e[r]));
@@ -234,7 +238,7 @@ struct Worker {
                 float xn2 = 0.f;
 #pragma unroll
                 for (int d = 0; d < NP; ++d) {
-                    x[d] = -0.5f * m2x[r][d];
+                    x[d] = -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x);
                     xn2 = __fmaf_ru(x[d], x[d], xn2);
                 }
                 const float xn = __fsqrt_ru(xn2);
