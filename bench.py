@@ -352,7 +352,7 @@ def run_precision(args):
     import torch
     from paper_2403_18766_gb300 import native
     from paper_2403_18766_gb300.synthetic import workload
-    X = workload("gmm_10m_n64_k100z")
+    X = workload("gmm_10m_n64_k100z", m=args.rows)
     m, n = X.shape
     k = 100
     Xd = torch.from_numpy(X).cuda()
@@ -385,7 +385,7 @@ def run_precision(args):
     bytes_bf = m * (128 + 4 + 4)                 # packed row + norm + label
     line = {"metric": "precision-form full pass (labels + f)", "value": bytes_bf / t_bf / 1e9,
             "unit": "GB/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
-            "config": {"workload": "gmm_10m_n64_k100z: m=1e7, n=64, 100 Gaussians (Zipf 1.2), k=100",
+            "config": {"workload": f"gmm_10m_n64_k100z: m={m}, n=64, 100 Gaussians (Zipf 1.2), k=100",
                        "dtype": "bf16 distance tiles, FP32 accumulate (tcgen05), FP32 re-score",
                        "tau": 1e-3, "l2": "flushed between calls"},
             "roofline": {"bound": "hbm", "achieved": bytes_bf / t_bf / 1e9, "peak": hbm, "unit": "GB/s",

@@ -82,6 +82,18 @@ typedef struct {
     int32_t set_len;
     int32_t workers;   /* W, competing workers (>= 1)                       */
     int32_t passes;    /* p, passes per round (Sec. 5: 10)                  */
+    int32_t kind;      /* exploration of [s_min, s_max] (ignored with a set):
+                          0 = uniform integer (the paper, Alg. 1);
+                          1 = octave-uniform: octave i in [0, O) uniform,
+                              then uniform inside [s_min 2^i, s_min 2^(i+1) - 1]
+                              (the last octave ends at s_max), O = max(1,
+                              least t with s_min 2^t >= s_max)              */
+    int32_t exploit;   /* 0..100: percent chance that a worker's size for a
+                          round is the rounded mean of L accumulated before
+                          the round (exploiting the current best size, the
+                          paper's future work, Sec. 6); 0 = the paper.
+                          Nonzero values read L back to the host once per
+                          round and draw no samples ahead                  */
 } bm_sample_policy;
 
 /* Stop conditions (Alg. 1 round count T and/or a wall-clock budget) and the

@@ -40,13 +40,40 @@ def sample_indices(seed, purpose, worker, rnd, pss, m, s):
         T *= 2
 
 
-def draw_size(seed, worker, rnd, policy):
-    """s_w for (worker, round): uniform integer in [s_min, s_max] or uniform over a set."""
+def draw_size(seed, worker, rnd, policy, L_sum=0, L_len=0):
+    """s_w for (worker, round), from the size stream (SIZE, worker, round, 0).
+
+    The paper (Alg. 1): a uniform integer in [s_min, s_max], or uniform over
+    a configured set.  The future-work variants (Sec. 6, "other ways to
+    explore the range and exploit the currently best size"):
+      kind 1  - octave-uniform: octave i uniform in [0, O) with O the least
+                t >= 1 with s_min * 2^t >= s_max (O = 1 when s_min = s_max),
+                then uniform inside [s_min 2^i, s_min 2^(i+1) - 1]; the last
+                octave ends at s_max;
+      exploit - with probability exploit/100 (draw (1, 0) below 100 less
+                than exploit), the mean of L before this round, rounded half
+                up and clipped to the size range, when L is not empty.
+    Draw (0, 0) picks the set entry, the value or the octave; draw (2, 0) the
+    value inside the octave."""
     key = rng.stream_key(seed, rng.P_SIZE, worker, rnd, 0)
+    exploit = int(policy.get("exploit", 0))
+    if exploit > 0 and L_len > 0 and rng.draw_below(key, 1, 0, 100) < exploit:
+        lo, hi = size_range(policy, 1 << 62)
+        v = (2 * L_sum + L_len) // (2 * L_len)
+        return int(min(max(v, lo), hi))
     if policy.get("set"):
         vals = list(policy["set"])
         return int(vals[rng.draw_below(key, 0, 0, len(vals))])
     lo, hi = int(policy["s_min"]), int(policy["s_max"])
+    if int(policy.get("kind", 0)) == 1:
+        t = 0
+        while lo * 2 ** t < hi:
+            t += 1
+        octaves = max(1, t)
+        i = rng.draw_below(key, 0, 0, octaves)
+        a = lo * 2 ** i
+        b = hi if i == octaves - 1 else lo * 2 ** (i + 1) - 1
+        return a + rng.draw_below(key, 2, 0, b - a + 1)
     return lo + rng.draw_below(key, 0, 0, hi - lo + 1)
 
 
@@ -97,8 +124,9 @@ def bigmeans(X, k, policy, budget, seed, mode="exact32"):
     inc_f = np.inf
 
     for t in range(T):
+        L_sum, L_len = sum(L), len(L)                        # L as it stood before the round
         for w in range(W):
-            s_w = draw_size(seed, w, t, policy)
+            s_w = draw_size(seed, w, t, policy, L_sum, L_len)
             log["sizes"][w].append(s_w)
             if not deg[w].all():                             # recompute f_hat_w with new s_w
                 idx = sample_indices(seed, rng.P_EVAL, w, t, 0, m, s_w)

@@ -149,29 +149,6 @@ int cluster_size(long long s_cap, int max_cs) {
     return (int)cs;
 }
 
-// Host copy of the library's sample-size draw (same Philox4x64-10 and Lemire
-// rule as the device code), used to size each worker's cluster.
-uint64_t host_draw_below(uint64_t seed, uint64_t k1, uint64_t c0, uint64_t c1, uint64_t bound) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-    uint64_t x0 = c0, x1 = c1, x2 = 0, x3 = 0, k0 = seed, kk1 = k1;
-    for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += W0; kk1 += W1; }
-        const unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
-        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
-        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
-        const uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ kk1;
-        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
-    }
-    const uint64_t w[4] = {x0, x1, x2, x3};
-    const uint64_t thr = (0ull - bound) % bound;
-    for (int i = 0; i < 4; ++i) {
-        const unsigned __int128 p = (unsigned __int128)w[i] * bound;
-        if ((uint64_t)p >= thr) return (uint64_t)(p >> 64);
-    }
-    return (uint64_t)(((unsigned __int128)w[3] * bound) >> 64);
-}
-
 long long next_pow2(long long v) {
     long long p = 1;
     while (p < v) p <<= 1;
@@ -199,6 +176,7 @@ struct bm_fit_ctx {
     Globals* glob = nullptr;
     int jobs = 0;                           // sample jobs per round: W * (P + 1)
     int prefetched = -1;                    // round whose samples were drawn ahead
+    long long L_sum0 = 0, L_len0 = 0;       // L at the start of the current round (exploit policy)
     int rounds_planned = 0x7fffffff;        // rounds the caller intends to run (T)
     cudaStream_t sst = nullptr;             // sampling stream (draws the next round ahead)
     cudaEvent_t ev_sdone = nullptr;
@@ -222,6 +200,20 @@ struct bm_fit_ctx {
 };
 
 namespace {
+
+SizePolicy size_policy(const bm_fit_ctx* c) {
+    SizePolicy p;
+    memset(&p, 0, sizeof p);
+    p.s_min = c->pol.s_min;
+    p.s_hi = c->s_hi;
+    for (int i = 0; i < 16; ++i) p.set[i] = c->pol.set[i];
+    p.set_len = c->pol.set_len;
+    p.kind = c->pol.kind;
+    p.exploit = c->pol.exploit;
+    p.L_sum = c->L_sum0;
+    p.L_len = c->L_len0;
+    return p;
+}
 
 WorkerArgs make_args(const bm_fit_ctx* c, int mode, int parity = 0) {
     WorkerArgs a;
@@ -252,6 +244,7 @@ SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs, int parity = 0) {
     a.s_min = c->pol.s_min; a.s_max = c->s_hi;
     for (int i = 0; i < 16; ++i) a.set[i] = c->pol.set[i];
     a.set_len = c->pol.set_len;
+    a.sp = size_policy(c);
     const long long J = (long long)parity * c->jobs;         // first job of this buffer half
     a.S_stride = c->s_cap * c->np; a.S = c->S + J * a.S_stride;
     a.idx_stride = c->s_cap; a.idx = c->idx + J * a.idx_stride;
@@ -415,9 +408,7 @@ bm_status status_from_flags(const Globals& h) {
 }
 
 long long size_of(const bm_fit_ctx* c, int w, int t) {
-    const uint64_t k1 = stream_k1(kPurposeSize, w, t, 0);
-    if (c->pol.set_len > 0) return c->pol.set[host_draw_below(c->seed, k1, 0, 0, (uint64_t)c->pol.set_len)];
-    return c->pol.s_min + (long long)host_draw_below(c->seed, k1, 0, 0, (uint64_t)(c->s_hi - c->pol.s_min + 1));
+    return policy_size(size_policy(c), c->seed, stream_k1(kPurposeSize, w, t, 0));
 }
 
 bm_status ensure_streams(bm_fit_ctx* c) {
@@ -449,6 +440,12 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     const int big = 0x7fffffff;
     CU(cudaMemcpyAsync(&c->glob->rounds_done, &big, sizeof(int), cudaMemcpyHostToDevice, c->st));
     const int parity = r0 & 1;
+    if (c->pol.exploit > 0) {                   // sizes of this round depend on L so far
+        Globals h;
+        if ((s = read_globals(c, &h))) return s;
+        c->L_sum0 = (long long)h.L_sum;
+        c->L_len0 = (long long)h.accepts;
+    }
     const size_t sp = span_begin(c, 0);
     if (c->prefetched == r0) {
         CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));           // drawn ahead on the sampling stream
@@ -480,7 +477,7 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     // Draw the next round's samples into the other half while the workers
     // run; that half was last read by the previous round, which finished
     // before ev_fork.
-    if (r0 + 1 < c->rounds_planned) {
+    if (r0 + 1 < c->rounds_planned && c->pol.exploit == 0) {
         CU(cudaStreamWaitEvent(c->sst, c->ev_fork, 0));
         SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, parity ^ 1);
         sa.rnd = r0 + 1;
@@ -536,6 +533,8 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, con
     if (pol.workers < 1 || pol.workers > 4096) return fail(BM_EINVAL, "workers = %d out of range", pol.workers);
     if (pol.passes < 1) return fail(BM_EINVAL, "passes = %d must be >= 1", pol.passes);
     if (pol.set_len < 0 || pol.set_len > 16) return fail(BM_EINVAL, "set_len = %d out of range", pol.set_len);
+    if (pol.kind != 0 && pol.kind != 1) return fail(BM_EINVAL, "policy kind = %d must be 0 or 1", pol.kind);
+    if (pol.exploit < 0 || pol.exploit > 100) return fail(BM_EINVAL, "exploit = %d out of [0, 100]", pol.exploit);
     long long s_lo, s_hi;
     if (pol.set_len > 0) {
         s_lo = s_hi = std::min<long long>(pol.set[0], m);

@@ -92,6 +92,29 @@ __host__ __device__ inline uint64_t stream_k1(int purpose, int worker, int round
 }
 
 // Lemire: accept word w when low64(w * bound) >= (2^64 - bound) mod bound.
+// Host copy of the library's sample-size draw (same Philox4x64-10 and Lemire
+// rule as the device code), used to size each worker's cluster.
+inline uint64_t host_draw_below(uint64_t seed, uint64_t k1, uint64_t c0, uint64_t c1, uint64_t bound) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = c0, x1 = c1, x2 = 0, x3 = 0, k0 = seed, kk1 = k1;
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; kk1 += W1; }
+        const unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        const uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ kk1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+    }
+    const uint64_t w[4] = {x0, x1, x2, x3};
+    const uint64_t thr = (0ull - bound) % bound;
+    for (int i = 0; i < 4; ++i) {
+        const unsigned __int128 p = (unsigned __int128)w[i] * bound;
+        if ((uint64_t)p >= thr) return (uint64_t)(p >> 64);
+    }
+    return (uint64_t)(((unsigned __int128)w[3] * bound) >> 64);
+}
+
 __device__ __forceinline__ uint64_t lemire_thr(uint64_t bound) { return (0ull - bound) % bound; }
 
 __device__ __forceinline__ uint64_t uniform_below(const P4& b, uint64_t bound, uint64_t thr) {

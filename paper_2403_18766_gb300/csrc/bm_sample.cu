@@ -83,9 +83,7 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
         rnd = a.rnd;
         purpose = (q < a.P) ? kPurposePass : kPurposeEval;
         pss = (q < a.P) ? q : 0;
-        const unsigned long long k1 = stream_k1(kPurposeSize, worker, rnd, 0);
-        if (a.set_len > 0) s = a.set[draw_below(a.seed, k1, 0, 0, (unsigned long long)a.set_len)];
-        else s = a.s_min + (long long)draw_below(a.seed, k1, 0, 0, (unsigned long long)(a.s_max - a.s_min + 1));
+        s = policy_size(a.sp, a.seed, stream_k1(kPurposeSize, worker, rnd, 0));
     } else if (a.mode == kSampleFinal) {
         long long s_lo = a.s_min, s_hi = a.s_max;
         if (a.set_len > 0) {

@@ -13,6 +13,56 @@ enum SampleMode : int {
     kSampleGather = 3,  // one job, indices given in idx: gather only
 };
 
+// Sample-size policy of one round (Alg. 1 "s_w <- random size", and the
+// exploration / exploitation variants of the paper's future work): the
+// range, the optional set, and L as it stood at the start of the round.
+struct SizePolicy {
+    long long s_min, s_hi;      // range, s_hi clipped to m
+    long long set[16];
+    int set_len;
+    int kind;                   // 0 uniform, 1 octave-uniform
+    int exploit;                // percent
+    long long L_sum, L_len;     // L before the round
+};
+
+// One bounded draw (c0, 0) of the size stream, same bits on host and device.
+__host__ __device__ inline uint64_t size_draw(uint64_t seed, uint64_t k1, uint64_t c0, uint64_t bound) {
+#ifdef __CUDA_ARCH__
+    return draw_below(seed, k1, c0, 0, bound);
+#else
+    return host_draw_below(seed, k1, c0, 0, bound);
+#endif
+}
+
+// s_w for the size stream k1 = (SIZE, w, round, 0): draw (1, 0) decides
+// exploitation, draw (0, 0) the set entry / value / octave, draw (2, 0) the
+// value inside the octave.
+__host__ __device__ inline long long policy_size(const SizePolicy& p, uint64_t seed, uint64_t k1) {
+    if (p.exploit > 0 && p.L_len > 0 && size_draw(seed, k1, 1, 100) < (uint64_t)p.exploit) {
+        long long lo = p.s_min, hi = p.s_hi;
+        if (p.set_len > 0) {
+            lo = hi = p.set[0];
+            for (int i = 1; i < p.set_len; ++i) {
+                lo = p.set[i] < lo ? p.set[i] : lo;
+                hi = p.set[i] > hi ? p.set[i] : hi;
+            }
+        }
+        const long long v = (2 * p.L_sum + p.L_len) / (2 * p.L_len);     // mean, half up
+        return v < lo ? lo : (v > hi ? hi : v);
+    }
+    if (p.set_len > 0) return p.set[size_draw(seed, k1, 0, (uint64_t)p.set_len)];
+    if (p.kind == 1) {
+        int t = 0;
+        while ((p.s_min << t) < p.s_hi) ++t;
+        const int octaves = t > 1 ? t : 1;
+        const int i = (int)size_draw(seed, k1, 0, (uint64_t)octaves);
+        const long long a = p.s_min << i;
+        const long long b = (i == octaves - 1) ? p.s_hi : (p.s_min << (i + 1)) - 1;
+        return a + (long long)size_draw(seed, k1, 2, (uint64_t)(b - a + 1));
+    }
+    return p.s_min + (long long)size_draw(seed, k1, 0, (uint64_t)(p.s_hi - p.s_min + 1));
+}
+
 struct SampleArgs {
     const float* X;
     long long m;
@@ -23,6 +73,7 @@ struct SampleArgs {
     long long s_min, s_max;
     long long set[16];
     int set_len;
+    SizePolicy sp;                             // round mode: the size of each worker
     // explicit stream (kSampleStep)
     int purpose, worker, rnd, pss;
     long long step_s;

@@ -23,7 +23,8 @@ RNG_SIZE, RNG_EVAL, RNG_PASS, RNG_KPP, RNG_FINAL = 1, 2, 3, 4, 5
 class SamplePolicy(ctypes.Structure):
     _fields_ = [("s_min", ctypes.c_int64), ("s_max", ctypes.c_int64),
                 ("set", ctypes.c_int64 * 16), ("set_len", ctypes.c_int32),
-                ("workers", ctypes.c_int32), ("passes", ctypes.c_int32)]
+                ("workers", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("kind", ctypes.c_int32), ("exploit", ctypes.c_int32)]
 
 
 class Budget(ctypes.Structure):
@@ -116,8 +117,10 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
-def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10, set=None):
-    """bm_sample_policy: a size range [s_min, s_max] or a set of sizes (`sizes` or `set`)."""
+def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10, set=None, kind=0, exploit=0):
+    """bm_sample_policy: a size range [s_min, s_max] or a set of sizes (`sizes` or `set`);
+    kind 0 = uniform, 1 = octave-uniform over the range; exploit = percent chance of
+    using the rounded mean of L so far."""
     pol = SamplePolicy()
     sizes = sizes if sizes is not None else set
     if sizes:
@@ -130,6 +133,7 @@ def make_policy(s_min=None, s_max=None, sizes=None, workers=4, passes=10, set=No
     else:
         pol.s_min, pol.s_max, pol.set_len = int(s_min), int(s_max), 0
     pol.workers, pol.passes = int(workers), int(passes)
+    pol.kind, pol.exploit = int(kind), int(exploit)
     return pol
 
 

@@ -243,3 +243,18 @@ def test_config2_full_size_sampled():
     assert f2 == rep["f_full"] and np.array_equal(Y2.cpu().numpy(), Y)
     assert rep["inexact_terms"] == 0
     assert rep["passes_done"] == 160
+
+
+# ------------------------------------------------- size policies (NEXT-4)
+@pytest.mark.parametrize("pol,rounds,seed", [
+    (dict(s_min=200, s_max=6000, workers=4, passes=2, kind=1), 2, 11),
+    (dict(s_min=200, s_max=6000, workers=3, passes=2, exploit=60), 3, 12),
+    (dict(s_min=150, s_max=3000, workers=3, passes=2, kind=1, exploit=100), 3, 13),
+    (dict(set=[300, 900, 2700], workers=3, passes=2, exploit=50), 3, 14),
+])
+def test_fit_size_policies_bit_exact(pol, rounds, seed):
+    X = gaussian_mixture(8000, 8, 6, seed=seed)
+    bud = dict(rounds=rounds, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    C, Y, rep, ref = _fit_both(X, 6, pol, bud, seed=seed)
+    _assert_same(C, Y, rep, ref)
+    assert rep["lloyd_iters"] == ref["log"]["lloyd_iters"]
