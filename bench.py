@@ -406,6 +406,72 @@ def run_precision(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals of clustering jobs of mixed m, n, k on one
+    serving context (continuous batching under a device-memory budget).
+    Job data is generated before the clock starts and kept in pinned host
+    memory; each job's latency runs from its arrival (submit) to its result
+    on the host (H2D copy, Algorithm 1, full-data pass, D2H copy included)."""
+    import torch
+    from paper_2403_18766_gb300 import native
+    from paper_2403_18766_gb300.synthetic import gaussian_mixture
+    g = np.random.default_rng(5005)
+    pool = []
+    for i in range(6):                                   # data sets the jobs draw from
+        m = int(round(10 ** g.uniform(5.0, np.log10(2e6))))
+        n = int(g.choice([8, 16, 32]))
+        pool.append(torch.from_numpy(gaussian_mixture(m, n, 20, seed=700 + i, outliers=0.005)).pin_memory())
+    n_jobs = max(8, args.steps * 8)
+    rate = float(args.rate)                              # jobs per second
+    gaps = g.exponential(1.0 / rate, n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    jobs = []
+    for i in range(n_jobs):
+        X = pool[int(g.integers(len(pool)))]
+        k = int(g.choice([5, 10, 25]))
+        m = X.shape[0]
+        pol = native.make_policy(s_min=max(1000, 2 * k), s_max=min(32000, m), workers=8, passes=5)
+        jobs.append((X, k, pol, native.make_budget(rounds=2), 9000 + i))
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.6, 40 << 30))
+    ctx = native.ServeContext(budget, 6)
+    for X, k, pol, bud, seed in jobs[:args.warmup]:      # warm-up jobs (not timed)
+        ctx.wait(ctx.submit(X, k, pol, bud, seed))
+    clocks = ClockSampler(0)
+    t0 = time.perf_counter()
+    ids = []
+    for (X, k, pol, bud, seed), at in zip(jobs, arrivals):
+        dt = at - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids.append((ctx.submit(X, k, pol, bud, seed), time.perf_counter() - t0))
+    res = [(ctx.wait(j), t_arr) for j, t_arr in ids]
+    t_end = time.perf_counter() - t0
+    clk = clocks.stop()
+    st = ctx.stats()
+    ctx.close()
+    # latency on the context's clock: done - submit (submit happens at the arrival)
+    lat = np.array([r["t_done_s"] - r["t_submit_s"] for r, _ in res])
+    qwait = np.array([r["t_admit_s"] - r["t_submit_s"] for r, _ in res])
+    ok = all(r["status"] == native.BM_OK for r, _ in res)
+    errors = sorted({r.get("error", "") for r, _ in res if r["status"] != native.BM_OK})
+    ptsk = sum(r["report"]["assign_rows"] * jobs[i][1] for i, (r, _) in enumerate(res))
+    line = {"metric": "p50/p99 job latency (serving, continuous batching)",
+            "value": float(np.percentile(lat, 99)) * 1e3, "unit": "ms (p99)", "higher_is_better": False,
+            "p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+            "queue_wait_p50_ms": float(np.percentile(qwait, 50)) * 1e3,
+            "jobs": n_jobs, "all_ok": ok, "errors": errors[:3], "makespan_s": t_end, "jobs_per_s": n_jobs / t_end,
+            "lloyd_ptsk_per_s": ptsk / t_end, "arrival_rate_per_s": rate,
+            "peak_active": st["peak_active"], "peak_in_use_gb": st["peak_in_use_bytes"] / 1e9,
+            "budget_gb": budget / 1e9, "clocks": clk,
+            "config": {"workload": f"Poisson({rate:g}/s) jobs over 6 Gaussian-mixture data sets (m log-uniform "
+                                   "in [1e5, 2e6], n in {8, 16, 32}, 20 components + 0.5% outliers); "
+                                   "k in {5, 10, 25}; W=8, p=5, T=2 rounds, s in [max(1000, 2k), min(32000, m)]",
+                       "max_active": 6, "data": "synthetic, pinned host memory"}}
+    print(json.dumps(line))
+    return 0 if ok else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,17 +479,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rate", type=float, default=150.0, help="serve mode: job arrivals per second")
     ap.add_argument("--workload", default=None, help="kernel modes: workload name (default: the headline's)")
     ap.add_argument("--rows", type=int, default=None, help="kernel modes: rows of the workload to use")
     ap.add_argument("--k", type=int, default=None, help="kernel modes: number of centroids")
     ap.add_argument("--centroids", choices=["rows", "fit"], default="rows",
                     help="kernel modes: centroids from evenly spaced rows, or from a short fit")
-    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision"], default="fit",
+    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision", "serve"], default="fit",
                     help="fit: the headline benchmark; fullpass / lloyd: one kernel family, "
                          "for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.mode == "serve":
+        return run_serve(args)
     if args.mode == "precision":
         return run_precision(args)
     if args.mode != "fit":

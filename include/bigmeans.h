@@ -56,7 +56,8 @@ typedef enum {
     BM_ENOMEM = 2,     /* workspace allocation failed                       */
     BM_ECUDA = 3,      /* a CUDA runtime call failed (message has details)  */
     BM_ETIMEOUT = 4,   /* a bounded device wait ran out                     */
-    BM_EINTERNAL = 5   /* sampling ran out of draws or another device flag  */
+    BM_EINTERNAL = 5,  /* sampling ran out of draws or another device flag  */
+    BM_EAGAIN = 6      /* serving: the job has not finished yet              */
 } bm_status;
 
 /* Purposes of the counter-based random streams (Philox4x64-10, Salmon et al.
@@ -309,6 +310,82 @@ bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const floa
  * ------------------------------------------------------------------------- */
 bm_status bm_set_fullpass_impl(int32_t impl);
 int32_t bm_last_fullpass_impl(void);
+
+/* ---------------------------------------------------------------------------
+ * bm_fit_footprint -- device bytes of the workspace a fit with these
+ * arguments allocates (bigmeans_fit / bm_fit_create), without allocating.
+ * Same argument checks as bm_fit_create.
+ * ------------------------------------------------------------------------- */
+bm_status bm_fit_footprint(int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                           const bm_budget* budget, int64_t* bytes_out);
+
+/* ---------------------------------------------------------------------------
+ * Serving (continuous batching of clustering jobs on one GPU).
+ *
+ * A context admits submitted jobs by device-memory footprint
+ * (bm_job_footprint: the fit's workspace + X + C + labels) against
+ * hbm_budget_bytes and runs up to max_active of them at once, each on its own
+ * host runner thread and CUDA streams, so their kernels overlap on the GPU.
+ * Whenever a job finishes, the queued jobs are scanned in arrival order and
+ * every one that fits the freed memory is admitted (first fit; a job passed
+ * over four times stops later arrivals from overtaking it).  A job runs
+ * Algorithm 1 end to end as bigmeans_fit_host on the caller's host buffers:
+ * X is copied to the device, stays resident with the centroids and the
+ * per-worker statistics for the job's lifetime, and C (and labels, if
+ * requested) are copied back before the job is reported done.  Results are
+ * those of bigmeans_fit_host with the same arguments, whatever else runs.
+ *
+ * Ownership: the caller keeps X_host, C_out_host and labels_out_host alive
+ * and untouched until the job is done (pinned memory makes the copies
+ * asynchronous).  Times in bm_result are seconds since bm_ctx_create.
+ * The runner threads start at the first bm_submit on the device current in
+ * the submitting thread; bm_ctx_create itself makes no CUDA call.
+ * Errors: BM_EINVAL for bad arguments or shapes (checked at submit),
+ * BM_ENOMEM at submit for a job larger than the whole budget; a job's own
+ * failure is its bm_result.status (message via bm_job_error).
+ * ------------------------------------------------------------------------- */
+typedef struct bm_ctx bm_ctx;
+typedef int64_t bm_job_id;
+typedef struct {
+    const float* X_host;         /* m x n row-major float32                    */
+    int64_t m;
+    int32_t n;
+    int32_t k;
+    bm_sample_policy policy;
+    bm_budget budget;
+    uint64_t seed;
+    float* C_out_host;           /* k x n                                      */
+    int32_t* labels_out_host;    /* m, or NULL                                 */
+} bm_job;
+typedef struct {
+    int32_t status;              /* the job's status; BM_EAGAIN until done      */
+    int32_t state;               /* 0 queued, 1 running, 2 done                */
+    double f_full;
+    int64_t s_opt;
+    double t_submit_s, t_admit_s, t_done_s;
+    int64_t footprint_bytes;
+    bm_report report;
+} bm_result;
+typedef struct {
+    int64_t budget_bytes, in_use_bytes, peak_in_use_bytes;
+    int32_t active, peak_active, queued, pad_;
+    int64_t done;
+    double now_s;
+} bm_ctx_info;
+
+bm_status bm_ctx_create(int64_t hbm_budget_bytes, int32_t max_active, bm_ctx** out);
+bm_status bm_job_footprint(const bm_job* job, int64_t* bytes_out);
+bm_status bm_submit(bm_ctx* ctx, const bm_job* job, bm_job_id* id_out);
+/* BM_OK when the job is done (result filled), BM_EAGAIN while queued or
+ * running (result holds the state and times so far). */
+bm_status bm_poll(bm_ctx* ctx, bm_job_id id, bm_result* result_out);
+/* Blocks until the job is done or timeout_s passes (timeout_s < 0: no limit). */
+bm_status bm_wait(bm_ctx* ctx, bm_job_id id, double timeout_s, bm_result* result_out);
+/* The error message of a failed job (empty if none), NUL-terminated. */
+bm_status bm_job_error(bm_ctx* ctx, bm_job_id id, char* buf, int64_t len);
+bm_status bm_ctx_stats(bm_ctx* ctx, bm_ctx_info* stats_out);
+/* Drops queued jobs, waits for running ones, frees the context. */
+void bm_ctx_destroy(bm_ctx* ctx);
 
 /* Thread-local message for the last non-OK status of this thread. */
 const char* bm_last_error(void);

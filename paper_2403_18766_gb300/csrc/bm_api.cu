@@ -303,6 +303,30 @@ void collect_spans(bm_fit_ctx* c) {
 // per round, two rounds' worth so the next round is drawn while this one
 // runs) the padded sample, its indices, draws and sampler table; per worker
 // the K-means++ D^2, labels, centroids and state.
+// Device bytes of a fit's workspace (the layout of alloc_workspace).
+size_t workspace_bytes(const bm_fit_ctx* c, int W) {
+    const long long k = c->k, np = c->np;
+    const long long J = 2ll * W * (c->pol.passes + 1);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off += (bytes + 255) & ~(size_t)255; };
+    take(sizeof(Globals));
+    take((size_t)J * c->s_cap * np * 4);
+    take((size_t)J * c->s_cap * 8);
+    take((size_t)J * c->Tcap * 4);
+    take((size_t)J * c->H * 8);
+    take((size_t)J * 4);
+    take((size_t)W * c->s_cap * 4);
+    take((size_t)W * c->s_cap * 4);
+    take((size_t)W * k * np * 4);
+    take((size_t)W * kMaxCluster * k * np * 4);
+    take((size_t)W * k);
+    take((size_t)W * 8);
+    take((size_t)W * 8);
+    take((size_t)c->L_cap * 8);
+    take(8);
+    return off;
+}
+
 bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const long long k = c->k, np = c->np;
     c->jobs = W * (c->pol.passes + 1);
@@ -462,7 +486,10 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     CU(cudaEventRecord(c->ev_fork, c->st));
     const int ns = (int)c->wst.size();
     for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(c->wst[i], c->ev_fork, 0));
-    for (int w = 0; w < c->pol.workers; ++w) {
+    // A failed launch must not return before the workers already launched
+    // are joined into c->st: the caller frees the workspace on c->st.
+    cudaError_t launch_err = cudaSuccess;
+    for (int w = 0; w < c->pol.workers && launch_err == cudaSuccess; ++w) {
         long long smax = 0;
         for (int t = r0; t < r1; ++t) smax = std::max(smax, size_of(c, w, t));
         WorkerArgs a = make_args(c, kModeRounds, parity);
@@ -471,8 +498,16 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
         a.worker_base = w;
         a.cs = cluster_size(smax, c->max_cs);
-        CU(launch_worker(c->np, a, 1, c->wst[w % ns]));
-        c->n_kernels++;
+        launch_err = launch_worker(c->np, a, 1, c->wst[w % ns]);
+        if (launch_err == cudaSuccess) c->n_kernels++;
+    }
+    if (launch_err != cudaSuccess) {
+        for (int i = 0; i < ns; ++i) {
+            cudaEventRecord(c->ev_join[i], c->wst[i]);
+            cudaStreamWaitEvent(c->st, c->ev_join[i], 0);
+        }
+        span_end(c, sp);
+        return fail(BM_ECUDA, "worker launch: %s", cudaGetErrorString(launch_err));
     }
     // Draw the next round's samples into the other half while the workers
     // run; that half was last read by the previous round, which finished
@@ -520,13 +555,16 @@ bm_status bm_set_fullpass_impl(int32_t impl) {
 int32_t bm_last_fullpass_impl(void) { return last_fullpass_impl(); }
 const char* bm_version(void) { return "bigmeans-gb300 0.1 (sm_103a)"; }
 
-bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
-                        const bm_budget* budget, uint64_t seed, void* stream, bm_fit_ctx** out) {
-    if (!out) return fail(BM_EINVAL, "out is NULL");
+}  // extern "C"
+
+namespace {
+// Validation and sizing of a fit (no device work): the context with every
+// planned field set and nothing allocated.
+bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                   const bm_budget* budget, uint64_t seed, void* stream, bm_fit_ctx** out) {
     *out = nullptr;
     if (!policy || !budget) return fail(BM_EINVAL, "policy and budget are required");
-    bm_status s = check_ptr(X_dev, "X_dev");
-    if (s) return s;
+    bm_status s;
     if ((s = check_shape(m, n, k))) return s;
     bm_sample_policy pol = *policy;
     bm_budget bud = *budget;
@@ -579,6 +617,33 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, con
     c->smem = worker_smem(c->np, k);
     c->rounds_planned = bud.rounds > 0 ? bud.rounds : 0x7fffffff;
     cert_constants(c->np, c->gB, c->gp2);
+    *out = c;
+    return BM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+bm_status bm_fit_footprint(int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                           const bm_budget* budget, int64_t* bytes_out) {
+    if (!bytes_out) return fail(BM_EINVAL, "bytes_out is NULL");
+    bm_fit_ctx* c = nullptr;
+    bm_status s = plan_fit(nullptr, m, n, k, policy, budget, 0, nullptr, &c);
+    if (s) return s;
+    *bytes_out = (int64_t)workspace_bytes(c, c->pol.workers);
+    delete c;
+    return BM_OK;
+}
+
+bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
+                        const bm_budget* budget, uint64_t seed, void* stream, bm_fit_ctx** out) {
+    if (!out) return fail(BM_EINVAL, "out is NULL");
+    *out = nullptr;
+    bm_status s = check_ptr(X_dev, "X_dev");
+    if (s) return s;
+    bm_fit_ctx* c = nullptr;
+    if ((s = plan_fit(X_dev, m, n, k, policy, budget, seed, stream, &c))) return s;
+    const bm_sample_policy& pol = c->pol;
     if ((s = alloc_workspace(c, pol.workers))) { delete c; return s; }
     cudaError_t e;
     if ((e = launch_init_state(c->fhat, pol.workers, c->deg, (long long)pol.workers * k, c->glob, c->st)) ||
@@ -659,6 +724,10 @@ bm_status bm_fit_report(bm_fit_ctx* c, bm_report* rep) {
 void bm_fit_destroy(bm_fit_ctx* c) {
     if (!c) return;
     if (c->prefetched >= 0 && c->ev_sdone) cudaStreamWaitEvent(c->st, c->ev_sdone, 0);
+    // nothing of this fit may still run when its workspace is released (the
+    // stream-ordered allocator may hand the memory to another stream at once)
+    for (cudaStream_t s : c->wst) cudaStreamSynchronize(s);
+    if (c->sst) cudaStreamSynchronize(c->sst);
     if (c->base) {
         cudaFreeAsync(c->base, c->st);
         cudaStreamSynchronize(c->st);

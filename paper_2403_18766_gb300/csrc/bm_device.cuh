@@ -10,6 +10,8 @@
 // * The FP32 direct-form squared distance that defines labels (Eq. 1).
 #pragma once
 #include <cstdint>
+#include <mutex>
+#include <set>
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 
@@ -94,6 +96,28 @@ __host__ __device__ inline uint64_t stream_k1(int purpose, int worker, int round
 // Lemire: accept word w when low64(w * bound) >= (2^64 - bound) mod bound.
 // Host copy of the library's sample-size draw (same Philox4x64-10 and Lemire
 // rule as the device code), used to size each worker's cluster.
+// Raise a kernel's dynamic shared-memory limit to the most the device allows,
+// once per kernel.  The limit is a process-wide attribute of the kernel, so
+// setting it per launch to that launch's size would race between host
+// threads launching the same kernel with different sizes (one thread's
+// smaller value failing the other's launch); every launch still passes its
+// own size.
+inline cudaError_t allow_max_smem(const void* func) {
+    static std::mutex mu;
+    static std::set<const void*> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(func)) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, func);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert(func);
+    return e;
+}
+
 inline uint64_t host_draw_below(uint64_t seed, uint64_t k1, uint64_t c0, uint64_t c1, uint64_t bound) {
     const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
     const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;

@@ -341,8 +341,7 @@ static cudaError_t launch_fullpass_t(const float* X, long long m, int n, const f
                                      const double* sel_f, int W, int* labels, Globals* g, float gB,
                                      float gp2, int incumbent, int sms, cudaStream_t st) {
     const size_t smem = fullpass_smem_bytes(NP, k, n);
-    cudaError_t e = cudaFuncSetAttribute(fullpass_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_max_smem((const void*)fullpass_kernel<NP>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fullpass_kernel<NP>, kFpThreads, smem);

@@ -400,7 +400,7 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
     // at least 80 KB so that at most two CTAs (2 x 256 tensor-memory
     // columns = all 512) share an SM and no allocation has to wait
     const size_t smem = std::max<size_t>(tc_smem_bytes(k, Npad), 80 * 1024);
-    cudaError_t e = cudaFuncSetAttribute(tc_fullpass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem((const void*)tc_fullpass_kernel);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fullpass_kernel, kTcThreads, smem);
@@ -413,7 +413,7 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t rs = (size_t)k * kTcK * 4;
-    e = cudaFuncSetAttribute(rescore_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+    e = allow_max_smem((const void*)rescore_kernel);
     if (e != cudaSuccess) return e;
     rescore_kernel<<<sms * 4, 256, rs, st>>>(Xf, xnorm, m, n, C, k, queue, labels, g);
     return cudaGetLastError();

@@ -523,7 +523,7 @@ cudaError_t launch_t(const CUtensorMap& tm, long long m, const float* C, int k, 
     const int warps_alloc = (threads / 32 + 3) & ~3;            // warps are given registers in fours
     if ((long long)fa.numRegs * 32 * warps_alloc > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
         return cudaErrorNotSupported;
-    e = cudaFuncSetAttribute(tcx_fullpass_kernel<NP, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_smem((const void*)tcx_fullpass_kernel<NP, NG>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcx_fullpass_kernel<NP, NG>, threads, smem);

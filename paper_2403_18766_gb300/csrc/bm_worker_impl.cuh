@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
 template <int NP>
 int worker_max_cluster_t(int k) {
     const size_t smem = worker_smem_bytes<NP>(k);
-    if (cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (allow_max_smem((const void*)worker_kernel<NP>) != cudaSuccess ||
         cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return 8;
@@ -822,8 +822,7 @@ int worker_max_cluster_t(int k) {
 template <int NP>
 cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) {
     const size_t smem = worker_smem_bytes<NP>(a.k);
-    cudaError_t e = cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = allow_max_smem((const void*)worker_kernel<NP>);
     if (e != cudaSuccess) return e;
     if (a.cs > 8) {
         e = cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -14,9 +14,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libbigmeans.so")
 
-BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EINTERNAL = range(6)
+BM_OK, BM_EINVAL, BM_ENOMEM, BM_ECUDA, BM_ETIMEOUT, BM_EINTERNAL, BM_EAGAIN = range(7)
 STATUS_NAMES = {0: "BM_OK", 1: "BM_EINVAL", 2: "BM_ENOMEM", 3: "BM_ECUDA", 4: "BM_ETIMEOUT",
-                5: "BM_EINTERNAL"}
+                5: "BM_EINTERNAL", 6: "BM_EAGAIN"}
 RNG_SIZE, RNG_EVAL, RNG_PASS, RNG_KPP, RNG_FINAL = 1, 2, 3, 4, 5
 
 
@@ -49,6 +49,26 @@ class Report(ctypes.Structure):
         d = {name: getattr(self, name) for name, _ in self._fields_}
         d["trace_cycles"] = list(d["trace_cycles"])
         return d
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("X_host", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("policy", SamplePolicy), ("budget", Budget),
+                ("seed", ctypes.c_uint64), ("C_out_host", ctypes.c_void_p),
+                ("labels_out_host", ctypes.c_void_p)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("state", ctypes.c_int32), ("f_full", ctypes.c_double),
+                ("s_opt", ctypes.c_int64), ("t_submit_s", ctypes.c_double), ("t_admit_s", ctypes.c_double),
+                ("t_done_s", ctypes.c_double), ("footprint_bytes", ctypes.c_int64), ("report", Report)]
+
+
+class CtxInfo(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("in_use_bytes", ctypes.c_int64),
+                ("peak_in_use_bytes", ctypes.c_int64), ("active", ctypes.c_int32),
+                ("peak_active", ctypes.c_int32), ("queued", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("done", ctypes.c_int64), ("now_s", ctypes.c_double)]
 
 
 class BigmeansError(RuntimeError):
@@ -87,6 +107,15 @@ SIGNATURES = {
                               ctypes.POINTER(_dbl), _RP, _p]),
     "bm_set_fullpass_impl": (_i32, [_i32]),
     "bm_last_fullpass_impl": (_i32, []),
+    "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
+    "bm_ctx_create": (_i32, [_i64, _i32, ctypes.POINTER(_p)]),
+    "bm_job_footprint": (_i32, [ctypes.POINTER(Job), ctypes.POINTER(_i64)]),
+    "bm_submit": (_i32, [_p, ctypes.POINTER(Job), ctypes.POINTER(_i64)]),
+    "bm_poll": (_i32, [_p, _i64, ctypes.POINTER(JobResult)]),
+    "bm_wait": (_i32, [_p, _i64, _dbl, ctypes.POINTER(JobResult)]),
+    "bm_job_error": (_i32, [_p, _i64, ctypes.c_char_p, _i64]),
+    "bm_ctx_stats": (_i32, [_p, ctypes.POINTER(CtxInfo)]),
+    "bm_ctx_destroy": (None, [_p]),
     "bm_last_error": (ctypes.c_char_p, []),
     "bm_version": (ctypes.c_char_p, []),
 }
@@ -307,3 +336,77 @@ def assign_bf16(packed, C, tau=1e-3, labels=True, stream=None):
 
 def version():
     return lib.bm_version().decode()
+
+
+def fit_footprint(m, n, k, policy, budget):
+    """bm_fit_footprint: device bytes of a fit's workspace."""
+    b = ctypes.c_int64(0)
+    _check(lib.bm_fit_footprint(int(m), int(n), int(k), ctypes.byref(policy), ctypes.byref(budget), ctypes.byref(b)))
+    return b.value
+
+
+class ServeContext:
+    """Serving context (bm_ctx_*): jobs admitted by device-memory footprint and
+    run concurrently.  Host buffers of a job are kept referenced until it is done."""
+
+    def __init__(self, hbm_budget_bytes, max_active=4):
+        self.ctx = ctypes.c_void_p(0)
+        _check(lib.bm_ctx_create(int(hbm_budget_bytes), int(max_active), ctypes.byref(self.ctx)))
+        self._keep = {}
+
+    def submit(self, X, k, policy, budget, seed=0, labels=True):
+        """X: host float32 array (numpy or CPU tensor, pinned preferred). Returns the job id."""
+        if isinstance(X, torch.Tensor):
+            Xt = X.contiguous()
+            assert Xt.device.type == "cpu" and Xt.dtype == torch.float32
+            m, n = Xt.shape
+            xptr = Xt.data_ptr()
+        else:
+            Xt = np.ascontiguousarray(X, dtype=np.float32)
+            m, n = Xt.shape
+            xptr = Xt.ctypes.data
+        pin = torch.cuda.is_available()
+        C = torch.empty((k, n), dtype=torch.float32, pin_memory=pin)
+        Y = torch.empty(m, dtype=torch.int32, pin_memory=pin) if labels else None
+        job = Job(X_host=xptr, m=m, n=n, k=k, policy=policy, budget=budget, seed=seed,
+                  C_out_host=C.data_ptr(), labels_out_host=(Y.data_ptr() if Y is not None else 0))
+        jid = ctypes.c_int64(0)
+        _check(lib.bm_submit(self.ctx, ctypes.byref(job), ctypes.byref(jid)))
+        self._keep[jid.value] = (Xt, C, Y, job)
+        return jid.value
+
+    def _result(self, jid, res):
+        d = {name: getattr(res, name) for name, _ in res._fields_ if name != "report"}
+        d["report"] = res.report.as_dict()
+        if res.state == 2:
+            Xt, C, Y, _ = self._keep[jid]
+            d["C"], d["labels"] = C, Y
+            if res.status != BM_OK:
+                buf = ctypes.create_string_buffer(512)
+                lib.bm_job_error(self.ctx, jid, buf, 512)
+                d["error"] = buf.value.decode()
+        return d
+
+    def poll(self, jid):
+        res = JobResult()
+        st = lib.bm_poll(self.ctx, int(jid), ctypes.byref(res))
+        if st not in (BM_OK, BM_EAGAIN):
+            _check(st)
+        return self._result(jid, res)
+
+    def wait(self, jid, timeout=None):
+        res = JobResult()
+        st = lib.bm_wait(self.ctx, int(jid), -1.0 if timeout is None else float(timeout), ctypes.byref(res))
+        if st not in (BM_OK, BM_EAGAIN):
+            _check(st)
+        return self._result(jid, res)
+
+    def stats(self):
+        info = CtxInfo()
+        _check(lib.bm_ctx_stats(self.ctx, ctypes.byref(info)))
+        return {name: getattr(info, name) for name, _ in info._fields_ if name != "pad_"}
+
+    def close(self):
+        if self.ctx:
+            lib.bm_ctx_destroy(self.ctx)
+            self.ctx = ctypes.c_void_p(0)
