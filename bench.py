@@ -406,6 +406,91 @@ def run_precision(args):
     return 0
 
 
+def run_batched(args):
+    """Workload 3: 64 competing workers on one 4e6 x 32 mixture (50 Gaussians
+    + 1% outliers), sample sizes octave-uniform (the integer stand-in for
+    log-uniform) in [2000, 131072], k in {10, 25, 50} per worker.  Workers
+    with different k cannot compete on one objective, so they form three
+    Big-means groups (22 / 21 / 21 workers, k assigned round-robin), each its
+    own fit; the three fits run at once from three host threads (their
+    kernels overlap on the GPU).  The cluster tile is autotuned first.  A step
+    is one round of all 64 workers; the value is Lloyd pts*k/s over all
+    groups, device-resident X, L2 flushed between steps."""
+    import threading
+    import torch
+    from paper_2403_18766_gb300 import native
+    from paper_2403_18766_gb300.synthetic import workload
+    X = workload("gmm_4m_n32_k50o", m=args.rows)
+    m, n = X.shape
+    Xd = torch.from_numpy(X).cuda()
+    groups = [(10, 22), (25, 21), (50, 21)]
+    pols = {k: native.make_policy(s_min=2000, s_max=131072, workers=w, passes=10, kind=1) for k, w in groups}
+    total_rounds = args.warmup + args.steps
+    tuned, tune_ms = native.autotune_rows_per_cta(Xd, 25, pols[25], native.make_budget(rounds=2), seed=5,
+                                                  candidates=(1024, 2048, 4096, 8192))
+    sess = {k: native.FitSession(Xd, k, pols[k], native.make_budget(rounds=total_rounds), seed=300 + k,
+                                 stream=torch.cuda.Stream()) for k, _ in groups}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_round():
+        errs = []
+
+        def run(k):
+            try:
+                sess[k].rounds(1)
+            except Exception as e:               # noqa: BLE001 - reported below
+                errs.append(e)
+        th = [threading.Thread(target=run, args=(k,)) for k, _ in groups]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        if errs:
+            raise errs[0]
+
+    for _ in range(args.warmup):
+        one_round()
+    rep0 = {k: sess[k].report() for k, _ in groups}
+    clocks = ClockSampler(0)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one_round()
+        torch.cuda.synchronize()
+        step_ms.append((time.perf_counter() - t0) * 1e3)
+    clk = clocks.stop()
+    rep1 = {k: sess[k].report() for k, _ in groups}
+    ptsk = sum((rep1[k]["assign_rows"] - rep0[k]["assign_rows"]) * k for k, _ in groups)
+    flops = sum(2.0 * n * k * (rep1[k]["assign_rows"] - rep0[k]["assign_rows"]) for k, _ in groups)
+    fin = {}
+    for k, _ in groups:
+        C, _, r = sess[k].finish(labels=False)
+        fin[k] = {"f_full": r["f_full"], "s_opt": r["s_opt"]}
+        sess[k].close()
+    native.set_rows_per_cta(0)
+    t = sum(step_ms) / 1e3
+    peaks, src = _peaks()
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", NOMINAL_MAX_MHZ))
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    line = {"metric": "Lloyd pts\u00b7k/s (batched workers, workload 3)", "value": ptsk / t, "unit": UNIT,
+            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3 / args.steps, "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": flops / t / 1e12 / alu_peak,
+                         "kernel": "worker_kernel<32> x 64 + sample_kernel<32> x 3 per step (wall time of the step)",
+                         "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+            "autotune": {"rows_per_cta": tuned, "round_ms": tune_ms},
+            "groups": {str(k): fin[k] for k, _ in groups}, "clocks": clk,
+            "config": {"workload": f"gmm_4m_n32_k50o: m={m}, n={n}, 50 Gaussians + 1% outliers; 64 workers "
+                                   "as 3 groups k=10/25/50 (22/21/21), s octave-uniform in [2000, 131072], p=10",
+                       "l2": "flushed between timed steps", "step": "one round of all 64 workers"}}
+    print(json.dumps(line))
+    return 0
+
+
 def run_serve(args):
     """Serving: Poisson arrivals of clustering jobs of mixed m, n, k on one
     serving context (continuous batching under a device-memory budget).
@@ -485,7 +570,7 @@ def main():
     ap.add_argument("--k", type=int, default=None, help="kernel modes: number of centroids")
     ap.add_argument("--centroids", choices=["rows", "fit"], default="rows",
                     help="kernel modes: centroids from evenly spaced rows, or from a short fit")
-    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision", "serve"], default="fit",
+    ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision", "serve", "batched"], default="fit",
                     help="fit: the headline benchmark; fullpass / lloyd: one kernel family, "
                          "for profiling")
     args = ap.parse_args()
@@ -493,6 +578,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "batched":
+        return run_batched(args)
     if args.mode == "precision":
         return run_precision(args)
     if args.mode != "fit":

@@ -312,6 +312,27 @@ bm_status bm_set_fullpass_impl(int32_t impl);
 int32_t bm_last_fullpass_impl(void);
 
 /* ---------------------------------------------------------------------------
+ * Cluster tile of the worker kernel and its autotuner.
+ * A worker runs as one thread-block cluster of up to 16 CTAs with about
+ * `rows_per_cta` sample rows per CTA (default 2048).  The value changes only
+ * speed: labels, centroids and objectives are identical for every value (all
+ * reductions are exact).  The setting is process-wide and read when a fit is
+ * created.
+ * bm_set_rows_per_cta: 0 restores the default; otherwise 256 .. 32767.
+ * bm_autotune_rows_per_cta: for each candidate, creates a 2-round fit of the
+ * given arguments, runs round 0 as warm-up and times round 1 with CUDA
+ * events on `stream`; sets the fastest candidate as the process value and
+ * returns it in *best_out (per-candidate milliseconds in ms_out, n_candidates
+ * entries, may be NULL).  1 <= n_candidates <= 16.
+ * ------------------------------------------------------------------------- */
+bm_status bm_set_rows_per_cta(int32_t rows);
+int32_t bm_get_rows_per_cta(void);
+bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
+                                   const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
+                                   void* stream, const int32_t* candidates, int32_t n_candidates,
+                                   int32_t* best_out, double* ms_out);
+
+/* ---------------------------------------------------------------------------
  * bm_fit_footprint -- device bytes of the workspace a fit with these
  * arguments allocates (bigmeans_fit / bm_fit_create), without allocating.
  * Same argument checks as bm_fit_create.

@@ -10,6 +10,7 @@
 // Everything is enqueued on the caller's stream; each entry point
 // synchronises that stream once before returning.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <chrono>
 #include <cmath>
@@ -139,10 +140,15 @@ long long draw_cap(long long m, long long s) {
     return (long long)std::ceil(cap);
 }
 
-// CTAs per worker cluster: about kRowsPerCta sample rows per CTA, at most
+// Target sample rows per CTA of a worker cluster (the tile the autotuner
+// chooses; results do not depend on it: every reduction is exact).
+std::atomic<int> g_rows_per_cta{kRowsPerCta};
+
+// CTAs per worker cluster: about rows_per_cta sample rows per CTA, at most
 // max_cs, and never more than kMaxRowsPerCta rows per CTA (0 = impossible).
-int cluster_size(long long s_cap, int max_cs) {
-    long long cs = std::max<long long>(1, (s_cap + kRowsPerCta - 1) / kRowsPerCta);
+int cluster_size(long long s_cap, int max_cs, int rows_per_cta = 0) {
+    const long long rpc = rows_per_cta > 0 ? rows_per_cta : g_rows_per_cta.load();
+    long long cs = std::max<long long>(1, (s_cap + rpc - 1) / rpc);
     cs = std::min<long long>(cs, max_cs);
     while (cs < max_cs && (s_cap + cs - 1) / cs > kMaxRowsPerCta) ++cs;
     if ((s_cap + cs - 1) / cs > kMaxRowsPerCta) return 0;
@@ -176,6 +182,7 @@ struct bm_fit_ctx {
     Globals* glob = nullptr;
     int jobs = 0;                           // sample jobs per round: W * (P + 1)
     int prefetched = -1;                    // round whose samples were drawn ahead
+    int rows_per_cta = 0;                   // cluster tile of this fit (fixed at create)
     long long L_sum0 = 0, L_len0 = 0;       // L at the start of the current round (exploit policy)
     int rounds_planned = 0x7fffffff;        // rounds the caller intends to run (T)
     cudaStream_t sst = nullptr;             // sampling stream (draws the next round ahead)
@@ -497,7 +504,7 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         a.round_end = r1;
         a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
         a.worker_base = w;
-        a.cs = cluster_size(smax, c->max_cs);
+        a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta);
         launch_err = launch_worker(c->np, a, 1, c->wst[w % ns]);
         if (launch_err == cudaSuccess) c->n_kernels++;
     }
@@ -603,7 +610,8 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
     c->pol = pol; c->bud = bud; c->seed = seed;
     c->s_lo = s_lo; c->s_hi = s_hi; c->s_cap = s_hi;
     c->max_cs = worker_max_cluster(c->np, k);
-    c->cs = cluster_size(s_hi, c->max_cs);
+    c->rows_per_cta = g_rows_per_cta.load();
+    c->cs = cluster_size(s_hi, c->max_cs, c->rows_per_cta);
     if (c->cs == 0) {
         delete c;
         return fail(BM_EINVAL, "s_max = %lld above %lld", s_hi, (long long)c->max_cs * kMaxRowsPerCta);
@@ -623,6 +631,56 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
 }  // namespace
 
 extern "C" {
+
+bm_status bm_set_rows_per_cta(int32_t rows) {
+    if (rows == 0) rows = kRowsPerCta;
+    if (rows < 256 || rows > kMaxRowsPerCta) return fail(BM_EINVAL, "rows per CTA = %d out of [256, %lld]", rows,
+                                                         (long long)kMaxRowsPerCta);
+    g_rows_per_cta.store(rows);
+    return BM_OK;
+}
+int32_t bm_get_rows_per_cta(void) { return g_rows_per_cta.load(); }
+
+bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
+                                   const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
+                                   void* stream, const int32_t* candidates, int32_t n_candidates,
+                                   int32_t* best_out, double* ms_out) {
+    if (!candidates || n_candidates < 1 || n_candidates > 16 || !best_out || !budget)
+        return fail(BM_EINVAL, "autotune: bad candidate list or outputs");
+    const int keep = g_rows_per_cta.load();
+    bm_budget bud = *budget;
+    bud.rounds = 2;
+    bud.seconds = 0;
+    double best_ms = 1e300;
+    int best = keep;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < n_candidates; ++i) {
+        bm_status s = bm_set_rows_per_cta(candidates[i]);
+        if (s) { g_rows_per_cta.store(keep); return s; }
+        bm_fit_ctx* c = nullptr;
+        if ((s = bm_fit_create(X_dev, m, n, k, policy, &bud, seed, stream, &c))) { g_rows_per_cta.store(keep); return s; }
+        cudaEvent_t a = nullptr, b = nullptr;
+        float ms = 0.f;
+        if ((s = bm_fit_rounds(c, 1)) == BM_OK) {              // round 0 warms up
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, st);
+            s = bm_fit_rounds(c, 1);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&ms, a, b);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+        bm_fit_destroy(c);
+        if (s) { g_rows_per_cta.store(keep); return s; }
+        if (ms_out) ms_out[i] = ms;
+        if (ms < best_ms) { best_ms = ms; best = candidates[i]; }
+    }
+    g_rows_per_cta.store(best);
+    *best_out = best;
+    return BM_OK;
+}
 
 bm_status bm_fit_footprint(int64_t m, int32_t n, int32_t k, const bm_sample_policy* policy,
                            const bm_budget* budget, int64_t* bytes_out) {

@@ -108,6 +108,10 @@ SIGNATURES = {
     "bm_set_fullpass_impl": (_i32, [_i32]),
     "bm_last_fullpass_impl": (_i32, []),
     "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
+    "bm_set_rows_per_cta": (_i32, [_i32]),
+    "bm_get_rows_per_cta": (_i32, []),
+    "bm_autotune_rows_per_cta": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_i32), _i32,
+                                        ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
     "bm_ctx_create": (_i32, [_i64, _i32, ctypes.POINTER(_p)]),
     "bm_job_footprint": (_i32, [ctypes.POINTER(Job), ctypes.POINTER(_i64)]),
     "bm_submit": (_i32, [_p, ctypes.POINTER(Job), ctypes.POINTER(_i64)]),
@@ -410,3 +414,25 @@ class ServeContext:
         if self.ctx:
             lib.bm_ctx_destroy(self.ctx)
             self.ctx = ctypes.c_void_p(0)
+
+
+def set_rows_per_cta(rows):
+    """bm_set_rows_per_cta (0 = default)."""
+    _check(lib.bm_set_rows_per_cta(int(rows)))
+
+
+def get_rows_per_cta():
+    return int(lib.bm_get_rows_per_cta())
+
+
+def autotune_rows_per_cta(X, k, policy, budget, seed=0, candidates=(1024, 2048, 4096, 8192), stream=None):
+    """bm_autotune_rows_per_cta: times one round per candidate, keeps the fastest.
+    Returns (best, {candidate: ms})."""
+    X = _dev_f32(X, "X")
+    cand = (ctypes.c_int32 * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_int32(0)
+    _check(lib.bm_autotune_rows_per_cta(_ptr(X), X.shape[0], X.shape[1], int(k), ctypes.byref(policy),
+                                        ctypes.byref(budget), int(seed), _stream(stream), cand, len(candidates),
+                                        ctypes.byref(best), ms))
+    return best.value, {int(c): float(t) for c, t in zip(candidates, ms)}

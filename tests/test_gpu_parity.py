@@ -258,3 +258,36 @@ def test_fit_size_policies_bit_exact(pol, rounds, seed):
     C, Y, rep, ref = _fit_both(X, 6, pol, bud, seed=seed)
     _assert_same(C, Y, rep, ref)
     assert rep["lloyd_iters"] == ref["log"]["lloyd_iters"]
+
+
+# ------------------------------------------- cluster tile (autotuner knob)
+def test_results_do_not_depend_on_the_cluster_tile():
+    X = gaussian_mixture(60_000, 16, 12, seed=31)
+    pol = dict(s_min=3000, s_max=40_000, workers=4, passes=2, kind=1)
+    bud = dict(rounds=2, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    outs = []
+    try:
+        for rows in (512, 0, 8192):
+            native.set_rows_per_cta(rows)
+            outs.append(native.fit(_t(X), 12, native.make_policy(**pol), native.make_budget(**bud), seed=3))
+    finally:
+        native.set_rows_per_cta(0)
+    (C0, Y0, r0) = outs[0]
+    for C, Y, r in outs[1:]:
+        assert torch.equal(C.view(torch.int32), C0.view(torch.int32)) and torch.equal(Y, Y0)
+        assert r["f_full"] == r0["f_full"] and r["lloyd_iters"] == r0["lloyd_iters"]
+    ref = obm.bigmeans(X, 12, pol, bud, seed=3)
+    _assert_same(C0.cpu().numpy(), Y0.cpu().numpy(), r0, ref)
+
+
+def test_autotuner_picks_a_candidate_and_sets_it():
+    X = gaussian_mixture(80_000, 32, 10, seed=32)
+    pol = native.make_policy(s_min=2000, s_max=50_000, workers=6, passes=2, kind=1)
+    try:
+        best, ms = native.autotune_rows_per_cta(_t(X), 10, pol, native.make_budget(rounds=2), seed=1,
+                                                candidates=(1024, 4096))
+        assert best in (1024, 4096) and native.get_rows_per_cta() == best
+        assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
+    finally:
+        native.set_rows_per_cta(0)
+    assert native.get_rows_per_cta() == 2048

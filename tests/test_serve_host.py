@@ -49,3 +49,14 @@ def test_footprint_is_workspace_plus_buffers():
     # more workers or larger samples need more workspace; m alone only changes the tables
     assert native.fit_footprint(m, n, k, _pol(workers=16), bud) > ws
     assert native.fit_footprint(m, n, k, _pol(workers=8, s_max=50_000), bud) > ws
+
+
+def test_cluster_tile_setting_is_checked():
+    assert native.get_rows_per_cta() == 2048
+    for bad in (-1, 100, 40_000):
+        with pytest.raises(native.BigmeansError):
+            native.set_rows_per_cta(bad)
+    native.set_rows_per_cta(4096)
+    assert native.get_rows_per_cta() == 4096
+    native.set_rows_per_cta(0)
+    assert native.get_rows_per_cta() == 2048
