@@ -196,6 +196,16 @@ struct Worker {
 #pragma unroll
             for (int r = 0; r < RT; ++r)
                 oldlab[r] = (mode == 2 && base + r < hi) ? lab_prev[base + r] : -1;
+            {   // start the L2 -> L1 fetch of this thread's rows of the next trip
+                const long long nb = base + (long long)kThreads * RT;
+                if (nb < hi) {
+                    const char* pn = reinterpret_cast<const char*>(S + nb * NP);
+#pragma unroll
+                    for (int o = 0; o < RT * NP * 4; o += 128)
+                        asm volatile("prefetch.global.L1 [%0];" ::"l"(pn + o));
+                    if (mode == 2) asm volatile("prefetch.global.L1 [%0];" ::"l"(lab_prev + nb));
+                }
+            }
             float g1[RT], g2[RT];
             int j1[RT];
 #pragma unroll
