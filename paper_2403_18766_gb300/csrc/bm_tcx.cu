@@ -213,15 +213,17 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         // ---------------------------------------------------------- producer
         if (lane == 0) {
             long long it = 0;
+            int s = 0;
+            unsigned ph = 0;                                // (it / S) & 1, kept incrementally
             for (;; ++it) {
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
-                const int s = (int)(it % S);
-                if (it >= S && !tc::wait(&empty[s], (unsigned)((it / S - 1) & 1), abort, g)) break;
+                if (it >= S && !tc::wait(&empty[s], ph ^ 1u, abort, g)) break;
                 tc::expect_tx(&full[s], (unsigned)tile_bytes);
                 for (int a = 0; a < sh.atoms; ++a)
                     tc::tma_load_2d(xs + (size_t)s * tile_bytes + (size_t)a * kTxAtomBytes, &tmap, 32 * a,
                                     (int)(tile * kTxRows), &full[s]);
+                if (++s == S) { s = 0; ph ^= 1u; }
             }
             if (*abort)       // drain the copies still in flight before the CTA exits
                 for (long long i = (it > S ? it - S : 0); i < it; ++i)
@@ -233,14 +235,16 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             const unsigned idesc = tc::idesc_tf32(kTxRows, sh.Npad);
             const unsigned bstride = (unsigned)(sh.Npad * 128);
             long long it = 0;
+            int s = 0;                                      // it % S, kept incrementally
             for (;; ++it) {
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
                 const int b = (int)(it % NG);
                 if (!tc::wait(&conv[b], (unsigned)((it / NG) & 1), abort, g)) break;
                 tc::fence_after();
-                const unsigned ax = tc::s_addr(sh.inplace ? xs + (size_t)(it % S) * tile_bytes
+                const unsigned ax = tc::s_addr(sh.inplace ? xs + (size_t)s * tile_bytes
                                                           : xh + (size_t)b * tile_bytes);
+                if (++s == S) s = 0;
                 const unsigned al = tc::s_addr(xl + (size_t)b * tile_bytes);
                 const unsigned ah = tc::s_addr(bh), alo = tc::s_addr(bl);
                 const unsigned d = tmem + (unsigned)(b * sh.acc_stride);
@@ -271,16 +275,17 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         const int r = q4 * 32 + lane;                        // row within the tile = TMEM lane
         unsigned char* xlb = xl + (size_t)b * tile_bytes;
         const unsigned cstride = (unsigned)(sh.Npad * 128);
+        int s = b;                                          // it % S and (it / S) & 1, kept
+        unsigned ph = 0;                                    // incrementally (S is a multiple of NG)
         for (long long it = b;; it += NG) {
             const long long tile = blockIdx.x + it * grid;
             if (tile >= ntiles) break;
-            const int s = (int)(it % S);
             unsigned char* st = xs + (size_t)s * tile_bytes;
             unsigned char* xhb = sh.inplace ? st : xh + (size_t)b * tile_bytes;
             // 1. the row: hi(x) and r(x) into this group's buffers; the stage
             //    is free again as soon as every warp of the group has read it
             int ok = 1;
-            if (lane == 0) ok = tc::wait(&full[s], (unsigned)((it / S) & 1), abort, g);
+            if (lane == 0) ok = tc::wait(&full[s], ph, abort, g);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             float xn2 = 0.f;
@@ -416,6 +421,8 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 acc_obj(facc, dv, gr.gf, inex);
                 if (labels) labels[row] = lab;
             }
+            s += NG;
+            if (s >= S) { s -= S; ph ^= 1u; }
         }
     }
 
