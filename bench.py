@@ -55,6 +55,24 @@ def _dist():
     return ws, rank
 
 
+def rank_seed(rank):
+    """Seed of the independent fit a rank runs (weak scaling: one problem per rank)."""
+    return 1000 + int(rank)
+
+
+def aggregate(t_local, work_local, device="cpu"):
+    """Whole-job numbers over the ranks of the default process group: the
+    slowest rank's time and the total work (units all ranks processed).
+    Works with any backend (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(work_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -185,10 +203,19 @@ def run_ours(args):
     bud = native.make_budget(rounds=total_rounds, **BUDGET)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    sess = native.FitSession(Xd, K_CLUSTERS, pol, bud, seed=1000 + rank)
+    sess = native.FitSession(Xd, K_CLUSTERS, pol, bud, seed=rank_seed(rank))
     clocks = ClockSampler(local)
+    trace = []                                  # (cumulative device s, f_incumbent) after each round
+    t_cum = 0.0
     for _ in range(args.warmup):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         sess.rounds(1)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t_cum += a.elapsed_time(b) / 1e3
+        trace.append((t_cum, sess.report()["f_incumbent"]))
     rep0 = sess.report()
     step_ms = []
     for _ in range(args.steps):
@@ -203,7 +230,11 @@ def run_ours(args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         step_ms.append(a.elapsed_time(b))
+        t_cum += step_ms[-1] / 1e3
+        trace.append((t_cum, sess.report()["f_incumbent"]))
     rep1 = sess.report()
+    f_end = trace[-1][1]
+    tto = next(((t, i + 1) for i, (t, f) in enumerate(trace) if f <= f_end * (1 + 1e-4)), (None, None))
     clk = clocks.stop()
     C, _, rep_fin = sess.finish(labels=False)
     sess.close()
@@ -217,12 +248,7 @@ def run_ours(args):
     t_full = rep1["t_fullpass_s"] - rep0["t_fullpass_s"]
     n_full = rep1["fullpass_launches"] - rep0["fullpass_launches"]
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        p = torch.tensor([float(ptsk_local)], dtype=torch.float64, device=dev)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        t_job, ptsk = float(t.item()), float(p.item())
+        t_job, ptsk = aggregate(t_local, ptsk_local, dev)
     else:
         t_job, ptsk = t_local, float(ptsk_local)
 
@@ -283,6 +309,9 @@ def run_ours(args):
                 "roofline": roofline, "roofline_fullpass": roof_full,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk,
+                "time_to_objective": {"target": "incumbent f(C, X) within 1e-4 (relative) of its value after "
+                                                "the last round", "seconds": tto[0], "rounds": tto[1],
+                                      "f_end": f_end, "trace": [[round(t, 6), f] for t, f in trace]},
                 "detail": {"step_ms": step_ms, "lloyd_rows": rows, "worker_ms_per_launch":
                            t_worker / max(n_worker, 1) * 1e3,
                            "rescored_rows": rep1["rescored_rows"],
