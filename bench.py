@@ -594,6 +594,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rate", type=float, default=150.0, help="serve mode: job arrivals per second")
+    ap.add_argument("--big-clusters", type=int, default=None, choices=[0, 1],
+                    help="512-thread CTAs for the workers whose cluster is at the size cap")
     ap.add_argument("--workload", default=None, help="kernel modes: workload name (default: the headline's)")
     ap.add_argument("--rows", type=int, default=None, help="kernel modes: rows of the workload to use")
     ap.add_argument("--k", type=int, default=None, help="kernel modes: number of centroids")
@@ -605,6 +607,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.big_clusters is not None and args.impl == "ours":
+        from paper_2403_18766_gb300 import native
+        native.set_big_clusters(args.big_clusters)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "batched":

@@ -327,6 +327,12 @@ int32_t bm_last_fullpass_impl(void);
  * ------------------------------------------------------------------------- */
 bm_status bm_set_rows_per_cta(int32_t rows);
 int32_t bm_get_rows_per_cta(void);
+/* on = 1: a worker whose cluster is at the size cap (16 CTAs) and still holds
+ * more than rows_per_cta sample rows per CTA runs with 512-thread CTAs (one
+ * per SM) instead of 256; on = 0 (default): always 256.  Speed only, as for
+ * the tile.  Process-wide, read at each round's launch. */
+bm_status bm_set_big_clusters(int32_t on);
+int32_t bm_get_big_clusters(void);
 bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
                                    const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
                                    void* stream, const int32_t* candidates, int32_t n_candidates,

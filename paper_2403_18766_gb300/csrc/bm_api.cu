@@ -143,6 +143,9 @@ long long draw_cap(long long m, long long s) {
 // Target sample rows per CTA of a worker cluster (the tile the autotuner
 // chooses; results do not depend on it: every reduction is exact).
 std::atomic<int> g_rows_per_cta{kRowsPerCta};
+// 1: workers whose cluster is at the size cap and still above the tile run
+// with 512-thread CTAs (twice the warps per SM for the longest workers).
+std::atomic<int> g_big_tpb{0};
 
 // CTAs per worker cluster: about rows_per_cta sample rows per CTA, at most
 // max_cs, and never more than kMaxRowsPerCta rows per CTA (0 = impossible).
@@ -505,6 +508,9 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
         a.worker_base = w;
         a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta);
+        // clusters at the size cap with more rows per CTA than the tile get
+        // 512-thread CTAs (one per SM) when the big-cluster option is on
+        a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
         launch_err = launch_worker(c->np, a, 1, c->wst[w % ns]);
         if (launch_err == cudaSuccess) c->n_kernels++;
     }
@@ -640,6 +646,13 @@ bm_status bm_set_rows_per_cta(int32_t rows) {
     return BM_OK;
 }
 int32_t bm_get_rows_per_cta(void) { return g_rows_per_cta.load(); }
+
+bm_status bm_set_big_clusters(int32_t on) {
+    if (on != 0 && on != 1) return fail(BM_EINVAL, "big-cluster option = %d must be 0 or 1", on);
+    g_big_tpb.store(on);
+    return BM_OK;
+}
+int32_t bm_get_big_clusters(void) { return g_big_tpb.load(); }
 
 bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
                                    const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,

@@ -20,6 +20,7 @@ namespace cg = cooperative_groups;
 
 constexpr int kThreads = 256;          // threads per CTA of the worker, sampling and prepass kernels
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxWarps = 16;            // largest CTA of any kernel here: 512 threads
 constexpr int kMaxCluster = 16;        // CTAs per worker cluster (non-portable above 8)
 
 // ------------------------------------------------------------------ globals
@@ -313,7 +314,9 @@ __device__ __forceinline__ unsigned __int128 warp_sum_u128(unsigned __int128 v) 
     return v;
 }
 
-// Sum over the CTA; result valid in thread 0.  `red` holds kWarps entries.
+// Block reductions over all warps of the CTA (blockDim.x / 32 of them);
+// `red` holds at least that many entries (one more for the scan).
+// Sum over the CTA; result valid in thread 0.
 template <typename T>
 __device__ __forceinline__ T block_sum(T v, T* red) {
     v = warp_sum(v);
@@ -323,7 +326,7 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
     __syncthreads();
     T s = 0;
     if (threadIdx.x == 0)
-        for (int i = 0; i < kWarps; ++i) s += red[i];
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     return s;
 }
 
@@ -335,7 +338,7 @@ __device__ __forceinline__ unsigned __int128 block_sum_u128(unsigned __int128 v,
     __syncthreads();
     unsigned __int128 s = 0;
     if (threadIdx.x == 0)
-        for (int i = 0; i < kWarps; ++i) s += red[i];
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
     return s;
 }
 
@@ -348,7 +351,7 @@ __device__ __forceinline__ unsigned int block_max_u32(unsigned int v, unsigned i
     __syncthreads();
     unsigned int s = 0;
     if (threadIdx.x == 0)
-        for (int i = 0; i < kWarps; ++i) s = max(s, red[i]);
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s = max(s, red[i]);
     return s;
 }
 
@@ -367,12 +370,13 @@ __device__ __forceinline__ long long block_exscan(long long v, long long* red, l
     __syncthreads();
     if (threadIdx.x == 0) {
         long long run = 0;
-        for (int i = 0; i < kWarps; ++i) { const long long t = red[i]; red[i] = run; run += t; }
-        red[kWarps] = run;
+        const int nw = (int)(blockDim.x >> 5);
+        for (int i = 0; i < nw; ++i) { const long long t = red[i]; red[i] = run; run += t; }
+        red[nw] = run;
     }
     __syncthreads();
     const long long excl = red[wid] + x - v;
-    *total = red[kWarps];
+    *total = red[blockDim.x >> 5];
     __syncthreads();
     return excl;
 }

@@ -31,6 +31,7 @@ struct WorkerArgs {
     unsigned long long deadline_ns;   // %globaltimer deadline, 0 = none
     int mode;
     int cs;                           // CTAs per cluster
+    int tpb;                          // threads per CTA: 256, or 512 (largest clusters)
     Globals* glob;
     // samples drawn by the sampling kernel: job (w, slot) = w * (P + 1) + slot
     float* S; long long S_stride;                 // s_cap * NP floats per job
@@ -81,9 +82,9 @@ __host__ __device__ inline size_t worker_smem_bytes(int k) {
     b += align16((size_t)k * 4);                // cnt
     b += align16((size_t)k) * 3;                // deg, empty, emptyall
     b += align16(sizeof(Xch));
-    b += align16(sizeof(unsigned __int128) * kWarps);
-    b += align16(8 * (kWarps + 1));
-    b += align16(4 * kWarps);
+    b += align16(sizeof(unsigned __int128) * kMaxWarps);
+    b += align16(8 * (kMaxWarps + 1));
+    b += align16(4 * kMaxWarps);
     b += align16(sizeof(CertC));
     b += align16(8 * 16);
     return b;

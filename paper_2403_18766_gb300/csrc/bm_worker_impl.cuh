@@ -31,9 +31,9 @@ struct Sm {
     unsigned char* empty; // k       owner-computed empties of the last assignment
     unsigned char* emptyall;  // k   gathered empties
     Xch* x;
-    unsigned __int128* red128;    // kWarps
-    long long* red64;             // kWarps + 1
-    unsigned int* redu;           // kWarps
+    unsigned __int128* red128;    // one per warp (kMaxWarps)
+    long long* red64;             // one per warp, + 1
+    unsigned int* redu;           // one per warp
     CertC* cert;
     long long* bcast;             // broadcast slots: 0 f, 1 stop, 2 M/pick, 3 base,
                                   // 4 total, 5-7 candidates, 8 deadline flag
@@ -53,9 +53,9 @@ __device__ inline Sm<NP> carve(int k) {
     s.empty = p;                   p += align16((size_t)k);
     s.emptyall = p;                p += align16((size_t)k);
     s.x = (Xch*)p;                 p += align16(sizeof(Xch));
-    s.red128 = (unsigned __int128*)p; p += align16(sizeof(unsigned __int128) * kWarps);
-    s.red64 = (long long*)p;       p += align16(8 * (kWarps + 1));
-    s.redu = (unsigned int*)p;     p += align16(4 * kWarps);
+    s.red128 = (unsigned __int128*)p; p += align16(sizeof(unsigned __int128) * kMaxWarps);
+    s.red64 = (long long*)p;       p += align16(8 * (kMaxWarps + 1));
+    s.redu = (unsigned int*)p;     p += align16(4 * kMaxWarps);
     s.cert = (CertC*)p;            p += align16(sizeof(CertC));
     s.bcast = (long long*)p;
     return s;
@@ -65,7 +65,8 @@ template <int NP>
 struct RowsPerThread { static constexpr int v = (64 / NP) > 8 ? 8 : ((64 / NP) < 1 ? 1 : 64 / NP); };
 
 // ---------------------------------------------------------------- the CTA
-template <int NP>
+// TPB: threads per CTA (256, or 512 for the largest clusters).
+template <int NP, int TPB>
 struct Worker {
     const WorkerArgs& a;
     cg::cluster_group cl;
@@ -118,17 +119,17 @@ struct Worker {
 
     // ------------------------------------------------------ centroid prep
     __device__ void load_centroids(const float* src) {
-        for (int e = threadIdx.x; e < k * NP; e += kThreads) sm.Ccur[e] = src[e];
+        for (int e = threadIdx.x; e < k * NP; e += TPB) sm.Ccur[e] = src[e];
         __syncthreads();
     }
     __device__ void store_centroids(float* dst) {
-        for (int e = threadIdx.x; e < k * NP; e += kThreads) dst[e] = sm.Ccur[e];
+        for (int e = threadIdx.x; e < k * NP; e += TPB) dst[e] = sm.Ccur[e];
         __syncthreads();
     }
     // fl(||c_j||^2) as an FMA chain and the certificate's upper bounds.
     __device__ void prep_centroids() {
         unsigned int mx = 0;
-        for (int j = threadIdx.x; j < k; j += kThreads) {
+        for (int j = threadIdx.x; j < k; j += TPB) {
             const float* c = sm.Ccur + (size_t)j * NP;
             float acc = 0.f, up = 0.f;
 #pragma unroll
@@ -159,8 +160,8 @@ struct Worker {
         long long lo, hi;
         slice(s, lo, hi);
         if (mode == 1) {
-            for (int e = threadIdx.x; e < k * acc_stride<NP>(); e += kThreads) sm.ACC[e] = 0;
-            for (int e = threadIdx.x; e < k; e += kThreads) sm.cnt[e] = 0;
+            for (int e = threadIdx.x; e < k * acc_stride<NP>(); e += TPB) sm.ACC[e] = 0;
+            for (int e = threadIdx.x; e < k; e += TPB) sm.cnt[e] = 0;
         }
         __syncthreads();
         const long long t_loop = clock64();
@@ -173,7 +174,7 @@ struct Worker {
         const int lane = threadIdx.x & 31;
         // warp-uniform trip count (the move step below uses warp ballots)
         for (long long base0 = lo + (long long)(threadIdx.x & ~31) * RT; base0 < hi;
-             base0 += (long long)kThreads * RT) {
+             base0 += (long long)TPB * RT) {
             const long long base = base0 + (long long)lane * RT;
             float2 m2x[RT][NP / 2];                          // -2 x, dimension pairs
 #pragma unroll
@@ -197,7 +198,7 @@ struct Worker {
             for (int r = 0; r < RT; ++r)
                 oldlab[r] = (mode == 2 && base + r < hi) ? lab_prev[base + r] : -1;
             {   // start the L2 -> L1 fetch of this thread's rows of the next trip
-                const long long nb = base + (long long)kThreads * RT;
+                const long long nb = base + (long long)TPB * RT;
                 if (nb < hi) {
                     const char* pn = reinterpret_cast<const char*>(S + nb * NP);
 #pragma unroll
@@ -327,8 +328,8 @@ struct Worker {
         if (lane == 0) { sm.red128[wid] = F; sm.red64[wid] = (long long)IR; }
         __syncthreads();
         if (threadIdx.x < 32) {
-            F = (lane < kWarps) ? sm.red128[lane] : (unsigned __int128)0;
-            unsigned long long ir = (lane < kWarps) ? (unsigned long long)sm.red64[lane] : 0ull;
+            F = (lane < (TPB / 32)) ? sm.red128[lane] : (unsigned __int128)0;
+            unsigned long long ir = (lane < (TPB / 32)) ? (unsigned long long)sm.red64[lane] : 0ull;
             F = warp_sum_u128(F);
             ir = warp_sum(ir);
             if (lane == 0) {
@@ -374,7 +375,7 @@ struct Worker {
         const int nOwned = (k - rank + cs - 1) / cs;
         const int G = cs <= 1 ? 1 : cs <= 2 ? 2 : cs <= 4 ? 4 : cs <= 8 ? 8 : 16;
         const int q = threadIdx.x % G;
-        const int groups = kThreads / G;
+        const int groups = TPB / G;
         const int total = nOwned * NP;
         // all threads run the same trip count so the shuffles stay converged
         for (int base = 0; base < total; base += groups) {
@@ -412,14 +413,14 @@ struct Worker {
     }
 
     __device__ void pull_new_centroids() {
-        for (int e = threadIdx.x; e < k * NP; e += kThreads) {
+        for (int e = threadIdx.x; e < k * NP; e += TPB) {
             const int j = e / NP;
             sm.Ccur[e] = cl.map_shared_rank(sm.Cnew, j % cs)[e];
         }
         __syncthreads();
     }
     __device__ void pull_empty() {
-        for (int j = threadIdx.x; j < k; j += kThreads)
+        for (int j = threadIdx.x; j < k; j += TPB)
             sm.emptyall[j] = cl.map_shared_rank(sm.empty, j % cs)[j];
         __syncthreads();
     }
@@ -535,7 +536,7 @@ struct Worker {
         for (int j = 0; j < k; ++j) any_live |= (sm.deg[j] == 0);
         unsigned int mloc = 0;
         if (any_live) {
-            for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+            for (long long i = lo + threadIdx.x; i < hi; i += TPB) {
                 float x[NP];
                 load_row(i, x);
                 float dm = __int_as_float(0x7f800000);
@@ -547,7 +548,7 @@ struct Worker {
         }
         __syncthreads();
         const int trials = a.trials < 1 ? 1 : (a.trials > 3 ? 3 : a.trials);
-        const long long ch = (hi - lo + kThreads - 1) / kThreads;
+        const long long ch = (hi - lo + TPB - 1) / TPB;
         const long long c0 = lo + ch * threadIdx.x, c1 = min(hi, c0 + ch);
         for (int j = 0; j < k; ++j) {
             if (!sm.deg[j]) continue;
@@ -618,7 +619,7 @@ struct Worker {
                         }
                     }
                     long long pot[3] = {0, 0, 0};
-                    for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+                    for (long long i = lo + threadIdx.x; i < hi; i += TPB) {
                         float x[NP];
                         load_row(i, x);
                         const float d2 = D2[i];
@@ -655,10 +656,10 @@ struct Worker {
             }
             // centroid j = S[pick]
             if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->reseeded, 1ull);
-            for (int d = threadIdx.x; d < NP; d += kThreads) sm.Ccur[(size_t)j * NP + d] = S[pick * NP + d];
+            for (int d = threadIdx.x; d < NP; d += TPB) sm.Ccur[(size_t)j * NP + d] = S[pick * NP + d];
             __syncthreads();
             mloc = 0;
-            for (long long i = lo + threadIdx.x; i < hi; i += kThreads) {
+            for (long long i = lo + threadIdx.x; i < hi; i += TPB) {
                 float x[NP];
                 load_row(i, x);
                 const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
@@ -674,16 +675,16 @@ struct Worker {
 
 // trials > 3 would need more broadcast slots; the host caps it at 3.
 
-template <int NP>
-__global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a) {
-    Worker<NP> W(a, cg::this_cluster());
+template <int NP, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs a) {
+    Worker<NP, TPB> W(a, cg::this_cluster());
     if (a.glob->nonfinite) return;            // uniform: read before any barrier
     const int w = W.w;
 
     if (a.mode == kModeStepKpp || a.mode == kModeStepLloyd) {
         // S (padded) and C (padded, in a.Cw) were staged by the host.
         W.load_centroids(a.Cw);
-        for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = a.deg[j];
+        for (int j = threadIdx.x; j < W.k; j += TPB) W.sm.deg[j] = a.deg[j];
         __syncthreads();
         W.cl.sync();
         if (a.mode == kModeStepKpp) {
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
             const double f = W.lloyd(a.step_s, iters);
             if (W.rank == 0 && threadIdx.x == 0) { *a.step_f = f; *a.step_iters = iters; }
             if (W.rank == 0)
-                for (int j = threadIdx.x; j < W.k; j += kThreads) a.step_empty[j] = W.sm.emptyall[j];
+                for (int j = threadIdx.x; j < W.k; j += TPB) a.step_empty[j] = W.sm.emptyall[j];
         }
         if (W.rank == 0) W.store_centroids(a.Cw);
         W.csync_global();
@@ -703,8 +704,8 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
 
     // worker state for this launch
     const long long t_kernel = clock64();
-    for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = a.deg[(long long)w * W.k + j];
-    for (int e = threadIdx.x; e < W.k * NP; e += kThreads)
+    for (int j = threadIdx.x; j < W.k; j += TPB) W.sm.deg[j] = a.deg[(long long)w * W.k + j];
+    for (int e = threadIdx.x; e < W.k * NP; e += TPB)
         W.Cw_mine[e] = a.Cw[(long long)w * W.k * NP + e];
     __syncthreads();
     double fhat = a.fhat[w];
@@ -767,7 +768,7 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
             const double f = W.lloyd(s_w, iters);
             if (f < fhat) {                              // incumbent rule
                 fhat = f;
-                for (int j = threadIdx.x; j < W.k; j += kThreads) W.sm.deg[j] = W.sm.emptyall[j];
+                for (int j = threadIdx.x; j < W.k; j += TPB) W.sm.deg[j] = W.sm.emptyall[j];
                 W.store_centroids(W.Cw_mine);
                 if (W.rank == 0 && threadIdx.x == 0) {
                     const unsigned long long pos = atomicAdd(&a.glob->accepts, 1ull);
@@ -787,9 +788,9 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
     if (failed && W.rank == 0 && threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
     // persist worker state
     if (W.rank == 0) {
-        for (int e = threadIdx.x; e < W.k * NP; e += kThreads)
+        for (int e = threadIdx.x; e < W.k * NP; e += TPB)
             a.Cw[(long long)w * W.k * NP + e] = W.Cw_mine[e];
-        for (int j = threadIdx.x; j < W.k; j += kThreads) a.deg[(long long)w * W.k + j] = W.sm.deg[j];
+        for (int j = threadIdx.x; j < W.k; j += TPB) a.deg[(long long)w * W.k + j] = W.sm.deg[j];
         if (threadIdx.x == 0) {
             a.fhat[w] = fhat;
             atomicMin(&a.glob->rounds_done, a.round_begin + rounds_completed);
@@ -805,14 +806,16 @@ __global__ void __launch_bounds__(kThreads, 2) worker_kernel(const WorkerArgs a)
 template <int NP>
 int worker_max_cluster_t(int k) {
     const size_t smem = worker_smem_bytes<NP>(k);
-    if (allow_max_smem((const void*)worker_kernel<NP>) != cudaSuccess ||
-        cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (allow_max_smem((const void*)worker_kernel<NP, 256>) != cudaSuccess ||
+        allow_max_smem((const void*)worker_kernel<NP, 512>) != cudaSuccess ||
+        cudaFuncSetAttribute(worker_kernel<NP, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(worker_kernel<NP, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -822,25 +825,25 @@ int worker_max_cluster_t(int k) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, worker_kernel<NP>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, worker_kernel<NP, 256>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
     return nclusters > 0 ? 16 : 8;
 }
 
-template <int NP>
-cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) {
+template <int NP, int TPB>
+cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st) {
     const size_t smem = worker_smem_bytes<NP>(a.k);
-    cudaError_t e = allow_max_smem((const void*)worker_kernel<NP>);
+    cudaError_t e = allow_max_smem((const void*)worker_kernel<NP, TPB>);
     if (e != cudaSuccess) return e;
     if (a.cs > 8) {
-        e = cudaFuncSetAttribute(worker_kernel<NP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(worker_kernel<NP, TPB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(clusters * a.cs), 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(TPB, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -850,7 +853,13 @@ cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, worker_kernel<NP>, a);
+    return cudaLaunchKernelEx(&cfg, worker_kernel<NP, TPB>, a);
+}
+
+// a.tpb = 512 runs the worker with 512-thread CTAs (one per SM), else 256.
+template <int NP>
+cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) {
+    return a.tpb == 512 ? launch_worker_tpb<NP, 512>(a, clusters, st) : launch_worker_tpb<NP, 256>(a, clusters, st);
 }
 
 }  // namespace bm

@@ -109,6 +109,8 @@ SIGNATURES = {
     "bm_last_fullpass_impl": (_i32, []),
     "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
     "bm_set_rows_per_cta": (_i32, [_i32]),
+    "bm_set_big_clusters": (_i32, [_i32]),
+    "bm_get_big_clusters": (_i32, []),
     "bm_get_rows_per_cta": (_i32, []),
     "bm_autotune_rows_per_cta": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_i32), _i32,
                                         ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
@@ -436,3 +438,12 @@ def autotune_rows_per_cta(X, k, policy, budget, seed=0, candidates=(1024, 2048, 
                                         ctypes.byref(budget), int(seed), _stream(stream), cand, len(candidates),
                                         ctypes.byref(best), ms))
     return best.value, {int(c): float(t) for c, t in zip(candidates, ms)}
+
+
+def set_big_clusters(on):
+    """bm_set_big_clusters: 512-thread CTAs for the workers whose cluster is at the cap."""
+    _check(lib.bm_set_big_clusters(int(bool(on))))
+
+
+def get_big_clusters():
+    return int(lib.bm_get_big_clusters())

@@ -291,3 +291,21 @@ def test_autotuner_picks_a_candidate_and_sets_it():
     finally:
         native.set_rows_per_cta(0)
     assert native.get_rows_per_cta() == 2048
+
+
+def test_results_do_not_depend_on_big_cluster_ctas():
+    X = gaussian_mixture(200_000, 16, 10, seed=33)
+    pol = dict(s_min=20_000, s_max=60_000, workers=3, passes=2)
+    bud = dict(rounds=2, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    outs = []
+    try:
+        for on in (0, 1):
+            native.set_big_clusters(on)
+            outs.append(native.fit(_t(X), 10, native.make_policy(**pol), native.make_budget(**bud), seed=4))
+    finally:
+        native.set_big_clusters(0)
+    (C0, Y0, r0), (C1, Y1, r1) = outs
+    assert torch.equal(C0.view(torch.int32), C1.view(torch.int32)) and torch.equal(Y0, Y1)
+    assert r0["f_full"] == r1["f_full"] and r0["lloyd_iters"] == r1["lloyd_iters"]
+    ref = obm.bigmeans(X, 10, pol, bud, seed=4)
+    _assert_same(C1.cpu().numpy(), Y1.cpu().numpy(), r1, ref)
