@@ -187,7 +187,12 @@ __device__ __forceinline__ void acc_obj(unsigned __int128& acc, float d, int gf,
 // between flushes.  Returns false if the value exceeded the 96-bit range.
 constexpr int kDigits = 6;
 constexpr long long kMaxRowsPerCta = 32767;
-__device__ __forceinline__ bool acc_digits(int* w, float x, int gx, unsigned int& inexact) {
+// The digit chunks of x on grid gx: x = sign (c0 + c1 2^16 + c2 2^32) 2^(16 i + gx)
+// (signed chunks).  Returns false if x needs digits beyond kDigits; i = -1
+// when x contributes nothing.
+__device__ __forceinline__ bool digits_of(float x, int gx, unsigned int& inexact, int& i, int& c0, int& c1,
+                                          int& c2) {
+    i = -1; c0 = c1 = c2 = 0;
     const uint32_t bits = __float_as_uint(x);
     const uint32_t mag = bits & 0x7fffffffu;
     if (mag == 0) return true;
@@ -202,15 +207,23 @@ __device__ __forceinline__ bool acc_digits(int* w, float x, int gx, unsigned int
         sh = 0;
         if (!mant) return true;
     }
-    const int i = sh >> 4, intra = sh & 15;
+    const int ii = sh >> 4, intra = sh & 15;
     const uint64_t v = (uint64_t)mant << intra;                 // < 2^39
-    int c0 = (int)(v & 0xffffu), c1 = (int)((v >> 16) & 0xffffu), c2 = (int)(v >> 32);
-    if (i + (c2 ? 2 : (c1 ? 1 : 0)) >= kDigits) return false;
+    c0 = (int)(v & 0xffffu); c1 = (int)((v >> 16) & 0xffffu); c2 = (int)(v >> 32);
+    if (ii + (c2 ? 2 : (c1 ? 1 : 0)) >= kDigits) { c0 = c1 = c2 = 0; return false; }
     if (bits >> 31) { c0 = -c0; c1 = -c1; c2 = -c2; }
+    i = ii;
+    return true;
+}
+
+__device__ __forceinline__ bool acc_digits(int* w, float x, int gx, unsigned int& inexact) {
+    int i, c0, c1, c2;
+    const bool ok = digits_of(x, gx, inexact, i, c0, c1, c2);
+    if (i < 0) return ok;
     if (c0) atomicAdd(&w[i], c0);
     if (c1) atomicAdd(&w[i + 1], c1);
     if (c2) atomicAdd(&w[i + 2], c2);
-    return true;
+    return ok;
 }
 
 // Correctly rounded double of a (signed) 128-bit integer times 2^g.

@@ -279,16 +279,18 @@ struct Worker {
                     const unsigned mv = __ballot_sync(0xffffffffu, moved);
                     if (__popc(mv) > 8) {
                         if (moved) {
-                            const float* xr = S + row * NP;
+                            // the row is in registers (x): no reload from the sample
                             atomicAdd(&sm.cnt[lab], 1);
                             int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
-#pragma unroll 1
-                            for (int d = 0; d < n; ++d) ok &= acc_digits(wb + d * kDigits, xr[d], gx, inex);
+#pragma unroll
+                            for (int d = 0; d < NP; ++d)
+                                if (d < n) ok &= acc_digits(wb + d * kDigits, x[d], gx, inex);
                             if (oldlab[r] >= 0) {
                                 atomicSub(&sm.cnt[oldlab[r]], 1);
                                 int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
-#pragma unroll 1
-                                for (int d = 0; d < n; ++d) ok &= acc_digits(wo + d * kDigits, -xr[d], gx, inex);
+#pragma unroll
+                                for (int d = 0; d < NP; ++d)
+                                    if (d < n) ok &= acc_digits(wo + d * kDigits, -x[d], gx, inex);
                             }
                             lab_prev[row] = lab;
                         }
@@ -320,7 +322,7 @@ struct Worker {
         }
         if (!ok) atomicOr(&a.glob->err, kErrDigits);
         const long long t_red = clock64();
-        if (acc) trace_add(8, t_loop);
+        if (acc) trace_add(mode == 1 ? 14 : 8, t_loop);   // 14: first assignment of a run
         // one fused CTA reduction: objective (128-bit) and the two counters
         unsigned __int128 F = warp_sum_u128(facc);
         const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
