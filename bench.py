@@ -274,8 +274,13 @@ def run_ours(args):
     bytes_full = m * n * 4.0
     full_gbs = bytes_full * n_full / t_full / 1e9 if t_full > 0 else 0.0
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic_full, digest_full = _traffic_for([os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
+                                              for f in ("bm_tcx.cu", "bm_tcgen05.cuh", "bm_device.cuh")])
     roof_full = {"bound": "hbm", "achieved": full_gbs, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": full_gbs / hbm_peak, "traffic": None,
+                 "frac": full_gbs / hbm_peak,
+                 "traffic": (traffic_full.get("dram_bytes_per_launch") if traffic_full
+                             and native.last_fullpass_impl() == 2 else None),
+                 "source_digest": digest_full,
                  "kernel": ("tcx_fullpass_kernel<16> (tcgen05 split-TF32, certified, labels + f(C, X))"
                             if native.last_fullpass_impl() == 2 else "fullpass_kernel<16> (labels + f(C, X))"),
                  "algorithmic": f"m*n*4 = {bytes_full:.4g} bytes per launch (X read once)",
