@@ -414,6 +414,16 @@ bm_status bm_ctx_stats(bm_ctx* ctx, bm_ctx_info* stats_out);
 /* Drops queued jobs, waits for running ones, frees the context. */
 void bm_ctx_destroy(bm_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Device memory of the library.  Workspaces and the device copies of host
+ * buffers come from a stream-ordered memory pool the library creates per
+ * device; freed memory stays in that pool (it is not returned to the driver)
+ * so that the next fit reuses it without mapping it again.
+ * bm_trim_memory releases all currently unused pool memory of every device
+ * the library has used.  (bm_assign_noalloc uses no pool memory.)
+ * ------------------------------------------------------------------------- */
+bm_status bm_trim_memory(void);
+
 /* Thread-local message for the last non-OK status of this thread. */
 const char* bm_last_error(void);
 

@@ -10,6 +10,8 @@
 // Everything is enqueued on the caller's stream; each entry point
 // synchronises that stream once before returning.
 #include <algorithm>
+#include <mutex>
+#include <map>
 #include <atomic>
 #include <cstdarg>
 #include <chrono>
@@ -104,6 +106,40 @@ int sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
     return v > 0 ? v : 1;
+}
+
+// The library's own stream-ordered memory pool on the current device: freed
+// memory stays in the pool (release threshold: never) and is reused by the
+// next fit without being mapped again.  bm_trim_memory returns it.
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t lib_pool(cudaMemPool_t* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) { *out = it->second; return cudaSuccess; }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = ~0ull;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+cudaError_t lib_alloc(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = lib_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 // gamma_q = q u / (1 - q u), u = 2^-24, rounded up to float.
@@ -358,7 +394,7 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const size_t o_ff = take((size_t)W * 8);
     const size_t o_L = take((size_t)c->L_cap * 8);
     const size_t o_t = take(8);
-    cudaError_t e = cudaMallocAsync(&c->base, off, c->st);
+    cudaError_t e = lib_alloc(&c->base, off, c->st);
     if (e != cudaSuccess) {
         c->base = nullptr;
         cudaGetLastError();
@@ -638,6 +674,15 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
 
 extern "C" {
 
+bm_status bm_trim_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (auto& kv : g_pools) {
+        const cudaError_t e = cudaMemPoolTrimTo(kv.second, 0);
+        if (e != cudaSuccess) return fail(BM_ECUDA, "trim: %s", cudaGetErrorString(e));
+    }
+    return BM_OK;
+}
+
 bm_status bm_set_rows_per_cta(int32_t rows) {
     if (rows == 0) rows = kRowsPerCta;
     if (rows < 256 || rows > kMaxRowsPerCta) return fail(BM_EINVAL, "rows per CTA = %d out of [256, %lld]", rows,
@@ -838,9 +883,9 @@ bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k
     const auto t0 = std::chrono::steady_clock::now();
     float* Xd = nullptr; float* Cd = nullptr; int32_t* Ld = nullptr;
     const size_t xb = (size_t)m * n * 4;
-    CU(cudaMallocAsync((void**)&Xd, xb, st));
-    if (cudaMallocAsync((void**)&Cd, (size_t)k * n * 4 + 16, st) != cudaSuccess ||
-        (labels_out_host && cudaMallocAsync((void**)&Ld, (size_t)m * 4, st) != cudaSuccess)) {
+    CU(lib_alloc((void**)&Xd, xb, st));
+    if (lib_alloc((void**)&Cd, (size_t)k * n * 4 + 16, st) != cudaSuccess ||
+        (labels_out_host && lib_alloc((void**)&Ld, (size_t)m * 4, st) != cudaSuccess)) {
         cudaFreeAsync(Xd, st);
         if (Cd) cudaFreeAsync(Cd, st);
         cudaStreamSynchronize(st);
@@ -1009,7 +1054,7 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
         return fail(BM_EINVAL, "k too large for the full pass");
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
-    CU(cudaMallocAsync(&base, gb + (size_t)k * np * 4, sm));
+    CU(lib_alloc(&base, gb + (size_t)k * np * 4, sm));
     Globals* g = (Globals*)base;
     float* Cp = (float*)((char*)base + gb);
     float gB, gp2;
@@ -1089,7 +1134,7 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
     cudaStream_t sm = (cudaStream_t)stream;
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
-    CU(cudaMallocAsync(&base, gb + (size_t)m * 4, sm));
+    CU(lib_alloc(&base, gb + (size_t)m * 4, sm));
     Globals* g = (Globals*)base;
     int* queue = (int*)((char*)base + gb);
     cudaError_t e;

@@ -109,6 +109,7 @@ SIGNATURES = {
     "bm_last_fullpass_impl": (_i32, []),
     "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
     "bm_set_rows_per_cta": (_i32, [_i32]),
+    "bm_trim_memory": (_i32, []),
     "bm_set_big_clusters": (_i32, [_i32]),
     "bm_get_big_clusters": (_i32, []),
     "bm_get_rows_per_cta": (_i32, []),
@@ -447,3 +448,8 @@ def set_big_clusters(on):
 
 def get_big_clusters():
     return int(lib.bm_get_big_clusters())
+
+
+def trim_memory():
+    """bm_trim_memory: return the library pool's unused device memory."""
+    _check(lib.bm_trim_memory())
