@@ -274,15 +274,16 @@ def run_ours(args):
     bytes_full = m * n * 4.0
     full_gbs = bytes_full * n_full / t_full / 1e9 if t_full > 0 else 0.0
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    tensor_full = native.last_fullpass_impl() == 2
     traffic_full, digest_full = _traffic_for([os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
-                                              for f in ("bm_tcx.cu", "bm_tcgen05.cuh", "bm_device.cuh")])
+                                              for f in (("bm_tcx.cu", "bm_tcgen05.cuh", "bm_device.cuh")
+                                                        if tensor_full else ("bm_fullpass.cu", "bm_device.cuh"))])
     roof_full = {"bound": "hbm", "achieved": full_gbs, "peak": hbm_peak, "unit": "GB/s",
                  "frac": full_gbs / hbm_peak,
-                 "traffic": (traffic_full.get("dram_bytes_per_launch") if traffic_full
-                             and native.last_fullpass_impl() == 2 else None),
+                 "traffic": traffic_full.get("dram_bytes_per_launch") if traffic_full else None,
                  "source_digest": digest_full,
                  "kernel": ("tcx_fullpass_kernel<16> (tcgen05 split-TF32, certified, labels + f(C, X))"
-                            if native.last_fullpass_impl() == 2 else "fullpass_kernel<16> (labels + f(C, X))"),
+                            if tensor_full else "fullpass_kernel<16> (FP32 ALU, certified, labels + f(C, X))"),
                  "algorithmic": f"m*n*4 = {bytes_full:.4g} bytes per launch (X read once)",
                  "avg_launch_us": t_full / max(n_full, 1) * 1e6, "peak_source": peak_src}
 
@@ -608,6 +609,8 @@ def main():
     ap.add_argument("--workload", default=None, help="kernel modes: workload name (default: the headline's)")
     ap.add_argument("--rows", type=int, default=None, help="kernel modes: rows of the workload to use")
     ap.add_argument("--k", type=int, default=None, help="kernel modes: number of centroids")
+    ap.add_argument("--fullpass-impl", type=int, default=0, choices=[0, 1, 2],
+                    help="full-data pass: 0 by shape, 1 FP32 ALU, 2 tensor cores where they apply")
     ap.add_argument("--centroids", choices=["rows", "fit"], default="rows",
                     help="kernel modes: centroids from evenly spaced rows, or from a short fit")
     ap.add_argument("--mode", choices=["fit", "fullpass", "lloyd", "precision", "serve", "batched"], default="fit",
@@ -619,6 +622,9 @@ def main():
     if args.big_clusters is not None and args.impl == "ours":
         from paper_2403_18766_gb300 import native
         native.set_big_clusters(args.big_clusters)
+    if args.fullpass_impl and args.impl == "ours":
+        from paper_2403_18766_gb300 import native
+        native.set_fullpass_impl(args.fullpass_impl)
     if args.mode == "serve":
         return run_serve(args)
     if args.mode == "batched":

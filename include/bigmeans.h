@@ -296,13 +296,17 @@ bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const floa
 /* ---------------------------------------------------------------------------
  * bm_set_fullpass_impl / bm_last_fullpass_impl -- choice of implementation
  * for the full-data pass of Eq. (1) (bm_assign, bm_assign_noalloc and the
- * full passes inside a fit).  Both implementations give identical labels and
+ * full passes inside a fit).  All implementations give identical labels and
  * f (the same FP32 direct-form definition, certified).
- *   impl 0 (default): the tensor-core pass (tcgen05, TF32 products of the
- *          expanded form, certified, uncertain rows re-scored in FP32) where
- *          it applies -- n % 4 == 0, X 16-byte aligned, k <= 256 -- else
+ *   impl 0 (default): by shape -- the tensor-core pass when n_pad * k >= 1024
+ *          (n_pad = n rounded up to 4, 8, 16, 32 or 64) and it applies, else
  *          the FP32-ALU pass;
- *   impl 1: always the FP32-ALU pass.
+ *   impl 1: always the FP32-ALU pass (register-tiled expanded form, certified,
+ *          uncertain rows re-scored in FP32);
+ *   impl 2: the tensor-core pass (tcgen05, TF32 products of the expanded
+ *          form, certified, uncertain rows re-scored in FP32) where it
+ *          applies -- n % 4 == 0, X 16-byte aligned, k <= 256 -- else the
+ *          FP32-ALU pass.
  * Any other value is rejected with BM_EINVAL.  The setting is process-wide;
  * change it only while no call of this library is running.
  * bm_last_fullpass_impl returns which one the last full pass launched by the

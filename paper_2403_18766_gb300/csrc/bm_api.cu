@@ -535,9 +535,18 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     // A failed launch must not return before the workers already launched
     // are joined into c->st: the caller frees the workspace on c->st.
     cudaError_t launch_err = cudaSuccess;
-    for (int w = 0; w < c->pol.workers && launch_err == cudaSuccess; ++w) {
+    // largest samples first: the longest workers start earliest (the order
+    // of independent workers changes no result)
+    std::vector<std::pair<long long, int>> order;
+    for (int w = 0; w < c->pol.workers; ++w) {
         long long smax = 0;
         for (int t = r0; t < r1; ++t) smax = std::max(smax, size_of(c, w, t));
+        order.push_back({-smax, w});
+    }
+    std::sort(order.begin(), order.end());
+    for (int oi = 0; oi < c->pol.workers && launch_err == cudaSuccess; ++oi) {
+        const int w = order[oi].second;
+        const long long smax = -order[oi].first;
         WorkerArgs a = make_args(c, kModeRounds, parity);
         a.round_begin = r0;
         a.round_end = r1;
@@ -547,7 +556,7 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         // clusters at the size cap with more rows per CTA than the tile get
         // 512-thread CTAs (one per SM) when the big-cluster option is on
         a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
-        launch_err = launch_worker(c->np, a, 1, c->wst[w % ns]);
+        launch_err = launch_worker(c->np, a, 1, c->wst[oi % ns]);
         if (launch_err == cudaSuccess) c->n_kernels++;
     }
     if (launch_err != cudaSuccess) {
@@ -597,7 +606,7 @@ extern "C" {
 const char* bm_last_error(void) { return g_err.c_str(); }
 
 bm_status bm_set_fullpass_impl(int32_t impl) {
-    if (impl != 0 && impl != 1) return fail(BM_EINVAL, "fullpass impl = %d must be 0 or 1", impl);
+    if (impl < 0 || impl > 2) return fail(BM_EINVAL, "fullpass impl = %d must be 0, 1 or 2", impl);
     set_fullpass_impl(impl);
     return BM_OK;
 }
@@ -1050,7 +1059,7 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
     cudaStream_t sm = (cudaStream_t)stream;
     const int np = padded_dim(n);
     const size_t smem = fullpass_smem_bytes(np, k, n);
-    if (smem > kSmemLimit && !(fullpass_impl_setting() == 0 && tcx_eligible(X_dev, m, n, np, k)))
+    if (smem > kSmemLimit && !(fullpass_impl_setting() != 1 && tcx_eligible(X_dev, m, n, np, k)))
         return fail(BM_EINVAL, "k too large for the full pass");
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;

@@ -37,73 +37,41 @@ __global__ void __launch_bounds__(kThreads) prepass_kernel(const float* __restri
     }
 }
 
-// ------------------------------------------------------------ TMA helpers
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// 1-D bulk copy global -> shared, completing on `bar` (addresses and size
-// multiples of 16 bytes).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait: gives up after `limit` polls and reports it.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, Globals* g) {
-    for (unsigned i = 0; i < (1u << 24); ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(&g->err, kErrTimeout);
-    return false;
-}
-
-constexpr int kFpThreads = 256;      // rows per tile = threads per CTA (one row each)
+constexpr int kFpThreads = 256;
+// Rows per thread: enough independent FMA chains per centroid to hide the
+// FMA latency, few enough registers for two CTAs per SM.
 template <int NP>
-__host__ __device__ constexpr int fp_stages() { return NP >= 64 ? 2 : 3; }   // tiles in flight
+struct FpRows { static constexpr int v = NP <= 4 ? 8 : NP == 8 ? 6 : NP == 16 ? 4 : NP == 32 ? 2 : 1; };
 
 // mode: selection of the centroid set.
 //   sel_f == nullptr: use C directly (k x NP, padded).
 //   otherwise: C = Cw + w* k NP with w* = argmin sel_f[0..W) (lowest index).
 // incumbent: when set, f_incumbent = min(f_incumbent, f) and best_worker = w*.
 //
-// X is consumed in tiles of kFpThreads rows: a persistent CTA walks tiles
-// t0, t0 + grid, ...; thread 0 keeps kFpStages tiles in flight with 1-D bulk
-// copies (TMA) completing on per-stage mbarriers; every thread assigns one
-// row of the current tile from shared memory.  The ragged last tile is read
-// with plain loads.
+// A persistent grid of warps walks X in warp tiles of 32 RT rows (row
+// base + 32 r + lane for lane's r-th row, so every 16-byte load of the warp
+// covers 32 consecutive rows); each warp asks L2 for its next tile while it
+// computes the current one.  Per row: g_j = fl(||c_j||^2) + sum_d (-2 x_d) c_j,d
+// as two interleaved partial sums (even and odd d, packed FP32 FMA) added
+// at the end -- NP + 1 terms in some order, inside the certificate's
+// gamma_{2NP+2} bound -- then the certificate of the least two, and d32 of
+// the winner (or of every centroid for an uncertain row).
 template <int NP>
-__global__ void __launch_bounds__(kFpThreads)
+__global__ void __launch_bounds__(kFpThreads, 2)
 fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __restrict__ Cw,
                 int k, const double* sel_f, int W, int* __restrict__ labels, Globals* g,
                 float gB, float gp2, int incumbent) {
+    constexpr int RT = FpRows<NP>::v;
     constexpr int kW = kFpThreads / 32;
-    constexpr int kFpStages = fp_stages<NP>();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    const size_t tile_bytes = (size_t)kFpThreads * n * 4;
-    float* stage_buf = reinterpret_cast<float*>(smem_raw);                       // kFpStages tiles
-    float* Cs = reinterpret_cast<float*>(smem_raw + kFpStages * tile_bytes);     // k * NP
-    float* CC = Cs + (size_t)k * NP;                                             // k
-    // per-warp row buffer with an odd stride (n + 1 words): conflict-free
-    // both for the copy out of the stage and for one row per lane
-    float* wbuf = CC + ((k + 3) & ~3) + (size_t)(threadIdx.x >> 5) * 32 * (n + 1);
-    __shared__ __align__(8) unsigned long long bar[kFpStages];
+    // Cs: rows NP floats apart (every lane reads the same centroid);
+    // Cg: a copy with rows an odd number of 16-byte units apart, read at
+    // per-lane labels (8 lanes of different clusters per 128-bit phase fall
+    // in 8 different 4-bank groups).
+    constexpr int kCs = ((NP / 4) & 1) ? NP : NP + 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Cs = reinterpret_cast<float*>(smem_raw);          // k * NP
+    float* Cg = Cs + (size_t)k * NP;                          // k * kCs
+    float* CC = Cg + (size_t)k * kCs;                         // k
     __shared__ unsigned __int128 red128[kW];
     __shared__ unsigned long long red64[kW];
     __shared__ unsigned int redu[kW];
@@ -112,33 +80,21 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
     __shared__ bool last;
 
     if (g->nonfinite) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
         int best = 0;
         if (sel_f)
             for (int w = 1; w < W; ++w)
                 if (sel_f[w] < sel_f[best]) best = w;
         wsel = best;
-        for (int st = 0; st < kFpStages; ++st) mbar_init(&bar[st], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-
-    const long long ntiles = (m + kFpThreads - 1) / kFpThreads;
-    const long long full_tiles = m / kFpThreads;              // tiles copied with TMA
-    const long long grid = gridDim.x;
-    auto issue = [&](long long tile, int st) {
-        if (tile < full_tiles) {
-            mbar_expect_tx(&bar[st], (unsigned)tile_bytes);
-            bulk_g2s(stage_buf + (size_t)st * kFpThreads * n, X + tile * kFpThreads * (long long)n,
-                     (unsigned)tile_bytes, &bar[st]);
-        }
-    };
-    if (tid == 0)
-        for (int st = 0; st < kFpStages; ++st) issue(blockIdx.x + st * grid, st);
-
     const float* C = Cw + (sel_f ? (long long)wsel * k * NP : 0ll);
-    for (int e = tid; e < k * NP; e += kFpThreads) Cs[e] = C[e];
+    for (int e = tid; e < k * NP; e += kFpThreads) {
+        const float v = C[e];
+        Cs[e] = v;
+        Cg[(size_t)(e / NP) * kCs + e % NP] = v;
+    }
     __syncthreads();
     unsigned int mx = 0;
     for (int j = tid; j < k; j += kFpThreads) {
@@ -155,7 +111,7 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
     {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        if ((tid & 31) == 0) redu[tid >> 5] = mx;
+        if (lane == 0) redu[tid >> 5] = mx;
         __syncthreads();
         if (tid == 0) {
             unsigned int mm = 0;
@@ -167,69 +123,91 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
     }
     const CertC cc = cert;
     const Grids gr = grids_from_maxbits(g->maxbits);
+    const bool vec = (n % 4) == 0 && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
     unsigned __int128 facc = 0;
     unsigned int inex = 0, resc = 0;
-    for (long long it = 0;; ++it) {
-        const long long tile = blockIdx.x + it * grid;
-        if (tile >= ntiles) break;
-        const int st = (int)(it % kFpStages);
-        const unsigned parity = (unsigned)((it / kFpStages) & 1);
-        const long long row = tile * kFpThreads + tid;
-        float m2x[NP];
-        if (tile < full_tiles) {
-            mbar_wait(&bar[st], parity, g);
-            const int lane = tid & 31;
-            const float* src = stage_buf + (size_t)st * kFpThreads * n + (size_t)(tid & ~31) * n;
-            __syncwarp();
-            for (int r = 0; r < 32; ++r)
-                for (int d = lane; d < n; d += 32) wbuf[r * (n + 1) + d] = src[r * n + d];
-            __syncwarp();
-            const float* xr = wbuf + lane * (n + 1);
+    const long long tile_rows = 32ll * RT;
+    const long long step = (long long)gridDim.x * kW * tile_rows;
+    const long long xbytes = m * (long long)n * 4;
+    for (long long base = ((long long)blockIdx.x * kW + (tid >> 5)) * tile_rows; base < m; base += step) {
+        float2 m2x[RT][NP / 2];                               // -2 x, dimension pairs
 #pragma unroll
-            for (int d = 0; d < NP; ++d) m2x[d] = (d < n) ? -2.f * xr[d] : 0.f;
-        } else {
-            const float* xr = X + row * (long long)n;
+        for (int r = 0; r < RT; ++r) {
+            const long long row = base + 32 * r + lane;
+            if (row < m) {
+                const float* p = X + row * (long long)n;
+                if (vec) {
 #pragma unroll
-            for (int d = 0; d < NP; ++d) m2x[d] = (row < m && d < n) ? -2.f * __ldg(xr + d) : 0.f;
+                    for (int q = 0; q < NP / 4; ++q) {
+                        const float4 v = (4 * q < n) ? __ldg(reinterpret_cast<const float4*>(p) + q)
+                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                        m2x[r][2 * q + 0] = make_float2(-2.f * v.x, -2.f * v.y);
+                        m2x[r][2 * q + 1] = make_float2(-2.f * v.z, -2.f * v.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int d = 0; d < NP / 2; ++d)
+                        m2x[r][d] = make_float2((2 * d < n) ? -2.f * __ldg(p + 2 * d) : 0.f,
+                                                (2 * d + 1 < n) ? -2.f * __ldg(p + 2 * d + 1) : 0.f);
+                }
+            } else {
+#pragma unroll
+                for (int d = 0; d < NP / 2; ++d) m2x[r][d] = make_float2(0.f, 0.f);
+            }
         }
-        // the stage is free once every thread has its row in registers
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(tile + kFpStages * grid, st);
+        {   // next warp tile of this warp: L2 prefetch, one 128-byte line per lane
+            const long long nb = (base + step) * (long long)n * 4;
+            const long long bytes = tile_rows * (long long)n * 4;
+            for (long long o = (long long)lane * 128; o < bytes; o += 32 * 128)
+                if (nb + o < xbytes)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const char*>(X) + nb + o));
         }
-        float g1 = __int_as_float(0x7f800000), g2 = g1;
-        int j1 = 0;
+        float g1[RT], g2[RT];
+        int j1[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) { g1[r] = __int_as_float(0x7f800000); g2[r] = g1[r]; j1[r] = 0; }
         for (int j = 0; j < k; ++j) {
             const float* cj = Cs + (size_t)j * NP;
-            float e = CC[j];
+            const float ccj = CC[j];
+            float2 e2[RT];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) e2[r] = make_float2(ccj, 0.f);
 #pragma unroll
             for (int q = 0; q < NP / 4; ++q) {
                 const float4 cv = reinterpret_cast<const float4*>(cj)[q];
-                e = __fmaf_rn(m2x[4 * q + 0], cv.x, e);
-                e = __fmaf_rn(m2x[4 * q + 1], cv.y, e);
-                e = __fmaf_rn(m2x[4 * q + 2], cv.z, e);
-                e = __fmaf_rn(m2x[4 * q + 3], cv.w, e);
+                const float2 c01 = make_float2(cv.x, cv.y), c23 = make_float2(cv.z, cv.w);
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    e2[r] = __ffma2_rn(m2x[r][2 * q + 0], c01, e2[r]);
+                    e2[r] = __ffma2_rn(m2x[r][2 * q + 1], c23, e2[r]);
+                }
             }
-            g2 = fminf(g2, fmaxf(g1, e));
-            j1 = (e < g1) ? j : j1;
-            g1 = fminf(g1, e);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const float e = __fadd_rn(e2[r].x, e2[r].y);
+                g2[r] = fminf(g2[r], fmaxf(g1[r], e));
+                j1[r] = (e < g1[r]) ? j : j1[r];
+                g1[r] = fminf(g1[r], e);
+            }
         }
-        if (row < m) {
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const long long row = base + 32 * r + lane;
+            if (row >= m) continue;
             float x[NP];
             float xn2 = 0.f;
 #pragma unroll
             for (int d = 0; d < NP; ++d) {
-                x[d] = -0.5f * m2x[d];
+                x[d] = -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x);
                 xn2 = __fmaf_ru(x[d], x[d], xn2);
             }
             const float xn = __fsqrt_ru(xn2);
             int lab;
             float dv;
-            if (certified(g1, g2, xn2, xn, cc, gB, gp2)) {
-                lab = j1;
-                dv = d32<NP>(x, Cs + (size_t)lab * NP);
+            if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
+                lab = j1[r];
+                dv = d32<NP>(x, Cg + (size_t)lab * kCs);
             } else {
                 resc++;
                 lab = 0;
@@ -246,7 +224,7 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
     // CTA reduction (one pass) and the grid-wide total
     unsigned __int128 F = warp_sum_u128(facc);
     const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
-    const int lane = tid & 31, wid = tid >> 5;
+    const int wid = tid >> 5;
     if (lane == 0) { red128[wid] = F; red64[wid] = IR; }
     __syncthreads();
     if (tid == 0) {
@@ -331,9 +309,9 @@ __global__ void globaltimer_kernel(unsigned long long* out) {
 
 // ------------------------------------------------------------ host launchers
 size_t fullpass_smem_bytes(int np, int k, int n) {
-    const int stages = np >= 64 ? 2 : 3;
-    return (size_t)stages * kFpThreads * n * 4 + (size_t)k * np * 4 + (size_t)((k + 3) & ~3) * 4 +
-           (size_t)(kFpThreads / 32) * 32 * (n + 1) * 4;
+    (void)n;
+    const int cs = ((np / 4) & 1) ? np : np + 4;
+    return (size_t)k * np * 4 + (size_t)k * cs * 4 + (size_t)k * 4;
 }
 
 template <int NP>
@@ -346,8 +324,9 @@ static cudaError_t launch_fullpass_t(const float* X, long long m, int n, const f
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fullpass_kernel<NP>, kFpThreads, smem);
     if (e != cudaSuccess) return e;
-    const long long tiles = (m + kFpThreads - 1) / kFpThreads;
-    const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), tiles));
+    const long long warp_tiles = (m + 32ll * FpRows<NP>::v - 1) / (32ll * FpRows<NP>::v);
+    const long long ctas = (warp_tiles + kFpThreads / 32 - 1) / (kFpThreads / 32);
+    const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), ctas));
     fullpass_kernel<NP><<<(unsigned)grid, kFpThreads, smem, st>>>(X, m, n, C, k, sel_f, W, labels, g, gB, gp2,
                                                                    incumbent);
     return cudaGetLastError();
@@ -357,19 +336,24 @@ cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, cons
                                 const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                                 int incumbent, int sms, cudaStream_t st);
 
-// Which implementation full passes use: 0 = the tensor-core pass where it
-// applies, else the FP32-ALU pass; 1 = always the FP32-ALU pass.  Both give
-// identical labels and objective (same definition, certified).
+// Which implementation full passes use: 0 = by shape (below), 1 = the
+// FP32-ALU pass, 2 = the tensor-core pass where it applies (else FP32-ALU).
+// All give identical labels and objective (same definition, certified).
 static std::atomic<int> g_fullpass_impl{0};
 static thread_local int g_last_impl = 0;
 void set_fullpass_impl(int impl) { g_fullpass_impl.store(impl); }
 int last_fullpass_impl() { return g_last_impl; }
 int fullpass_impl_setting() { return g_fullpass_impl.load(); }
-
+// By shape: the FP32-ALU pass costs about k NP / 2 packed FMAs per row, the
+// tensor-core pass a fixed epilogue per row and centroid column, so the
+// tensor cores win once the contraction per row is large.
+bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k >= 1024; }
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int sms, cudaStream_t st) {
-    if (g_fullpass_impl.load() == 0) {
+    int impl = g_fullpass_impl.load();
+    if (impl == 0) impl = fullpass_prefers_tensor(np, k) ? 2 : 1;
+    if (impl == 2) {
         const cudaError_t e = launch_tcx_fullpass(np, X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, st);
         if (e != cudaErrorNotSupported) {
             g_last_impl = 2;
@@ -386,7 +370,6 @@ cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const fl
     }
     return cudaErrorInvalidValue;
 }
-
 cudaError_t launch_prepass(const float* v, long long count, Globals* g, int grid, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     prepass_kernel<<<grid, kThreads, 0, st>>>(v, count, g);

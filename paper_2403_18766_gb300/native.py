@@ -292,7 +292,7 @@ def assign(X, C, labels=True, stream=None):
 
 
 def set_fullpass_impl(impl):
-    """bm_set_fullpass_impl: 0 = tensor-core full pass where it applies, 1 = FP32-ALU pass."""
+    """bm_set_fullpass_impl: 0 = by shape, 1 = FP32-ALU pass, 2 = tensor-core pass where it applies."""
     _check(lib.bm_set_fullpass_impl(int(impl)))
 
 

@@ -1,8 +1,8 @@
 """GPU parity of the tensor-core exact full pass (tcgen05 kind::tf32 proposal,
 certified, uncertain rows re-scored in the FP32 direct form).
 
-Labels and f(C, X) must equal the oracle bit for bit, exactly as the FP32-ALU
-pass does, for every shape the tensor-core pass takes (n % 4 == 0): one and
+Labels and f(C, X) must equal the oracle bit for bit, and equal those of the
+FP32-ALU pass, for every shape the tensor-core pass takes (n % 4 == 0): one and
 two 32-float column blocks, k up to 256, tiles with ragged tails, m below one
 tile, ties between duplicated centroids and data far from the origin (where
 the TF32 error bound makes many rows uncertain).  Ineligible inputs (n % 4 !=
@@ -34,8 +34,9 @@ def _default_impl():
 
 
 def _both(X, C):
+    """(tensor-core pass where it applies, FP32-ALU pass) on the same input."""
     Xd, Cd = _t(X), _t(C)
-    native.set_fullpass_impl(0)
+    native.set_fullpass_impl(2)
     Y0, f0, r0 = native.assign(Xd, Cd)
     impl0 = native.last_fullpass_impl()
     native.set_fullpass_impl(1)
@@ -63,18 +64,28 @@ def test_tensor_core_pass_is_bit_exact(m, n, k):
     assert r0["inexact_terms"] == 0
 
 
-def test_widest_case_runs_on_tensor_cores_only():
-    """n = 64, k = 176: beyond the FP32-ALU pass's shared memory, taken by the
-    tensor-core pass alone."""
+def test_widest_case_both_passes():
+    """n = 64, k = 176: the widest shape the tensor-core pass takes (its
+    B operands and stages fill the shared memory)."""
     X = gaussian_mixture(20_000, 64, 88, seed=21)
     C = X[np.random.default_rng(3).integers(0, X.shape[0], 176)].copy()
-    Y, f, rep = native.assign(_t(X), _t(C))
-    assert native.last_fullpass_impl() == 2
+    (Y0, f0, _, i0), (Y1, f1, _, i1) = _both(X, C)
+    assert (i0, i1) == (2, 1)
+    lab, dist = okm.assign(X, C)
+    assert np.array_equal(Y0, lab) and f0 == okm.exact_sum(dist)
+    assert np.array_equal(Y1, Y0) and f1 == f0
+
+
+@pytest.mark.parametrize("n,k,want", [(16, 25, 1), (64, 100, 2), (32, 50, 2), (3, 100, 1)])
+def test_default_choice_by_shape(n, k, want):
+    """impl 0 takes the tensor cores once n_pad * k >= 1024 (and n % 4 == 0)."""
+    X = gaussian_mixture(5000, n, 6, seed=n + k)
+    C = X[np.random.default_rng(k).integers(0, X.shape[0], k)].copy()
+    native.set_fullpass_impl(0)
+    Y, f, _ = native.assign(_t(X), _t(C))
+    assert native.last_fullpass_impl() == want
     lab, dist = okm.assign(X, C)
     assert np.array_equal(Y.cpu().numpy(), lab) and f == okm.exact_sum(dist)
-    native.set_fullpass_impl(1)
-    with pytest.raises(native.BigmeansError):
-        native.assign(_t(X), _t(C))
 
 
 def test_ties_between_duplicated_centroids():
@@ -121,3 +132,5 @@ def test_misaligned_x_is_rejected():
 def test_bad_impl_value_is_rejected():
     with pytest.raises(native.BigmeansError):
         native.set_fullpass_impl(7)
+    with pytest.raises(native.BigmeansError):
+        native.set_fullpass_impl(-1)
