@@ -2,7 +2,7 @@
 
 Competitive stochastic sample size Big-means, restated step by step from
 Algorithm 1 and its description (Sec. 4.2, Sec. 4.3), with the settings of
-Sec. 5.  Readings of points the paper leaves open (all listed in the design doc):
+Sec. 5.  Readings of points the paper leaves open:
 
 * the uniform sample is drawn without replacement: bounded draws r_0, r_1, ...
   in [0, m) are taken in counter order and repeats are skipped until s

@@ -11,7 +11,9 @@
 #pragma once
 #include <cstdint>
 #include <mutex>
+#include <map>
 #include <set>
+#include <tuple>
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
 
@@ -116,6 +118,37 @@ inline cudaError_t allow_max_smem(const void* func) {
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
     if (e == cudaSuccess) done.insert(func);
+    return e;
+}
+
+// Resident CTAs per SM of `func` at (threads, dynamic shared memory),
+// computed once per triple (the launchers call this on every launch).
+inline cudaError_t blocks_per_sm(const void* func, int threads, size_t smem, int* out) {
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, int, size_t>, int> memo;
+    const auto key = std::make_tuple(func, threads, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const auto it = memo.find(key);
+        if (it != memo.end()) { *out = it->second; return cudaSuccess; }
+    }
+    int v = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, func, threads, smem);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    memo[key] = v;
+    *out = v;
+    return cudaSuccess;
+}
+// Attributes of `func`, read once.
+inline cudaError_t func_attributes(const void* func, cudaFuncAttributes* out) {
+    static std::mutex mu;
+    static std::map<const void*, cudaFuncAttributes> memo;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto it = memo.find(func);
+    if (it != memo.end()) { *out = it->second; return cudaSuccess; }
+    const cudaError_t e = cudaFuncGetAttributes(out, func);
+    if (e == cudaSuccess) memo[func] = *out;
     return e;
 }
 
@@ -285,13 +318,50 @@ __device__ __forceinline__ float d32(const float (&x)[NP], const float* __restri
     return acc;
 }
 
+// The same d32(x, c) from the row held as m2x = -2 x (dimension pairs):
+// fma(1/2, -2 x_d, c_d) = fl(c_d - x_d) = -fl(x_d - c_d) (one rounding of an
+// exact value), so its square is the direct form's t*t; the squares are
+// added in ascending d as above.
+template <int NP>
+__device__ __forceinline__ float d32_m2x(const float2 (&m2x)[NP / 2], const float* __restrict__ c) {
+    const float2 half = make_float2(0.5f, 0.5f);
+    float acc = 0.f;
+#pragma unroll
+    for (int d4 = 0; d4 < NP / 4; ++d4) {
+        const float4 cv = reinterpret_cast<const float4*>(c)[d4];
+        float2 t0 = __ffma2_rn(half, m2x[2 * d4 + 0], make_float2(cv.x, cv.y));
+        float2 t1 = __ffma2_rn(half, m2x[2 * d4 + 1], make_float2(cv.z, cv.w));
+        t0 = __fmul2_rn(t0, t0);
+        t1 = __fmul2_rn(t1, t1);
+        acc = __fadd_rn(acc, t0.x);
+        acc = __fadd_rn(acc, t0.y);
+        acc = __fadd_rn(acc, t1.x);
+        acc = __fadd_rn(acc, t1.y);
+    }
+    return acc;
+}
+// An upper bound of ||x||^2 from m2x = -2 x: every operation rounds upward
+// (so any order bounds the sum from above); the factor 1/4 is applied last.
+template <int NP>
+__device__ __forceinline__ float xnorm2_up_m2x(const float2 (&m2x)[NP / 2]) {
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < NP / 2; ++d) s = __ffma2_ru(m2x[d], m2x[d], s);
+    return __fmul_ru(0.25f, __fadd_ru(s.x, s.y));
+}
+
 // Certificate constants of one centroid set (upper bounds, rounded upward):
 //   cmax2 >= max_j ||c_j||^2, cmax >= sqrt(cmax2).
 struct CertC { float cmax2, cmax; };
 
-// Per-row certificate for the expanded-form argmin (see the design doc for the
-// derivation).  g1 <= g2 are the two least values of
-// fl(||c||^2 + sum(-2 x_d) c_d) over centroids; xn2 >= ||x||^2, xn >= ||x||.
+// Per-row certificate for the expanded-form argmin.  g1 <= g2 are the two
+// least values of g_j = fl(||c_j||^2 + sum(-2 x_d) c_j,d) over centroids;
+// xn2 >= ||x||^2, xn >= ||x||.  Each g_j is within B = gB (cmax2 + 2 ||x||
+// cmax) of the exact ||c_j||^2 - 2 x.c_j (an NP + 1 term sum of rounded
+// products), so the exact squared distance to the centroid of g1 is at most
+// d1 = g1 + B + ||x||^2; the FP32 direct form of a distance D lies within
+// gamma_{NP+2} D of D.  Hence a centroid whose g exceeds g1 by more than
+// 2 B + gp2 d1 has a larger FP32 direct-form distance.
 // gB >= gamma_{2NP+2}, gp2 >= 2 (1 + 2^-14) gamma_{NP+2}.  Returns true when
 // the argmin of the FP32 direct-form distances is certainly the index of g1.
 // Threshold of the certificate: any centroid j with fl_rd(g_j - g1) > thr has

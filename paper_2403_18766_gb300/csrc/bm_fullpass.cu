@@ -142,8 +142,8 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
                     for (int q = 0; q < NP / 4; ++q) {
                         const float4 v = (4 * q < n) ? __ldg(reinterpret_cast<const float4*>(p) + q)
                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                        m2x[r][2 * q + 0] = make_float2(-2.f * v.x, -2.f * v.y);
-                        m2x[r][2 * q + 1] = make_float2(-2.f * v.z, -2.f * v.w);
+                        m2x[r][2 * q + 0] = __fmul2_rn(make_float2(-2.f, -2.f), make_float2(v.x, v.y));
+                        m2x[r][2 * q + 1] = __fmul2_rn(make_float2(-2.f, -2.f), make_float2(v.z, v.w));
                     }
                 } else {
 #pragma unroll
@@ -195,25 +195,19 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
         for (int r = 0; r < RT; ++r) {
             const long long row = base + 32 * r + lane;
             if (row >= m) continue;
-            float x[NP];
-            float xn2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < NP; ++d) {
-                x[d] = -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x);
-                xn2 = __fmaf_ru(x[d], x[d], xn2);
-            }
+            const float xn2 = xnorm2_up_m2x<NP>(m2x[r]);
             const float xn = __fsqrt_ru(xn2);
             int lab;
             float dv;
             if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
                 lab = j1[r];
-                dv = d32<NP>(x, Cg + (size_t)lab * kCs);
+                dv = d32_m2x<NP>(m2x[r], Cg + (size_t)lab * kCs);
             } else {
                 resc++;
                 lab = 0;
-                dv = d32<NP>(x, Cs);
+                dv = d32_m2x<NP>(m2x[r], Cs);
                 for (int j = 1; j < k; ++j) {
-                    const float dj = d32<NP>(x, Cs + (size_t)j * NP);
+                    const float dj = d32_m2x<NP>(m2x[r], Cs + (size_t)j * NP);
                     if (dj < dv) { dv = dj; lab = j; }
                 }
             }
@@ -322,7 +316,7 @@ static cudaError_t launch_fullpass_t(const float* X, long long m, int n, const f
     cudaError_t e = allow_max_smem((const void*)fullpass_kernel<NP>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fullpass_kernel<NP>, kFpThreads, smem);
+    e = blocks_per_sm((const void*)fullpass_kernel<NP>, kFpThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     const long long warp_tiles = (m + 32ll * FpRows<NP>::v - 1) / (32ll * FpRows<NP>::v);
     const long long ctas = (warp_tiles + kFpThreads / 32 - 1) / (kFpThreads / 32);

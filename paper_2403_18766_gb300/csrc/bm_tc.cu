@@ -403,7 +403,7 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
     cudaError_t e = allow_max_smem((const void*)tc_fullpass_kernel);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fullpass_kernel, kTcThreads, smem);
+    e = blocks_per_sm((const void*)tc_fullpass_kernel, kTcThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, std::min(per_sm, 512 / kTcTmemCols));     // tensor-memory columns per SM
     const long long tiles = (m + kTcRows - 1) / kTcRows;

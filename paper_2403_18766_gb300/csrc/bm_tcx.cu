@@ -525,7 +525,7 @@ cudaError_t launch_t(const CUtensorMap& tm, long long m, const float* C, int k, 
     smem = std::max(smem, (size_t)(228 * 1024) / (size_t)(tmem_per_sm + 1) + 1024);
     smem = std::min<size_t>(smem, 219 * 1024);
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, tcx_fullpass_kernel<NP, NG>);
+    cudaError_t e = func_attributes((const void*)tcx_fullpass_kernel<NP, NG>, &fa);
     if (e != cudaSuccess) return e;
     const int warps_alloc = (threads / 32 + 3) & ~3;            // warps are given registers in fours
     if ((long long)fa.numRegs * 32 * warps_alloc > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
@@ -533,7 +533,7 @@ cudaError_t launch_t(const CUtensorMap& tm, long long m, const float* C, int k, 
     e = allow_max_smem((const void*)tcx_fullpass_kernel<NP, NG>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tcx_fullpass_kernel<NP, NG>, threads, smem);
+    e = blocks_per_sm((const void*)tcx_fullpass_kernel<NP, NG>, threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, std::min(per_sm, tmem_per_sm));
     const long long tiles = (m + kTxRows - 1) / kTxRows;

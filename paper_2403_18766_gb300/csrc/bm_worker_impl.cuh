@@ -245,25 +245,19 @@ struct Worker {
             for (int r = 0; r < RT; ++r) {
                 const long long row = base + r;
                 const bool valid = row < hi;
-                float x[NP];
-                float xn2 = 0.f;
-#pragma unroll
-                for (int d = 0; d < NP; ++d) {
-                    x[d] = -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x);
-                    xn2 = __fmaf_ru(x[d], x[d], xn2);
-                }
+                const float xn2 = xnorm2_up_m2x<NP>(m2x[r]);
                 const float xn = __fsqrt_ru(xn2);
                 int lab = 0;
                 float dv = 0.f;
                 if (valid) {
                     if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
                         lab = j1[r];
-                        dv = d32<NP>(x, sm.Ccur + (size_t)lab * NP);
+                        dv = d32_m2x<NP>(m2x[r], sm.Ccur + (size_t)lab * NP);
                     } else {
                         resc++;
-                        dv = d32<NP>(x, sm.Ccur);
+                        dv = d32_m2x<NP>(m2x[r], sm.Ccur);
                         for (int j = 1; j < k; ++j) {
-                            const float dj = d32<NP>(x, sm.Ccur + (size_t)j * NP);
+                            const float dj = d32_m2x<NP>(m2x[r], sm.Ccur + (size_t)j * NP);
                             if (dj < dv) { dv = dj; lab = j; }
                         }
                     }
@@ -279,18 +273,23 @@ struct Worker {
                     const unsigned mv = __ballot_sync(0xffffffffu, moved);
                     if (__popc(mv) > 8) {
                         if (moved) {
-                            // the row is in registers (x): no reload from the sample
+                            // the row is in registers (x = -m2x / 2, exact): no
+                            // reload from the sample
                             atomicAdd(&sm.cnt[lab], 1);
                             int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
 #pragma unroll
                             for (int d = 0; d < NP; ++d)
-                                if (d < n) ok &= acc_digits(wb + d * kDigits, x[d], gx, inex);
+                                if (d < n)
+                                    ok &= acc_digits(wb + d * kDigits,
+                                                     -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x), gx, inex);
                             if (oldlab[r] >= 0) {
                                 atomicSub(&sm.cnt[oldlab[r]], 1);
                                 int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
 #pragma unroll
                                 for (int d = 0; d < NP; ++d)
-                                    if (d < n) ok &= acc_digits(wo + d * kDigits, -x[d], gx, inex);
+                                    if (d < n)
+                                        ok &= acc_digits(wo + d * kDigits,
+                                                         0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x), gx, inex);
                             }
                             lab_prev[row] = lab;
                         }
