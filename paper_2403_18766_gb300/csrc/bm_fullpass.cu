@@ -341,7 +341,7 @@ int fullpass_impl_setting() { return g_fullpass_impl.load(); }
 // By shape: the FP32-ALU pass costs about k NP / 2 packed FMAs per row, the
 // tensor-core pass a fixed epilogue per row and centroid column, so the
 // tensor cores win once the contraction per row is large.
-bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k >= 1024; }
+bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k > 1024; }
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int sms, cudaStream_t st) {
