@@ -337,6 +337,16 @@ int32_t bm_get_rows_per_cta(void);
  * the tile.  Process-wide, read at each round's launch. */
 bm_status bm_set_big_clusters(int32_t on);
 int32_t bm_get_big_clusters(void);
+/* How samples are drawn without replacement (Sec. 4.1: a uniform sample of
+ * s distinct points, here the first s distinct values of the job's counter
+ * stream of bounded draws, in order of first occurrence).  impl 0 (default):
+ * a shared-memory bitmap of the m indices where it fits (m up to about
+ * 1.1e6, less when the worker's shared memory is large), else per-job
+ * open-addressing tables in device memory; impl 1: always the tables.
+ * Both give identical samples.  Other values: BM_EINVAL.  Process-wide,
+ * read when each sampling launch is prepared. */
+bm_status bm_set_sampler_impl(int32_t impl);
+int32_t bm_get_sampler_impl(void);
 bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
                                    const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
                                    void* stream, const int32_t* candidates, int32_t n_candidates,

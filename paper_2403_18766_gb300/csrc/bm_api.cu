@@ -182,6 +182,7 @@ std::atomic<int> g_rows_per_cta{kRowsPerCta};
 // 1: workers whose cluster is at the size cap and still above the tile run
 // with 512-thread CTAs (twice the warps per SM for the longest workers).
 std::atomic<int> g_big_tpb{0};
+std::atomic<int> g_sample_tables{0};
 
 // CTAs per worker cluster: about rows_per_cta sample rows per CTA, at most
 // max_cs, and never more than kMaxRowsPerCta rows per CTA (0 = impossible).
@@ -298,6 +299,12 @@ SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs, int parity = 0) {
     a.H = c->H; a.table_stride = c->H; a.table = c->table + J * a.table_stride;
     a.gen_base = c->gen;
     c->gen += (unsigned int)jobs;
+    // shared-memory bitmap of the m values when it fits beside a worker CTA
+    const long long words = (c->m + 31) / 32;
+    const size_t sb = sample_smem_bytes((int)std::min<long long>(words, 1 << 30));
+    if (mode != kSampleGather && !g_sample_tables.load() && words <= (1 << 30) && sb <= 144 * 1024 &&
+        sb + worker_smem(c->np, c->k) <= 200 * 1024)
+        a.bitmap_words = (int)words;
     a.job_s = c->job_s + J; a.glob = c->glob;
     return a;
 }
@@ -707,6 +714,13 @@ bm_status bm_set_big_clusters(int32_t on) {
     return BM_OK;
 }
 int32_t bm_get_big_clusters(void) { return g_big_tpb.load(); }
+
+bm_status bm_set_sampler_impl(int32_t impl) {
+    if (impl != 0 && impl != 1) return fail(BM_EINVAL, "sampler impl = %d must be 0 or 1", impl);
+    g_sample_tables.store(impl);
+    return BM_OK;
+}
+int32_t bm_get_sampler_impl(void) { return g_sample_tables.load(); }
 
 bm_status bm_autotune_rows_per_cta(const float* X_dev, int64_t m, int32_t n, int32_t k,
                                    const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,

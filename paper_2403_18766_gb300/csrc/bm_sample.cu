@@ -7,8 +7,10 @@
 // into contiguous padded rows that the worker kernel then reuses.
 //
 // A sample of size s is the first s distinct values among the bounded draws
-// r_0, r_1, ... of its Philox stream, in order of first occurrence.  Each job
-// inserts its draws into an open-addressing table whose slots hold
+// r_0, r_1, ... of its Philox stream, in order of first occurrence.  When a
+// bitmap of the m values fits in shared memory, a job marks the values it has
+// taken in that bitmap (sample_by_bitmap); otherwise it inserts its draws into
+// an open-addressing table in global memory whose slots hold
 // (generation << 32 | t): the generation of the job marks a slot as used, so
 // the table never needs clearing, and the value of a slot is draws[t].  A
 // draw t is kept when the slot of its value holds t itself (the least t).
@@ -69,6 +71,60 @@ __device__ __forceinline__ long long pow2_at_least(long long v) {
     return p;
 }
 
+// The same sample with a shared-memory bitmap of the m values (used when it
+// fits): the draws are taken in chunks of kThreads in counter order.  A draw
+// t of value r is the first occurrence of r when r's bit is clear at the
+// start of t's chunk and t is the least draw of r inside the chunk (a small
+// shared hash table keyed by r keeps that least t).  The chunk's first
+// occurrences extend the sample in t order and then set their bits.  Returns
+// the number of values found (s, or fewer when `cap` draws were not enough).
+__device__ long long sample_by_bitmap(const SampleArgs& a, long long s, unsigned long long k1, long long cap,
+                                      long long* idx, long long* red64) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* mini = reinterpret_cast<unsigned long long*>(smem_raw);   // kMiniSlots
+    unsigned int* bits = reinterpret_cast<unsigned int*>(mini + kMiniSlots);      // bitmap_words
+    const long long m = a.m;
+    for (int i = threadIdx.x; i < a.bitmap_words; i += kThreads) bits[i] = 0u;
+    for (int i = threadIdx.x; i < kMiniSlots; i += kThreads) mini[i] = ~0ull;
+    __syncthreads();
+    const unsigned long long thr = lemire_thr((unsigned long long)m);
+    long long got = 0;
+    for (long long t0 = 0; t0 < cap && got < s; t0 += kThreads) {     // block-uniform
+        const long long t = t0 + threadIdx.x;
+        unsigned int r = 0, h = 0;
+        bool cand = false;
+        if (t < cap) {
+            const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
+            r = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
+            cand = ((bits[r >> 5] >> (r & 31)) & 1u) == 0u;
+        }
+        const unsigned long long key = ((unsigned long long)r << 32) | (unsigned int)t;
+        if (cand) {   // at most kThreads keys in 4 kThreads slots: a free slot always exists
+            h = tab_hash(r) & (kMiniSlots - 1);
+            for (int p = 0; p < kMiniSlots; ++p) {
+                unsigned long long cur = mini[h];
+                if (cur == ~0ull) {
+                    cur = atomicCAS(&mini[h], ~0ull, key);
+                    if (cur == ~0ull) break;
+                }
+                if ((unsigned int)(cur >> 32) == r) { atomicMin(&mini[h], key); break; }
+                h = (h + 1u) & (kMiniSlots - 1);
+            }
+        }
+        __syncthreads();
+        const bool first = cand && mini[h] == key;
+        __syncthreads();
+        if (cand) mini[h] = ~0ull;                       // empty again for the next chunk
+        if (first) atomicOr(&bits[r >> 5], 1u << (r & 31));
+        long long total;
+        const long long excl = block_exscan(first ? 1ll : 0ll, red64, &total);
+        if (first && got + excl < s) idx[got + excl] = (long long)r;
+        got += total;
+    }
+    __syncthreads();
+    return got < s ? got : s;
+}
+
 template <int NP>
 __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
     __shared__ long long red64[kWarps + 1];
@@ -98,7 +154,16 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
     }
     long long* idx = a.idx + (long long)job * a.idx_stride;
     float* S = a.S + (long long)job * a.S_stride;
-    if (a.mode != kSampleGather) {
+    if (a.mode != kSampleGather && a.bitmap_words > 0) {
+        const unsigned long long k1 = stream_k1(purpose, worker, rnd, pss);
+        const long long got = s > 0 ? sample_by_bitmap(a, s, k1, a.Tcap, idx, red64) : 0;
+        if (got < s) {
+            if (threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
+            s = 0;
+        }
+        __threadfence_block();
+        __syncthreads();
+    } else if (a.mode != kSampleGather) {
         const long long m = a.m;
         unsigned int* draws = a.draws + (long long)job * a.draws_stride;
         unsigned long long* tab = a.table + (long long)job * a.table_stride;
@@ -156,8 +221,10 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
         if (threadIdx.x == 0 && a.job_s) a.job_s[job] = (int)s;
         return;
     }
-    // gather (padded rows, zeros in the padding)
+    // gather (padded rows, zeros in the padding); 16-byte loads when the rows
+    // of X are 16-byte aligned
     const int n = a.n;
+    const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
     const long long items = s * (NP / 4);
     for (long long e = threadIdx.x; e < items; e += kThreads) {
         const long long i = e / (NP / 4);
@@ -166,10 +233,14 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (row >= 0 && row < a.m) {
             const float* xr = a.X + row * (long long)n;
-            v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
-            v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
-            v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
-            v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+            if (vec) {
+                if (4 * q < n) v = __ldg(reinterpret_cast<const float4*>(xr) + q);
+            } else {
+                v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
+                v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
+                v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
+                v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+            }
         } else if (q == 0) {
             atomicOr(&a.glob->err, kErrArgs);
         }
@@ -180,7 +251,12 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
 
 template <int NP>
 static cudaError_t launch_sample_t(const SampleArgs& a, int jobs, cudaStream_t st) {
-    sample_kernel<NP><<<jobs, kThreads, 0, st>>>(a);
+    const size_t smem = sample_smem_bytes(a.bitmap_words);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = allow_max_smem((const void*)sample_kernel<NP>);
+        if (e != cudaSuccess) return e;
+    }
+    sample_kernel<NP><<<jobs, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -84,10 +84,18 @@ struct SampleArgs {
     long long Tcap;
     unsigned long long* table; long long H; long long table_stride;
     unsigned int gen_base;                     // generation of job 0 (tables are never cleared)
+    int bitmap_words;                          // > 0: draw with a shared-memory bitmap of the m
+                                               // values ((m + 31) / 32 words) instead of the tables
     int* job_s;                                // out: sample size of each job
     Globals* glob;
 };
 
+// Slots of the per-chunk hash table of the bitmap path (4 per thread).
+constexpr int kMiniSlots = 4 * kThreads;
+// Dynamic shared memory of a sampling launch.
+inline size_t sample_smem_bytes(int bitmap_words) {
+    return bitmap_words > 0 ? (size_t)kMiniSlots * 8 + (((size_t)bitmap_words * 4 + 15) & ~(size_t)15) : 0;
+}
 cudaError_t launch_sample(int np, const SampleArgs& a, int jobs, cudaStream_t st);
 
 }  // namespace bm

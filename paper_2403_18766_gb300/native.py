@@ -112,6 +112,8 @@ SIGNATURES = {
     "bm_trim_memory": (_i32, []),
     "bm_set_big_clusters": (_i32, [_i32]),
     "bm_get_big_clusters": (_i32, []),
+    "bm_set_sampler_impl": (_i32, [_i32]),
+    "bm_get_sampler_impl": (_i32, []),
     "bm_get_rows_per_cta": (_i32, []),
     "bm_autotune_rows_per_cta": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_i32), _i32,
                                         ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
@@ -448,6 +450,15 @@ def set_big_clusters(on):
 
 def get_big_clusters():
     return int(lib.bm_get_big_clusters())
+
+
+def set_sampler_impl(impl):
+    """bm_set_sampler_impl: 0 = shared-memory bitmap where it fits, 1 = device tables."""
+    _check(lib.bm_set_sampler_impl(int(impl)))
+
+
+def get_sampler_impl():
+    return int(lib.bm_get_sampler_impl())
 
 
 def trim_memory():

@@ -36,13 +36,48 @@ def _eq_f32(a, b):
 
 
 # ------------------------------------------------------------------ a1 sample
+@pytest.fixture
+def sampler_impl(request):
+    native.set_sampler_impl(request.param)
+    yield request.param
+    native.set_sampler_impl(0)
+
+
+@pytest.mark.parametrize("sampler_impl", [0, 1], indirect=True)
 @pytest.mark.parametrize("m,s", [(1, 1), (7, 0), (50, 50), (1000, 999), (10_000, 2000),
-                                 (100_000, 64_000), (1_000_000, 65_537), (3, 2)])
-def test_sample_bit_exact(m, s):
+                                 (100_000, 64_000), (1_000_000, 65_537), (3, 2), (257, 256),
+                                 (2_500_000, 3000)])
+def test_sample_bit_exact(m, s, sampler_impl):
+    """Both samplers (shared-memory bitmap where it fits, device tables)
+    against the oracle; m = 2.5e6 takes the tables even in the default mode."""
     for purpose, w, t, p in [(orng.P_PASS, 0, 0, 0), (orng.P_EVAL, 3, 7, 0), (orng.P_FINAL, 0, 0, 0)]:
         got = native.sample(12345, purpose, w, t, p, m, s).cpu().numpy()
         ref = obm.sample_indices(12345, purpose, w, t, p, m, s)
         assert np.array_equal(got, ref), (m, s, purpose)
+
+
+def test_fit_same_with_either_sampler():
+    X = gaussian_mixture(60_000, 8, 6, seed=41)
+    pol = dict(s_min=2000, s_max=50_000, workers=4, passes=3)
+    bud = dict(rounds=2, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    outs = []
+    try:
+        for impl in (0, 1):
+            native.set_sampler_impl(impl)
+            outs.append(native.fit(_t(X), 6, native.make_policy(**pol), native.make_budget(**bud), seed=8))
+    finally:
+        native.set_sampler_impl(0)
+    (C0, Y0, r0), (C1, Y1, r1) = outs
+    assert torch.equal(C0.view(torch.int32), C1.view(torch.int32)) and torch.equal(Y0, Y1)
+    assert r0["f_full"] == r1["f_full"] and r0["s_opt"] == r1["s_opt"]
+    ref = obm.bigmeans(X, 6, pol, bud, seed=8)
+    _assert_same(C0.cpu().numpy(), Y0.cpu().numpy(), r0, ref)
+
+
+def test_sampler_impl_value_checked():
+    with pytest.raises(native.BigmeansError):
+        native.set_sampler_impl(2)
+    assert native.get_sampler_impl() == 0
 
 
 # ------------------------------------------------------------------ a2 gather
