@@ -51,8 +51,8 @@ int last_fullpass_impl();
 int fullpass_impl_setting();
 bool tcx_eligible(const float* X, long long m, int n, int np, int k);
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
-                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, int sms,
-                               cudaStream_t st);
+                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, float gB,
+                               float gp2, int sms, cudaStream_t st);
 }  // namespace bm
 
 using namespace bm;
@@ -1160,10 +1160,12 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
     CU(lib_alloc(&base, gb + (size_t)m * 4, sm));
     Globals* g = (Globals*)base;
     int* queue = (int*)((char*)base + gb);
+    float gB, gp2;
+    cert_constants(64, gB, gp2);                   // rows of the precision form are 64 wide
     cudaError_t e;
     if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
         (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
-        (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, labels_out_dev, queue, g,
+        (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, labels_out_dev, queue, g, gB, gp2,
                                 sm_count(), sm))) {
         cudaFreeAsync(base, sm);
         cudaStreamSynchronize(sm);

@@ -194,25 +194,45 @@ fullpass_kernel(const float* __restrict__ X, long long m, int n, const float* __
 #pragma unroll
         for (int r = 0; r < RT; ++r) {
             const long long row = base + 32 * r + lane;
-            if (row >= m) continue;
+            const bool valid = row < m;
             const float xn2 = xnorm2_up_m2x<NP>(m2x[r]);
             const float xn = __fsqrt_ru(xn2);
-            int lab;
-            float dv;
-            if (certified(g1[r], g2[r], xn2, xn, cc, gB, gp2)) {
-                lab = j1[r];
-                dv = d32_m2x<NP>(m2x[r], Cg + (size_t)lab * kCs);
-            } else {
-                resc++;
-                lab = 0;
-                dv = d32_m2x<NP>(m2x[r], Cs);
-                for (int j = 1; j < k; ++j) {
+            const bool good = certified(g1[r], g2[r], xn2, xn, cc, gB, gp2);
+            int lab = j1[r];
+            float dv = good ? d32_m2x<NP>(m2x[r], Cg + (size_t)lab * kCs) : 0.f;
+            // uncertain rows, one at a time by the whole warp (no divergence
+            // into a per-lane scan of all k): lanes take centroids lane,
+            // lane + 32, ... of the row (read again by every lane; its lane's
+            // registers are free by now), then a warp argmin, lowest index on
+            // ties
+            unsigned pend = __ballot_sync(0xffffffffu, valid && !good);
+            if (lane == 0) resc += __popc(pend);
+            while (pend) {
+                const int src = __ffs(pend) - 1;
+                pend &= pend - 1u;
+                const float* p = X + (base + 32 * r + src) * (long long)n;
+#pragma unroll
+                for (int d = 0; d < NP / 2; ++d)
+                    m2x[r][d] = make_float2((2 * d < n) ? -2.f * __ldg(p + 2 * d) : 0.f,
+                                            (2 * d + 1 < n) ? -2.f * __ldg(p + 2 * d + 1) : 0.f);
+                float bd = __int_as_float(0x7f800000);
+                int bj = 0x7fffffff;
+                for (int j = lane; j < k; j += 32) {
                     const float dj = d32_m2x<NP>(m2x[r], Cs + (size_t)j * NP);
-                    if (dj < dv) { dv = dj; lab = j; }
+                    if (dj < bd || bj == 0x7fffffff) { bd = dj; bj = j; }
                 }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                    if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
+                }
+                if (lane == src) { dv = bd; lab = bj; }
             }
-            acc_obj(facc, dv, gr.gf, inex);
-            if (labels) labels[row] = lab;
+            if (valid) {
+                acc_obj(facc, dv, gr.gf, inex);
+                if (labels) labels[row] = lab;
+            }
         }
     }
     // CTA reduction (one pass) and the grid-wide total
@@ -341,7 +361,7 @@ int fullpass_impl_setting() { return g_fullpass_impl.load(); }
 // By shape: the FP32-ALU pass costs about k NP / 2 packed FMAs per row, the
 // tensor-core pass a fixed epilogue per row and centroid column, so the
 // tensor cores win once the contraction per row is large.
-bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k > 1024; }
+bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k > 1600; }
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int sms, cudaStream_t st) {

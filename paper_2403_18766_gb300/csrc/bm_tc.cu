@@ -300,53 +300,142 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
     }
 }
 
-// Exact re-score of the queued close calls (FP32 direct form over all k,
-// lowest index on ties), thread per row with the row in registers; adds the
-// rows' distances to the objective words and, in its last CTA, rounds the
-// objective of both kernels once.
+// Exact re-score of the queued close calls: the exact-mode label (argmin of
+// the FP32 direct form, lowest index on ties) and distance of each queued
+// row, found like the FP32-ALU full pass does -- the expanded form
+// g_j = fl(||c_j||^2) + sum_d (-2 x_d) c_j,d in packed FP32 FMAs (four
+// interleaved partial sums, a tree of NP + 1 terms inside the gamma_{2NP+2}
+// bound), the certificate of the two least values, the winner's direct form;
+// rows the certificate does not settle take the direct form over all k.
+// Thread per row with the row in registers; adds the rows' distances to the
+// objective words and, in its last CTA, rounds the objective of both kernels
+// once.
+constexpr int kRsStride = kTcK + 4;      // gathered copy: odd number of 16-byte units per row
 __global__ void __launch_bounds__(256)
 rescore_kernel(const float* __restrict__ Xf, const float* __restrict__ xnorm, long long m, int n,
                const float* __restrict__ C, int k, const int* __restrict__ queue, int* __restrict__ labels,
-               Globals* g) {
+               Globals* g, float gB, float gp2) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    float* Cs = reinterpret_cast<float*>(smem_raw);                 // k x 64
+    float* Cs = reinterpret_cast<float*>(smem_raw);                 // k x 64 (same centroid in every lane)
+    float* Cg = Cs + (size_t)k * kTcK;                               // k x kRsStride (per-lane winners)
+    float* CC = Cg + (size_t)k * kRsStride;                          // k
     __shared__ unsigned __int128 red128[8];
     __shared__ unsigned long long red64[8];
+    __shared__ unsigned int redu[8];
+    __shared__ CertC cert;
     __shared__ bool last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (g->nonfinite) return;
     for (int e = tid; e < k * kTcK; e += 256) {
         const int j = e / kTcK, d = e % kTcK;
-        Cs[e] = d < n ? C[(size_t)j * n + d] : 0.f;
+        const float v = d < n ? C[(size_t)j * n + d] : 0.f;
+        Cs[e] = v;
+        Cg[(size_t)j * kRsStride + d] = v;
     }
     __syncthreads();
+    unsigned int mx = 0;
+    for (int j = tid; j < k; j += 256) {
+        float acc = 0.f, up = 0.f;
+#pragma unroll 8
+        for (int d = 0; d < kTcK; ++d) {
+            const float c = Cs[(size_t)j * kTcK + d];
+            acc = __fmaf_rn(c, c, acc);
+            up = __fmaf_ru(c, c, up);
+        }
+        CC[j] = acc;
+        mx = max(mx, __float_as_uint(up));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) redu[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned int mm = 0;
+        for (int i = 0; i < 8; ++i) mm = max(mm, redu[i]);
+        cert.cmax2 = __uint_as_float(mm);
+        cert.cmax = __fsqrt_ru(cert.cmax2);
+    }
+    __syncthreads();
+    const CertC cc = cert;
     const long long m_pad = (m + kTcRows - 1) / kTcRows * kTcRows;
     const Grids gr = grids_from_maxbits(max(g->maxbits, __float_as_uint(xnorm[m_pad])));
     const long long q = g->queue_len;
+    const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(Xf) & 15) == 0;
+    // row `row` of Xf as m2x = -2 x, zero past n
+    auto load_m2x = [&](long long row, float2 (&m2x)[kTcK / 2]) {
+        const float* xr = Xf + row * (long long)n;
+        if (vec) {                                                   // 16-byte loads of the row
+#pragma unroll
+            for (int q4 = 0; q4 < kTcK / 4; ++q4) {
+                const float4 v = (4 * q4 < n) ? __ldg(reinterpret_cast<const float4*>(xr) + q4)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                m2x[2 * q4 + 0] = __fmul2_rn(make_float2(-2.f, -2.f), make_float2(v.x, v.y));
+                m2x[2 * q4 + 1] = __fmul2_rn(make_float2(-2.f, -2.f), make_float2(v.z, v.w));
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < kTcK / 2; ++d)
+                m2x[d] = make_float2(2 * d < n ? -2.f * xr[2 * d] : 0.f, 2 * d + 1 < n ? -2.f * xr[2 * d + 1] : 0.f);
+        }
+    };
     unsigned __int128 facc = 0;
     unsigned int inex = 0;
-    for (long long i = (long long)blockIdx.x * 256 + tid; i < q; i += (long long)gridDim.x * 256) {
-        const long long row = queue[i];
-        float x[kTcK];
-        const float* xr = Xf + row * (long long)n;
-#pragma unroll
-        for (int d = 0; d < kTcK; ++d) x[d] = d < n ? xr[d] : 0.f;
-        float best = __int_as_float(0x7f800000);
-        int bj = 0;
+    // warp-uniform trips of 32 queued rows (uncertain rows are resolved by
+    // the whole warp below)
+    for (long long w0 = ((long long)blockIdx.x * 8 + warp) * 32; w0 < q; w0 += (long long)gridDim.x * 256) {
+        const long long i = w0 + lane;
+        const bool valid = i < q;
+        const long long row = valid ? queue[i] : 0;
+        float2 m2x[kTcK / 2];                                        // -2 x, dimension pairs
+        load_m2x(row, m2x);
+        float g1 = __int_as_float(0x7f800000), g2 = g1;
+        int j1 = 0;
         for (int j = 0; j < k; ++j) {
-            const float* cj = Cs + (size_t)j * kTcK;
-            float acc = 0.f;
+            const float4* cj = reinterpret_cast<const float4*>(Cs + (size_t)j * kTcK);
+            float2 ea = make_float2(CC[j], 0.f), eb = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int d = 0; d < kTcK; ++d) {
-                if (d < n) {
-                    const float t = __fsub_rn(x[d], cj[d]);
-                    acc = __fadd_rn(acc, __fmul_rn(t, t));
-                }
+            for (int q4 = 0; q4 < kTcK / 4; ++q4) {
+                const float4 cv = cj[q4];
+                ea = __ffma2_rn(m2x[2 * q4 + 0], make_float2(cv.x, cv.y), ea);
+                eb = __ffma2_rn(m2x[2 * q4 + 1], make_float2(cv.z, cv.w), eb);
             }
-            if (acc < best) { best = acc; bj = j; }
+            const float2 es = __fadd2_rn(ea, eb);
+            const float e = __fadd_rn(es.x, es.y);
+            g2 = fminf(g2, fmaxf(g1, e));
+            j1 = (e < g1) ? j : j1;
+            g1 = fminf(g1, e);
         }
-        acc_obj(facc, best, gr.gf, inex);
-        if (labels) labels[row] = bj;
+        const float xn2 = xnorm2_up_m2x<kTcK>(m2x);
+        const float xn = __fsqrt_ru(xn2);
+        const bool good = certified(g1, g2, xn2, xn, cc, gB, gp2);
+        int lab = j1;
+        float dv = good ? d32_m2x<kTcK>(m2x, Cg + (size_t)j1 * kRsStride) : 0.f;
+        // uncertain rows, one at a time: lanes take centroids lane, lane + 32,
+        // ... of the row (read again by every lane), then a warp argmin with
+        // the lowest index on ties
+        unsigned pend = __ballot_sync(0xffffffffu, valid && !good);
+        while (pend) {
+            const int src = __ffs(pend) - 1;
+            pend &= pend - 1u;
+            load_m2x(__shfl_sync(0xffffffffu, row, src), m2x);
+            float bd = __int_as_float(0x7f800000);
+            int bj = 0x7fffffff;
+            for (int j = lane; j < k; j += 32) {
+                const float dj = d32_m2x<kTcK>(m2x, Cs + (size_t)j * kTcK);
+                if (dj < bd || bj == 0x7fffffff) { bd = dj; bj = j; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
+            }
+            if (lane == src) { dv = bd; lab = bj; }
+        }
+        if (valid) {
+            acc_obj(facc, dv, gr.gf, inex);
+            if (labels) labels[row] = lab;
+        }
     }
     unsigned __int128 F = warp_sum_u128(facc);
     const unsigned long long I = warp_sum((unsigned long long)inex);
@@ -394,8 +483,8 @@ cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad
 }
 
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
-                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, int sms,
-                               cudaStream_t st) {
+                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, float gB,
+                               float gp2, int sms, cudaStream_t st) {
     const int Npad = (k + 15) & ~15;
     // at least 80 KB so that at most two CTAs (2 x 256 tensor-memory
     // columns = all 512) share an SM and no allocation has to wait
@@ -412,10 +501,10 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
                                                                  Npad, tau, labels, queue, g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t rs = (size_t)k * kTcK * 4;
+    const size_t rs = (size_t)k * (kTcK + kRsStride + 1) * 4;
     e = allow_max_smem((const void*)rescore_kernel);
     if (e != cudaSuccess) return e;
-    rescore_kernel<<<sms * 4, 256, rs, st>>>(Xf, xnorm, m, n, C, k, queue, labels, g);
+    rescore_kernel<<<sms * 4, 256, rs, st>>>(Xf, xnorm, m, n, C, k, queue, labels, g, gB, gp2);
     return cudaGetLastError();
 }
 
