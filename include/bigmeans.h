@@ -265,6 +265,20 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
                          int64_t m, int32_t n, const float* C_dev, int32_t k, float tau,
                          int32_t* labels_out_dev, double* f_out_host, bm_report* report_out,
                          void* stream);
+/* bm_assign_bf16_certified -- bm_assign_bf16 with labels certified equal to
+ * those of bm_assign: a row is also re-scored unless its two least g differ
+ * by more than the bound of the BF16 form, 2 B + gp2 (g1 + B + ||x||^2) with
+ * B = 2^-7 (max ||c||^2 + 2 ||x|| max ||c||) (BF16 rounding of x and c,
+ * FP32 accumulation, with a factor 2 of slack) and gp2 the direct form's
+ * relative error at 64 dimensions; ||x||^2 is bounded by norms[r] (1 + 2^-7).
+ * That is, a row keeps the tensor-core label only where that label is
+ * provably the exact-mode argmin.  Distances of rows that are not re-scored
+ * are still ||x||^2 + g (f differs from bm_assign as for bm_assign_bf16).
+ * Arguments, layout, ownership and errors as for bm_assign_bf16. */
+bm_status bm_assign_bf16_certified(const void* Xb_dev, const float* norms_dev, const float* X_dev,
+                                   int64_t m, int32_t n, const float* C_dev, int32_t k, float tau,
+                                   int32_t* labels_out_dev, double* f_out_host, bm_report* report_out,
+                                   void* stream);
 
 /* ---------------------------------------------------------------------------
  * bm_assign_noalloc -- the full-data pass of bm_assign (labels of every row of

@@ -51,8 +51,8 @@ int last_fullpass_impl();
 int fullpass_impl_setting();
 bool tcx_eligible(const float* X, long long m, int n, int np, int k);
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
-                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, float gB,
-                               float gp2, int sms, cudaStream_t st);
+                               const float* C, int k, float tau, int certify, int* labels, int* queue, Globals* g,
+                               float gB, float gp2, int sms, cudaStream_t st);
 }  // namespace bm
 
 using namespace bm;
@@ -1144,9 +1144,9 @@ bm_status bm_pack_bf16(const float* X_dev, int64_t m, int32_t n, void* Xb_out_de
     return BM_OK;
 }
 
-bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m, int32_t n,
-                         const float* C_dev, int32_t k, float tau, int32_t* labels_out_dev, double* f_out_host,
-                         bm_report* rep, void* stream) {
+static bm_status assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m, int32_t n,
+                             const float* C_dev, int32_t k, float tau, int certify, int32_t* labels_out_dev,
+                             double* f_out_host, bm_report* rep, void* stream) {
     if (m < 1 || m >= (1ll << 31)) return fail(BM_EINVAL, "m = %lld out of range", (long long)m);
     if (n < 1 || n > 64) return fail(BM_EINVAL, "n = %d out of range [1, 64]", n);
     if (k < 1 || k > 256) return fail(BM_EINVAL, "k = %d out of range [1, 256] for the tensor-core pass", k);
@@ -1165,8 +1165,8 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
     cudaError_t e;
     if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
         (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
-        (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, labels_out_dev, queue, g, gB, gp2,
-                                sm_count(), sm))) {
+        (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, certify, labels_out_dev, queue, g,
+                                gB, gp2, sm_count(), sm))) {
         cudaFreeAsync(base, sm);
         cudaStreamSynchronize(sm);
         return fail(BM_ECUDA, "tensor-core pass launch: %s", cudaGetErrorString(e));
@@ -1188,6 +1188,18 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
         rep->inexact_terms = (int64_t)h.inexact;
     }
     return BM_OK;
+}
+
+bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m, int32_t n,
+                         const float* C_dev, int32_t k, float tau, int32_t* labels_out_dev, double* f_out_host,
+                         bm_report* rep, void* stream) {
+    return assign_bf16(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, 0, labels_out_dev, f_out_host, rep, stream);
+}
+
+bm_status bm_assign_bf16_certified(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m,
+                                   int32_t n, const float* C_dev, int32_t k, float tau, int32_t* labels_out_dev,
+                                   double* f_out_host, bm_report* rep, void* stream) {
+    return assign_bf16(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, 1, labels_out_dev, f_out_host, rep, stream);
 }
 
 }  // extern "C"

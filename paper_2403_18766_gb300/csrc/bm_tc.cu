@@ -150,7 +150,8 @@ __device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
 __global__ void __launch_bounds__(kTcThreads, 1)
 tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict__ xnorm,
                    const float* __restrict__ Xf, long long m, int n, const float* __restrict__ C, int k,
-                   int Npad, float tau, int* __restrict__ labels, int* __restrict__ queue, Globals* g) {
+                   int Npad, float tau, int certify, float gBF, float gp2, int* __restrict__ labels,
+                   int* __restrict__ queue, Globals* g) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((1024 - (s_addr(smem_raw) & 1023)) & 1023);
     unsigned char* xs = base;                                             // stages
@@ -161,6 +162,8 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
     __shared__ unsigned tmem_slot;
     __shared__ unsigned __int128 red128[kTcThreads / 32];
     __shared__ unsigned long long red64[kTcThreads / 32];
+    __shared__ unsigned int redu[kTcThreads / 32];
+    __shared__ CertC cert;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (g->nonfinite) return;
@@ -196,6 +199,27 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
             acc = __fmaf_rn(b, b, acc);
         }
         ccb[j] = (j < k) ? acc : __int_as_float(0x7f800000);   // padded columns never win
+    }
+    {   // certificate constants from the FP32 centroids (upper bounds)
+        unsigned int mx = 0;
+        for (int j = tid; j < k; j += kTcThreads) {
+            float up = 0.f;
+            for (int d = 0; d < n; ++d) {
+                const float c = C[(size_t)j * n + d];
+                up = __fmaf_ru(c, c, up);
+            }
+            mx = max(mx, __float_as_uint(up));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if (lane == 0) redu[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned int mm = 0;
+            for (int i = 0; i < kTcThreads / 32; ++i) mm = max(mm, redu[i]);
+            cert.cmax2 = __uint_as_float(mm);
+            cert.cmax = __fsqrt_ru(cert.cmax2);
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B visible to the tensor core
     tc_fence_before();
@@ -261,8 +285,18 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
             }
         }
         // Close calls go to a queue re-scored by rescore_kernel with the
-        // exact definition; the others are final here.
-        const bool close = row < m && !(g2 - g1 >= tau * xx);
+        // exact definition; the others are final here.  With `certify`, a
+        // row is also a close call unless the certificate with the BF16
+        // error factor gBF proves that j1 is the exact-mode label: the FP32
+        // ||x||^2 is at most xx (1 + 2^-7) (BF16 rounding of x and the RN sum
+        // of xx), and every g is within gBF (cmax^2 + 2 ||x|| cmax) of
+        // ||c_j||^2 - 2 x.c_j.
+        bool close = row < m && !(g2 - g1 >= tau * xx);
+        if (certify && row < m && !close) {
+            const CertC cc = cert;
+            const float xn2 = __fmul_ru(xx, 1.0f + 0x1p-7f);
+            close = !certified(g1, g2, xn2, __fsqrt_ru(xn2), cc, gBF, gp2);
+        }
         const unsigned cq = __ballot_sync(0xffffffffu, close);
         if (cq) {
             unsigned qbase = 0;
@@ -482,9 +516,15 @@ cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad
     return cudaGetLastError();
 }
 
+// BF16 error factor of the certified precision form: rounding of x and c to
+// BF16 (2^-9 each, so products within 2^-8 + 2^-18 of x c), FP32
+// accumulation over four K = 16 instructions, ||c_bf16||^2 in FP32 and the
+// final fma, with a factor 2 of slack.
+constexpr float kGammaBF16 = 0x1p-7f;
+
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
-                               const float* C, int k, float tau, int* labels, int* queue, Globals* g, float gB,
-                               float gp2, int sms, cudaStream_t st) {
+                               const float* C, int k, float tau, int certify, int* labels, int* queue, Globals* g,
+                               float gB, float gp2, int sms, cudaStream_t st) {
     const int Npad = (k + 15) & ~15;
     // at least 80 KB so that at most two CTAs (2 x 256 tensor-memory
     // columns = all 512) share an SM and no allocation has to wait
@@ -498,7 +538,8 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
     const long long tiles = (m + kTcRows - 1) / kTcRows;
     const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * per_sm, tiles));
     tc_fullpass_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>((const __nv_bfloat16*)Xb, xnorm, Xf, m, n, C, k,
-                                                                 Npad, tau, labels, queue, g);
+                                                                 Npad, tau, certify, kGammaBF16, gp2, labels,
+                                                                 queue, g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t rs = (size_t)k * (kTcK + kRsStride + 1) * 4;

@@ -105,6 +105,8 @@ SIGNATURES = {
     "bm_pack_bf16": (_i32, [_p, _i64, _i32, _p, _p, _p]),
     "bm_assign_bf16": (_i32, [_p, _p, _p, _i64, _i32, _p, _i32, ctypes.c_float, _p,
                               ctypes.POINTER(_dbl), _RP, _p]),
+    "bm_assign_bf16_certified": (_i32, [_p, _p, _p, _i64, _i32, _p, _i32, ctypes.c_float, _p,
+                              ctypes.POINTER(_dbl), _RP, _p]),
     "bm_set_fullpass_impl": (_i32, [_i32]),
     "bm_last_fullpass_impl": (_i32, []),
     "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
@@ -330,16 +332,17 @@ class PackedBF16:
         _check(lib.bm_pack_bf16(_ptr(self.X), m, n, _ptr(self.Xb), _ptr(self.norms), _stream(stream)))
 
 
-def assign_bf16(packed, C, tau=1e-3, labels=True, stream=None):
-    """bm_assign_bf16: precision-form full pass on tensor cores."""
+def assign_bf16(packed, C, tau=1e-3, labels=True, stream=None, certified=False):
+    """bm_assign_bf16 (or bm_assign_bf16_certified): precision-form full pass on tensor cores."""
     C = _dev_f32(C, "C")
     X = packed.X
     Y = torch.empty(X.shape[0], dtype=torch.int32, device=X.device) if labels else None
     f = ctypes.c_double(0)
     rep = Report()
-    _check(lib.bm_assign_bf16(_ptr(packed.Xb), _ptr(packed.norms), _ptr(X), X.shape[0], X.shape[1],
-                              _ptr(C), C.shape[0], float(tau), _ptr(Y), ctypes.byref(f),
-                              ctypes.byref(rep), _stream(stream)))
+    fn = lib.bm_assign_bf16_certified if certified else lib.bm_assign_bf16
+    _check(fn(_ptr(packed.Xb), _ptr(packed.norms), _ptr(X), X.shape[0], X.shape[1],
+              _ptr(C), C.shape[0], float(tau), _ptr(Y), ctypes.byref(f),
+              ctypes.byref(rep), _stream(stream)))
     return Y, f.value, rep.as_dict()
 
 

@@ -109,3 +109,34 @@ def test_default_tau_matches_exact_labels_except_near_ties(m, n, k):
         xx = (Xn[rows].astype(np.float64) ** 2).sum(1)
         assert np.all(srt[:, 1] - srt[:, 0] < 0.05 * xx + 1.0)   # only close calls differ
     assert abs(f - fr) <= 5e-3 * fr
+
+
+@pytest.mark.parametrize("m,n,k", CASES)
+@pytest.mark.parametrize("tau", [0.0, 1e-3])
+def test_certified_labels_equal_the_exact_pass(m, n, k, tau):
+    """bm_assign_bf16_certified: every label equals bm_assign's (a row keeps
+    its tensor-core label only where the BF16 bound proves it), with at least
+    the rows of the plain rule re-scored."""
+    X, C = _case(m, n, k, 17 * m + k)
+    P = native.PackedBF16(X)
+    Y, f, rep = native.assign_bf16(P, C, tau=tau, certified=True)
+    Yr, fr, _ = native.assign(X, C)
+    assert torch.equal(Y, Yr)
+    _, _, rep_plain = native.assign_bf16(P, C, tau=tau)
+    assert rep["rescored_rows"] >= rep_plain["rescored_rows"]
+    assert abs(f - fr) <= 5e-3 * fr
+
+
+def test_certified_near_ties_and_far_from_origin():
+    """Duplicated and nearly duplicated centroids, and data far from the origin
+    (where BF16 cannot separate most rows): labels still equal the exact pass."""
+    X = gaussian_mixture(20_000, 16, 8, seed=23) + np.float32(500.0)
+    C = X[np.random.default_rng(5).integers(0, X.shape[0], 12)].copy()
+    C[3] = C[2]
+    C[7] = C[6] + np.float32(1e-3)
+    Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    P = native.PackedBF16(Xd)
+    Y, f, rep = native.assign_bf16(P, Cd, tau=0.0, certified=True)
+    Yr, fr, _ = native.assign(Xd, Cd)
+    assert torch.equal(Y, Yr)
+    assert rep["rescored_rows"] > 0
