@@ -332,7 +332,7 @@ int32_t bm_last_fullpass_impl(void);
 /* ---------------------------------------------------------------------------
  * Cluster tile of the worker kernel and its autotuner.
  * A worker runs as one thread-block cluster of up to 16 CTAs with about
- * `rows_per_cta` sample rows per CTA (default 2048).  The value changes only
+ * `rows_per_cta` sample rows per CTA (default 1024).  The value changes only
  * speed: labels, centroids and objectives are identical for every value (all
  * reductions are exact).  The setting is process-wide and read when a fit is
  * created.

@@ -91,7 +91,7 @@ bm_status fail(bm_status s, const char* fmt, ...) {
     } while (0)
 
 constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kRowsPerCta = 2048;
+constexpr int kRowsPerCta = 1024;
 
 int padded_dim(int n) {
     if (n <= 4) return 4;

@@ -325,7 +325,7 @@ def test_autotuner_picks_a_candidate_and_sets_it():
         assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
     finally:
         native.set_rows_per_cta(0)
-    assert native.get_rows_per_cta() == 2048
+    assert native.get_rows_per_cta() == 1024
 
 
 def test_results_do_not_depend_on_big_cluster_ctas():

@@ -52,11 +52,11 @@ def test_footprint_is_workspace_plus_buffers():
 
 
 def test_cluster_tile_setting_is_checked():
-    assert native.get_rows_per_cta() == 2048
+    assert native.get_rows_per_cta() == 1024
     for bad in (-1, 100, 40_000):
         with pytest.raises(native.BigmeansError):
             native.set_rows_per_cta(bad)
     native.set_rows_per_cta(4096)
     assert native.get_rows_per_cta() == 4096
     native.set_rows_per_cta(0)
-    assert native.get_rows_per_cta() == 2048
+    assert native.get_rows_per_cta() == 1024
