@@ -116,7 +116,9 @@ typedef struct {
     double f_incumbent;     /* least full f seen over rounds (or f_full)      */
     int64_t s_opt;          /* rounded mean of L                              */
     int32_t best_worker;    /* argmin of the common recheck                   */
-    int32_t rounds_done;    /* rounds completed by every worker               */
+    int32_t rounds_done;    /* rounds launched (with a time budget the workers
+                               stop between passes at the deadline, so the last
+                               round can be partial: see passes_done)         */
     int64_t passes_done;    /* passes over all workers                        */
     int64_t lloyd_iters;    /* centroid updates over all Lloyd runs           */
     int64_t assign_rows;    /* rows assigned inside Lloyd runs (sum s_w per

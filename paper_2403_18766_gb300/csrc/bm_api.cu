@@ -514,8 +514,6 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     bm_status s;
     if ((s = ensure_streams(c))) return s;
     if (r1 != r0 + 1) return fail(BM_EINTERNAL, "one round per launch");
-    const int big = 0x7fffffff;
-    CU(cudaMemcpyAsync(&c->glob->rounds_done, &big, sizeof(int), cudaMemcpyHostToDevice, c->st));
     const int parity = r0 & 1;
     if (c->pol.exploit > 0) {                   // sizes of this round depend on L so far
         Globals h;
