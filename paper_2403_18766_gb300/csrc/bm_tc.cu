@@ -18,6 +18,7 @@
 // The objective is the exact sum of the per-row distances (integer fixed
 // point), rounded once.
 #include <algorithm>
+#include <mutex>
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -531,10 +532,22 @@ cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* 
     const size_t smem = std::max<size_t>(tc_smem_bytes(k, Npad), 80 * 1024);
     cudaError_t e = allow_max_smem((const void*)tc_fullpass_kernel);
     if (e != cudaSuccess) return e;
+    // the tiles arrive by bulk copy into shared memory, so the whole carveout
+    // goes to shared memory (else only one CTA of this size fits per SM)
+    static std::once_flag carve;
+    std::call_once(carve, [] {
+        cudaFuncSetAttribute((const void*)tc_fullpass_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    });
+    // Two CTAs per SM: the shared memory of two fits (ncu: shared-memory
+    // limit 2, register limit 8) and two allocations take all 512 tensor-
+    // memory columns.  The occupancy query is not used for this count: it
+    // answered 1 here although both fit.  Were a second CTA not resident, it
+    // would run after the first (no wait between them).
     int per_sm = 0;
     e = blocks_per_sm((const void*)tc_fullpass_kernel, kTcThreads, smem, &per_sm);
     if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, 512 / kTcTmemCols));     // tensor-memory columns per SM
+    per_sm = 512 / kTcTmemCols;
     const long long tiles = (m + kTcRows - 1) / kTcRows;
     const long long grid = std::max<long long>(1, std::min<long long>((long long)sms * per_sm, tiles));
     tc_fullpass_kernel<<<(unsigned)grid, kTcThreads, smem, st>>>((const __nv_bfloat16*)Xb, xnorm, Xf, m, n, C, k,
