@@ -92,7 +92,7 @@ typedef struct {
     int32_t exploit;   /* 0..100: percent chance that a worker's size for a
                           round is the rounded mean of L accumulated before
                           the round (exploiting the current best size, the
-                          paper's future work, Sec. 6); 0 = the paper.
+                          paper's future work, Sec. 7); 0 = the paper.
                           Nonzero values read L back to the host once per
                           round and draw no samples ahead                  */
 } bm_sample_policy;
@@ -299,7 +299,11 @@ bm_status bm_assign_bf16_certified(const void* Xb_dev, const float* norms_dev, c
  *     report is omitted.
  *   - The first call on each device looks up the scratch's device address
  *     (with that device current); make that first call before any stream
- *     capture.
+ *     capture begins.  Every call waits for its work to finish and reads
+ *     f(C, X) back to the host before it returns.
+ *   - Errors: the statuses of bm_assign for the same failures (the device
+ *     flags are mapped by the same function), plus BM_EINVAL for the size
+ *     limit above.
  *   - All calls share the one scratch array and each call clears its
  *     accumulators first, so calls that overlap on the GPU (different
  *     streams or threads without ordering) race: order them, e.g. issue them
@@ -441,7 +445,11 @@ bm_status bm_wait(bm_ctx* ctx, bm_job_id id, double timeout_s, bm_result* result
 /* The error message of a failed job (empty if none), NUL-terminated. */
 bm_status bm_job_error(bm_ctx* ctx, bm_job_id id, char* buf, int64_t len);
 bm_status bm_ctx_stats(bm_ctx* ctx, bm_ctx_info* stats_out);
-/* Drops queued jobs, waits for running ones, frees the context. */
+/* Drops queued jobs (each is reported done with status BM_EINVAL and the
+ * message "dropped: ..."), waits for running ones, wakes every thread blocked
+ * in bm_wait on this context and waits until they have returned, then frees
+ * the context.  No other call on the context may start once bm_ctx_destroy
+ * has been called (the context is freed when it returns). */
 void bm_ctx_destroy(bm_ctx* ctx);
 
 /* ---------------------------------------------------------------------------
@@ -453,6 +461,27 @@ void bm_ctx_destroy(bm_ctx* ctx);
  * the library has used.  (bm_assign_noalloc uses no pool memory.)
  * ------------------------------------------------------------------------- */
 bm_status bm_trim_memory(void);
+
+/* ---------------------------------------------------------------------------
+ * Failure-injection hooks for tests (the paper has no counterpart: they check
+ * the library's own failure handling without faulting a GPU).
+ * bm_debug_fail_allocs: the next `count` device allocations of the library
+ *   (workspaces and the device copies of host buffers) fail as if the device
+ *   were out of memory, so the calls that make them return BM_ENOMEM and
+ *   release what they had taken.  0 turns it off; count < 0 is BM_EINVAL.
+ * bm_debug_set_wait_limit: limit of every bounded wait of the tensor-core
+ *   exact full pass (bm_set_fullpass_impl, impl 2) launched afterwards:
+ *   `polls` polls of an mbarrier, each suspending for at most `sleep_ns`
+ *   (0: plain polls).  A wait that runs out sets the timeout flag; every role
+ *   of the CTA stops, the copies and MMAs still in flight are waited for,
+ *   tensor memory is freed, and the call returns BM_ETIMEOUT with the
+ *   context still usable.  polls = 0 restores the default (2^18 polls of at
+ *   most 20 us); sleep_ns above 1e6 is BM_EINVAL.
+ * Both settings are process-wide; change them only while no call of this
+ * library is running.
+ * ------------------------------------------------------------------------- */
+bm_status bm_debug_fail_allocs(int32_t count);
+bm_status bm_debug_set_wait_limit(uint32_t polls, uint32_t sleep_ns);
 
 /* Thread-local message for the last non-OK status of this thread. */
 const char* bm_last_error(void);

@@ -44,8 +44,9 @@ def draw_size(seed, worker, rnd, policy, L_sum=0, L_len=0):
     """s_w for (worker, round), from the size stream (SIZE, worker, round, 0).
 
     The paper (Alg. 1): a uniform integer in [s_min, s_max], or uniform over
-    a configured set.  The future-work variants (Sec. 6, "other ways to
-    explore the range and exploit the currently best size"):
+    a configured set.  The future-work variants (Sec. 7 proposes trying
+    further ways of exploring the size range and of reusing the best size
+    found so far):
       kind 1  - octave-uniform: octave i uniform in [0, O) with O the least
                 t >= 1 with s_min * 2^t >= s_max (O = 1 when s_min = s_max),
                 then uniform inside [s_min 2^i, s_min 2^(i+1) - 1]; the last

@@ -50,6 +50,7 @@ void set_fullpass_impl(int impl);
 int last_fullpass_impl();
 int fullpass_impl_setting();
 bool tcx_eligible(const float* X, long long m, int n, int np, int k);
+void set_tcx_wait_limit(unsigned polls, unsigned ns);
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
                                const float* C, int k, float tau, int certify, int* labels, int* queue, Globals* g,
                                float gB, float gp2, int sms, cudaStream_t st);
@@ -135,7 +136,13 @@ cudaError_t lib_pool(cudaMemPool_t* out) {
     return cudaSuccess;
 }
 
+// Test hook (bm_debug_fail_allocs): the next N device allocations of the
+// library fail as if the device were out of memory.
+std::atomic<int> g_fail_allocs{0};
+
 cudaError_t lib_alloc(void** p, size_t bytes, cudaStream_t st) {
+    for (int left = g_fail_allocs.load(); left > 0;)
+        if (g_fail_allocs.compare_exchange_weak(left, left - 1)) return cudaErrorMemoryAllocation;
     cudaMemPool_t pool = nullptr;
     const cudaError_t e = lib_pool(&pool);
     if (e != cudaSuccess) return e;
@@ -472,6 +479,11 @@ void fill_report(const bm_fit_ctx* c, const Globals& h, bm_report* rep) {
     rep->t_sample_s = c->t_sample;
 }
 
+}  // namespace
+
+namespace bm {
+// Status of a call from the device flags it left in its Globals record (also
+// used by bm_assign_noalloc, so that both entry points report a failure alike).
 bm_status status_from_flags(const Globals& h) {
     if (h.nonfinite) return fail(BM_EINVAL, "X contains %u non-finite values", h.nonfinite);
     if (h.maxbits >= 0x7e800000u)
@@ -483,6 +495,9 @@ bm_status status_from_flags(const Globals& h) {
     if (h.err) return fail(BM_EINTERNAL, "device error flags 0x%x", h.err);
     return BM_OK;
 }
+}  // namespace bm
+
+namespace {
 
 long long size_of(const bm_fit_ctx* c, int w, int t) {
     return policy_size(size_policy(c), c->seed, stream_k1(kPurposeSize, w, t, 0));
@@ -616,6 +631,18 @@ bm_status bm_set_fullpass_impl(int32_t impl) {
     return BM_OK;
 }
 int32_t bm_last_fullpass_impl(void) { return last_fullpass_impl(); }
+
+bm_status bm_debug_fail_allocs(int32_t count) {
+    if (count < 0) return fail(BM_EINVAL, "count = %d must be >= 0", count);
+    g_fail_allocs.store(count);
+    return BM_OK;
+}
+
+bm_status bm_debug_set_wait_limit(uint32_t polls, uint32_t sleep_ns) {
+    if (sleep_ns > 1000000u) return fail(BM_EINVAL, "sleep_ns = %u above 1e6", sleep_ns);
+    set_tcx_wait_limit(polls, sleep_ns);
+    return BM_OK;
+}
 const char* bm_version(void) { return "bigmeans-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -26,6 +26,7 @@ cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const fl
                             int incumbent, int grid, cudaStream_t st);
 cudaError_t launch_prepass(const float* v, long long count, Globals* g, int grid, cudaStream_t st);
 cudaError_t launch_pad(const float* src, long long rows, int n, int np, float* dst, cudaStream_t st);
+bm_status status_from_flags(const Globals& h);
 }  // namespace bm
 
 namespace {
@@ -112,9 +113,8 @@ extern "C" bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n,
     if ((e = cudaMemcpyAsync(&h, g, sizeof h, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
         return err(BM_ECUDA, "full pass: %s", cudaGetErrorString(e));
-    if (h.nonfinite) return err(BM_EINVAL, "X or C contains %u non-finite values", h.nonfinite);
-    if (h.maxbits >= 0x7e800000u) return err(BM_EINVAL, "max |x| must be below 2^126");
-    if (h.err) return err(BM_EINTERNAL, "device error flags 0x%x", h.err);
+    const bm_status fs = bm::status_from_flags(h);      // the same statuses as bm_assign
+    if (fs != BM_OK) return fs;
     if (f_out_host) *f_out_host = h.f_full;
     return BM_OK;
 }

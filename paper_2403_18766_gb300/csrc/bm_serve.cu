@@ -68,6 +68,7 @@ struct bm_ctx {
     int64_t in_use = 0, peak_in_use = 0;
     int active = 0, peak_active = 0;
     int64_t done_count = 0;
+    int waiters = 0;                     // threads inside bm_wait
     bool stop = false;
 
     // First fit in arrival order; a job passed over 4 times blocks later
@@ -214,10 +215,13 @@ bm_status bm_wait(bm_ctx* c, bm_job_id id, double timeout_s, bm_result* r) {
     if (it == c->jobs.end()) return BM_EINVAL;
     Job* j = it->second.get();
     const auto pred = [&] { return j->state == 2; };
+    c->waiters++;
     if (timeout_s < 0) c->done_cv.wait(lk, pred);
     else c->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), pred);
     fill_result(*j, r);
-    return (j->state == 2) ? BM_OK : BM_EAGAIN;
+    const bm_status st = (j->state == 2) ? BM_OK : BM_EAGAIN;
+    if (--c->waiters == 0) c->done_cv.notify_all();      // bm_ctx_destroy may be waiting for this
+    return st;
 }
 
 bm_status bm_job_error(bm_ctx* c, bm_job_id id, char* buf, int64_t len) {
@@ -252,10 +256,24 @@ void bm_ctx_destroy(bm_ctx* c) {
     {
         std::lock_guard<std::mutex> lk(c->mu);
         c->stop = true;
-        c->queue.clear();                                     // queued jobs are dropped
+        for (Job* j : c->queue) {                             // queued jobs are dropped:
+            j->state = 2;                                     // reported as done, with an error
+            j->status = BM_EINVAL;
+            j->error = "dropped: the serving context was destroyed before the job was admitted";
+            j->t_done = now_s(c->t0);
+        }
+        c->queue.clear();
     }
     c->cv.notify_all();
+    c->done_cv.notify_all();
     for (auto& t : c->runners) t.join();                      // running jobs finish
+    {
+        // threads blocked in bm_wait return (every job is done now) before
+        // the context goes away
+        std::unique_lock<std::mutex> lk(c->mu);
+        c->done_cv.notify_all();
+        c->done_cv.wait(lk, [&] { return c->waiters == 0; });
+    }
     delete c;
 }
 

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "bm_device.cuh"
+#include "bm_tcgen05.cuh"
 
 namespace bm {
 
@@ -68,79 +69,24 @@ __global__ void pack_bf16_kernel(const float* __restrict__ X, long long m, int n
     if (mx) atomicMax(reinterpret_cast<unsigned int*>(norms + m_pad), mx);
 }
 
-// ------------------------------------------------------- PTX wrappers
-__device__ __forceinline__ unsigned s_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// ------------------------------------------------------- PTX helpers
+// The wrappers of bm_tcgen05.cuh, plus this kernel's bounded wait: after
+// 2^24 polls it sets the timeout flag and the caller carries on (the call
+// then reports BM_ETIMEOUT).
+using tc::s_addr;
 
-__device__ __forceinline__ void tc_mbar_init(unsigned long long* b, unsigned cnt) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(cnt) : "memory");
-}
-__device__ __forceinline__ void tc_expect_tx(unsigned long long* b, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void tc_bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     s_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(s_addr(b))
-                 : "memory");
-}
-__device__ __forceinline__ bool tc_try_wait(unsigned long long* b, unsigned parity) {
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok)
-                 : "r"(s_addr(b)), "r"(parity)
-                 : "memory");
-    return ok != 0;
-}
-// Bounded wait; on timeout the error flag is set and the caller carries on.
 __device__ __forceinline__ bool tc_wait(unsigned long long* b, unsigned parity, Globals* g) {
     for (unsigned i = 0; i < (1u << 24); ++i)
-        if (tc_try_wait(b, parity)) return true;
+        if (tc::try_wait(b, parity)) return true;
     atomicOr(&g->err, kErrTimeout);
     return false;
 }
 
-// 64-bit shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
-// groups 1024 bytes apart, descriptor version 1.
-__device__ __forceinline__ unsigned long long smem_desc_sw128(unsigned addr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((addr >> 4) & 0x3FFFu);          // start address
-    d |= (unsigned long long)1u << 16;                          // leading byte offset (unused here)
-    d |= (unsigned long long)(1024u >> 4) << 32;                // stride byte offset
-    d |= (unsigned long long)1u << 46;                          // version
-    d |= (unsigned long long)2u << 61;                          // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
-// K-major, N and M as given.
-__host__ __device__ constexpr unsigned idesc_bf16_f32(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long adesc, unsigned long long bdesc,
-                                       unsigned idesc, unsigned accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void tc_commit(unsigned long long* b) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(b))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 16 columns of 32-bit tensor-memory cells -> 16 registers per thread.
+// 32 lanes x 16 columns of 32-bit tensor-memory cells -> 16 floats per thread.
 __device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
     unsigned r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tc::ld16(taddr, r);
+    tc::wait_ld();
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
@@ -170,16 +116,11 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
     if (g->nonfinite) return;
 
     // tensor memory: warp 0 allocates and later frees
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
-                     "r"(kTcTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTcTmemCols);
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) tc_mbar_init(&bar_x[s], 1);
-        tc_mbar_init(&bar_mma, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int s = 0; s < kTcStages; ++s) tc::mbar_init(&bar_x[s], 1);
+        tc::mbar_init(&bar_mma, 1);
+        tc::mbar_init_fence();
     }
     // centroids: BF16 B operand (swizzled) and ||c_bf16||^2
     for (int e = tid; e < Npad * (kTcK / 8); e += kTcThreads) {
@@ -222,10 +163,10 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
             cert.cmax = __fsqrt_ru(cert.cmax2);
         }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B visible to the tensor core
-    tc_fence_before();
+    tc::fence_proxy_async();                                   // B visible to the tensor core
+    tc::fence_before();
     __syncthreads();
-    tc_fence_after();
+    tc::fence_after();
     const unsigned tmem = tmem_slot;
 
     const long long ntiles = (m + kTcRows - 1) / kTcRows;
@@ -235,11 +176,11 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
         for (int s = 0; s < kTcStages; ++s) {
             const long long t = blockIdx.x + (long long)s * grid;
             if (t < ntiles) {
-                tc_expect_tx(&bar_x[s], tile_bytes);
-                tc_bulk_g2s(xs + (size_t)s * tile_bytes, Xb + t * kTcRows * kTcK, tile_bytes, &bar_x[s]);
+                tc::expect_tx(&bar_x[s], tile_bytes);
+                tc::bulk_g2s(xs + (size_t)s * tile_bytes, Xb + t * kTcRows * kTcK, tile_bytes, &bar_x[s]);
             }
         }
-    const unsigned idesc = idesc_bf16_f32(kTcRows, Npad);
+    const unsigned idesc = tc::idesc_bf16(kTcRows, Npad);
     const long long m_pad = (m + kTcRows - 1) / kTcRows * kTcRows;
     const Grids gr = grids_from_maxbits(max(g->maxbits, __float_as_uint(xnorm[m_pad])));
     unsigned __int128 facc = 0;
@@ -251,16 +192,16 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
         const int st = (int)(it % kTcStages);
         if (tid == 0) {
             ok &= tc_wait(&bar_x[st], (unsigned)((it / kTcStages) & 1), g);
-            tc_fence_after();
+            tc::fence_after();
             const unsigned a0 = s_addr(xs + (size_t)st * tile_bytes), b0 = s_addr(bs);
 #pragma unroll
             for (int kk = 0; kk < kTcK / 16; ++kk)
-                tc_mma(tmem, smem_desc_sw128(a0 + 32 * kk), smem_desc_sw128(b0 + 32 * kk), idesc, kk > 0);
-            tc_commit(&bar_mma);
+                tc::mma_bf16(tmem, tc::desc_sw128(a0 + 32 * kk), tc::desc_sw128(b0 + 32 * kk), idesc, kk > 0);
+            tc::commit(&bar_mma);
         }
         // every thread waits for the accumulator of this tile
         ok &= tc_wait(&bar_mma, (unsigned)(it & 1), g);
-        tc_fence_after();
+        tc::fence_after();
         const long long row = tile * kTcRows + warp * 32 + lane;
         const float xx = row < m ? xnorm[row] : 0.f;
         float g1 = __int_as_float(0x7f800000), g2 = g1;
@@ -276,13 +217,13 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
                 g1 = fminf(g1, e);
             }
         }
-        tc_fence_before();
+        tc::fence_before();
         __syncthreads();                    // accumulator read, X stage consumed
         if (tid == 0) {
             const long long nt = tile + (long long)kTcStages * grid;
             if (nt < ntiles) {
-                tc_expect_tx(&bar_x[st], tile_bytes);
-                tc_bulk_g2s(xs + (size_t)st * tile_bytes, Xb + nt * kTcRows * kTcK, tile_bytes, &bar_x[st]);
+                tc::expect_tx(&bar_x[st], tile_bytes);
+                tc::bulk_g2s(xs + (size_t)st * tile_bytes, Xb + nt * kTcRows * kTcK, tile_bytes, &bar_x[st]);
             }
         }
         // Close calls go to a queue re-scored by rescore_kernel with the
@@ -311,11 +252,11 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
         }
     }
     // free tensor memory (every MMA of this CTA completed before its last wait)
-    tc_fence_before();
+    tc::fence_before();
     __syncthreads();
     if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, kTcTmemCols);
     }
     // objective: CTA reduction, then the grid-wide total (last CTA rounds it)
     unsigned __int128 F = warp_sum_u128(facc);

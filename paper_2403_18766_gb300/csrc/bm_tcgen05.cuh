@@ -42,12 +42,20 @@ __device__ __forceinline__ bool try_wait_sleep(unsigned long long* b, unsigned p
         : "memory");
     return ok != 0;
 }
+// Limits of the bounded waits: `polls` polls, each suspending the thread for
+// at most `ns` nanoseconds (0: a plain poll).  The default, 2^18 polls of at
+// most 20 us, ends a wait after about 5 s; bm_debug_set_wait_limit sets
+// smaller values for a test that makes a wait run out.
+struct WaitLimit { unsigned polls, ns; };
+constexpr WaitLimit kDefaultWait = {1u << 18, 20000u};
+
 // Bounded wait.  Gives up when `abort` is raised by another role of the CTA,
-// or after 2^18 polls of at most 20 us each (then it raises `abort` and the
-// timeout flag), so that no role of a CTA can wait forever on another.
-__device__ __forceinline__ bool wait(unsigned long long* b, unsigned parity, volatile int* abort, Globals* g) {
-    for (unsigned i = 0; i < (1u << 18); ++i) {
-        if (try_wait_sleep(b, parity, 20000u)) return true;
+// or once the limit is spent (then it raises `abort` and the timeout flag),
+// so that no role of a CTA can wait forever on another.
+__device__ __forceinline__ bool wait(unsigned long long* b, unsigned parity, volatile int* abort, Globals* g,
+                                     WaitLimit lim) {
+    for (unsigned i = 0; i < lim.polls; ++i) {
+        if (lim.ns ? try_wait_sleep(b, parity, lim.ns) : try_wait(b, parity)) return true;
         if (*abort) return false;
     }
     *abort = 1;

@@ -43,6 +43,7 @@
 // accumulator b and its own hi(x) / r(x) tiles, so the MMA of one tile
 // overlaps the epilogues of the others.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <mutex>
 
@@ -71,6 +72,7 @@ struct TxShape {
     int groups;      // epilogue warpgroups (= accumulators = r(x) buffers)
     int inplace;     // 1: hi(x) written over the stage, which is held until the
                      //    group's epilogue ends; 0: hi(x) in a group buffer
+    tc::WaitLimit wait;  // limit of every bounded wait
 };
 
 // Shared memory (1024-byte aligned pieces):
@@ -209,6 +211,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
 
     unsigned __int128 facc = 0;
     unsigned int inex = 0, resc = 0;
+    long long issued = 0;             // producer: copies issued; MMA warp: tiles committed
     if (warp == kProducer) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
@@ -218,16 +221,14 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             for (;; ++it) {
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
-                if (it >= S && !tc::wait(&empty[s], ph ^ 1u, abort, g)) break;
+                if (it >= S && !tc::wait(&empty[s], ph ^ 1u, abort, g, sh.wait)) break;
                 tc::expect_tx(&full[s], (unsigned)tile_bytes);
                 for (int a = 0; a < sh.atoms; ++a)
                     tc::tma_load_2d(xs + (size_t)s * tile_bytes + (size_t)a * kTxAtomBytes, &tmap, 32 * a,
                                     (int)(tile * kTxRows), &full[s]);
                 if (++s == S) { s = 0; ph ^= 1u; }
             }
-            if (*abort)       // drain the copies still in flight before the CTA exits
-                for (long long i = (it > S ? it - S : 0); i < it; ++i)
-                    for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&full[i % S], (unsigned)((i / S) & 1)); ++p) {}
+            issued = it;
         }
     } else if (warp == kMma) {
         // --------------------------------------------------------------- MMA
@@ -240,7 +241,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 const long long tile = blockIdx.x + it * grid;
                 if (tile >= ntiles) break;
                 const int b = (int)(it % NG);
-                if (!tc::wait(&conv[b], (unsigned)((it / NG) & 1), abort, g)) break;
+                if (!tc::wait(&conv[b], (unsigned)((it / NG) & 1), abort, g, sh.wait)) break;
                 tc::fence_after();
                 const unsigned ax = tc::s_addr(sh.inplace ? xs + (size_t)s * tile_bytes
                                                           : xh + (size_t)b * tile_bytes);
@@ -263,9 +264,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
                 }
                 tc::commit(&accf[b]);
             }
-            if (*abort && it > 0)     // the last commit covers every MMA issued
-                for (unsigned p = 0;
-                     p < (1u << 22) && !tc::try_wait(&accf[(it - 1) % NG], (unsigned)(((it - 1) / NG) & 1)); ++p) {}
+            issued = it;
         }
     } else {
         // --------------------------------------------------- epilogue groups
@@ -285,7 +284,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             // 1. the row: hi(x) and r(x) into this group's buffers; the stage
             //    is free again as soon as every warp of the group has read it
             int ok = 1;
-            if (lane == 0) ok = tc::wait(&full[s], ph, abort, g);
+            if (lane == 0) ok = tc::wait(&full[s], ph, abort, g, sh.wait);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             float xn2 = 0.f;
@@ -309,7 +308,7 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
             }
             const float xn = __fsqrt_ru(xn2);
             // 2. the accumulator of this tile
-            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it / NG) & 1), abort, g);
+            if (lane == 0) ok = tc::wait(&accf[b], (unsigned)((it / NG) & 1), abort, g, sh.wait);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc::fence_after();
@@ -426,9 +425,26 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
         }
     }
 
-    // teardown: every MMA has completed (consumed, or drained on abort)
+    // teardown.  Without an abort every copy and every MMA was consumed by a
+    // wait of the epilogue.  After an abort (a bounded wait ran out), once
+    // every role has stopped (the barrier below; the flag is final then),
+    // the producer waits for its copies still in flight (only the last S can
+    // be: each earlier stage was released by the epilogue after its copy
+    // landed) and the MMA thread for its last commit, which covers every MMA
+    // it issued, so that nothing writes this CTA's shared or tensor memory
+    // after it is released.
     tc::fence_before();
     __syncthreads();
+    if (*abort) {
+        if (warp == kProducer && lane == 0)
+            for (long long i = (issued > S ? issued - S : 0); i < issued; ++i)
+                for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&full[i % S], (unsigned)((i / S) & 1)); ++p) {}
+        if (warp == kMma && lane == 0 && issued > 0)
+            for (unsigned p = 0;
+                 p < (1u << 22) && !tc::try_wait(&accf[(issued - 1) % NG], (unsigned)(((issued - 1) / NG) & 1));
+                 ++p) {}
+        __syncthreads();
+    }
     if (warp == kMma) {
         tc::fence_after();
         tc::tmem_dealloc(tmem, (unsigned)sh.tmem_cols);
@@ -570,12 +586,20 @@ float tcx_gamma(int np) {
     return 2.0f * (float)(ksteps * 9) * 0x1p-23f + 8.0f * 0x1p-20f;
 }
 
+// Limits of the bounded waits of the next launches (process-wide).
+static std::atomic<unsigned> g_wait_polls{tc::kDefaultWait.polls}, g_wait_ns{tc::kDefaultWait.ns};
+void set_tcx_wait_limit(unsigned polls, unsigned ns) {
+    g_wait_polls.store(polls ? polls : tc::kDefaultWait.polls);
+    g_wait_ns.store(polls ? ns : tc::kDefaultWait.ns);
+}
+
 // Launch the tensor-core exact pass; cudaErrorNotSupported when not eligible.
 cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                                 const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                                 int incumbent, int sms, cudaStream_t st) {
     TxShape sh;
     if (!tcx_eligible(X, m, n, np, k) || !tx_shape(np, k, sh)) return cudaErrorNotSupported;
+    sh.wait = {g_wait_polls.load(), g_wait_ns.load()};
     CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
     const cuuint64_t strides[1] = {(cuuint64_t)n * 4};

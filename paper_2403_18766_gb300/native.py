@@ -108,6 +108,8 @@ SIGNATURES = {
     "bm_assign_bf16_certified": (_i32, [_p, _p, _p, _i64, _i32, _p, _i32, ctypes.c_float, _p,
                               ctypes.POINTER(_dbl), _RP, _p]),
     "bm_set_fullpass_impl": (_i32, [_i32]),
+    "bm_debug_fail_allocs": (_i32, [_i32]),
+    "bm_debug_set_wait_limit": (_i32, [ctypes.c_uint32, ctypes.c_uint32]),
     "bm_last_fullpass_impl": (_i32, []),
     "bm_fit_footprint": (_i32, [_i64, _i32, _i32, _PP, _BP, ctypes.POINTER(_i64)]),
     "bm_set_rows_per_cta": (_i32, [_i32]),
@@ -462,6 +464,16 @@ def set_sampler_impl(impl):
 
 def get_sampler_impl():
     return int(lib.bm_get_sampler_impl())
+
+
+def debug_fail_allocs(count):
+    """bm_debug_fail_allocs: the next `count` device allocations of the library fail (test hook)."""
+    _check(lib.bm_debug_fail_allocs(int(count)))
+
+
+def debug_set_wait_limit(polls, sleep_ns=0):
+    """bm_debug_set_wait_limit: bounded-wait limit of the tensor-core exact pass (0 = default; test hook)."""
+    _check(lib.bm_debug_set_wait_limit(int(polls), int(sleep_ns)))
 
 
 def trim_memory():

@@ -3,12 +3,14 @@
 * the packed rows are torch's round-to-nearest bfloat16 of X, in the
   documented swizzled layout, and the norms are fl(sum bf16(x)^2);
 * tau = inf re-scores every row with the exact FP32 definition, so labels and
-  f equal bm_assign bit for bit (checks the bookkeeping of the kernel);
+  f equal bm_assign and the CPU oracle bit for bit (checks the bookkeeping of
+  the kernel);
 * tau = 0 takes every label from the tensor cores: they must equal the argmin
   of a bfloat16 / FP32-accumulate reference except where two centroids are
   within the accumulation error (checks descriptors, swizzle, TMEM reads);
 * the default tau = 1e-3 agrees with the exact pass on all but near ties and
-  reports how far its objective is from the exact one.
+  reports how far its objective is from the exact one;
+* the certified variant's labels equal the oracle's exact-mode labels.
 """
 import math
 
@@ -30,6 +32,17 @@ def _case(m, n, k, seed, components=None):
     X = gaussian_mixture(m, n, components or max(2, k // 2), seed=seed)
     C = X[np.random.default_rng(seed).integers(0, m, k)].copy()
     return torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+
+
+_ORACLE = {}
+
+
+def _oracle(X, C, key):
+    """Exact-mode labels and f(C, X) from the CPU oracle (Eq. 1), cached per case."""
+    if key not in _ORACLE:
+        lab, dist = okm.assign(X.cpu().numpy(), C.cpu().numpy())
+        _ORACLE[key] = (lab, okm.exact_sum(dist))
+    return _ORACLE[key]
 
 
 def _unswizzle(Xb_bytes, m):
@@ -72,6 +85,8 @@ def test_tau_inf_is_the_exact_pass(m, n, k):
     assert torch.equal(Y, Yr)
     assert f == fr
     assert rep["rescored_rows"] == m
+    lab, fo = _oracle(X, C, (m, n, k, 7 * m + k))
+    assert np.array_equal(Y.cpu().numpy(), lab) and f == fo
 
 
 @pytest.mark.parametrize("m,n,k", CASES)
@@ -99,6 +114,8 @@ def test_default_tau_matches_exact_labels_except_near_ties(m, n, k):
     P = native.PackedBF16(X)
     Y, f, rep = native.assign_bf16(P, C, tau=1e-3)
     Yr, fr, _ = native.assign(X, C)
+    lab, fo = _oracle(X, C, (m, n, k, 13 * m + k))
+    assert np.array_equal(Yr.cpu().numpy(), lab) and fr == fo
     mism = (Y != Yr).nonzero().flatten()
     assert mism.numel() <= max(3, m // 100)
     if mism.numel():
@@ -122,6 +139,9 @@ def test_certified_labels_equal_the_exact_pass(m, n, k, tau):
     Y, f, rep = native.assign_bf16(P, C, tau=tau, certified=True)
     Yr, fr, _ = native.assign(X, C)
     assert torch.equal(Y, Yr)
+    lab, fo = _oracle(X, C, (m, n, k, 17 * m + k))
+    assert np.array_equal(Y.cpu().numpy(), lab)
+    assert abs(f - fo) <= 5e-3 * fo
     _, _, rep_plain = native.assign_bf16(P, C, tau=tau)
     assert rep["rescored_rows"] >= rep_plain["rescored_rows"]
     assert abs(f - fr) <= 5e-3 * fr
@@ -139,4 +159,6 @@ def test_certified_near_ties_and_far_from_origin():
     Y, f, rep = native.assign_bf16(P, Cd, tau=0.0, certified=True)
     Yr, fr, _ = native.assign(Xd, Cd)
     assert torch.equal(Y, Yr)
+    lab, _ = okm.assign(X, C)
+    assert np.array_equal(Y.cpu().numpy(), lab)
     assert rep["rescored_rows"] > 0

@@ -1,7 +1,8 @@
 """GPU tests of the serving context (continuous batching).
 
 * every job's result (C bits, labels, f) is the same alone and in a mix of
-  concurrently running jobs, and the same as bigmeans_fit_host;
+  concurrently running jobs, the same as bigmeans_fit_host, and the same as
+  the CPU oracle's Algorithm 1 on that job;
 * admission keeps the device memory in use under the budget, runs jobs
   concurrently when they fit, and queues them when they do not;
 * a small job may overtake a large one that does not fit yet (first fit).
@@ -17,6 +18,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+from oracle import bigmeans as obm  # noqa: E402
 from paper_2403_18766_gb300 import native  # noqa: E402
 from paper_2403_18766_gb300.synthetic import gaussian_mixture  # noqa: E402
 
@@ -57,6 +59,14 @@ def test_results_alone_equal_results_in_the_mix():
     for a, b in zip(alone, mixed):
         _same(a, b)
     assert st["peak_active"] >= 2                      # jobs did overlap on the device
+    # jobs taken from the mix against the CPU oracle (Algorithm 1, exact mode)
+    for i in (0, 5):
+        m, n, k, lo, hi, W, p, T, seed = JOBS[i]
+        ref = obm.bigmeans(specs[i][0].numpy(), k, dict(s_min=lo, s_max=hi, workers=W, passes=p),
+                           dict(rounds=T, max_lloyd=300, tol=1e-4, kpp_candidates=3), seed)
+        assert np.array_equal(mixed[i]["C"].numpy().view(np.int32), ref["C"].view(np.int32))
+        assert np.array_equal(mixed[i]["labels"].numpy(), ref["labels"])
+        assert mixed[i]["f_full"] == ref["f_full"] and mixed[i]["s_opt"] == ref["s_opt"]
     # and the same as the plain host-buffer fit
     X, k, pol, bud, seed = specs[1]
     C, Y, rep = native.fit_host(X, k, pol, bud, seed=seed)

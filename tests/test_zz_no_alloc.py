@@ -26,13 +26,25 @@ def _case(m, n, k, seed):
     return torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
 
 
-def test_noalloc_matches_bm_assign_two_calls_in_a_row():
-    cases = [_case(100_003, 16, 25, 1), _case(40_000, 33, 40, 2)]
+@pytest.fixture(params=[0, 2], ids=["impl-by-shape", "impl-tensor-cores"])
+def fullpass_impl(request):
+    native.set_fullpass_impl(request.param)
+    yield request.param
+    native.set_fullpass_impl(0)
+
+
+def test_noalloc_matches_bm_assign_two_calls_in_a_row(fullpass_impl):
+    """By shape: n = 16, k = 25 and n = 33 take the FP32-ALU pass, n = 64,
+    k = 100 the tensor-core pass; with impl 2 every case with n % 4 == 0
+    takes the tensor-core pass through the same fixed scratch."""
+    cases = [_case(100_003, 16, 25, 1), _case(40_000, 33, 40, 2), _case(60_001, 64, 100, 3)]
+    expect_tc = {0: [False, False, True], 2: [True, False, True]}[fullpass_impl]
     for _ in range(2):                          # the scratch keeps the previous call's contents
-        for X, C in cases:
+        for (X, C), tc in zip(cases, expect_tc):
             Y_ref, f_ref, _ = native.assign(X, C)
             Y, f = native.assign_noalloc(X, C)
             torch.cuda.synchronize()
+            assert native.last_fullpass_impl() == (2 if tc else 1)
             assert torch.equal(Y, Y_ref)
             assert f == f_ref                  # exact objective: bit-identical doubles
 
