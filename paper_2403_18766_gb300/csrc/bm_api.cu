@@ -191,14 +191,22 @@ std::atomic<int> g_rows_per_cta{kRowsPerCta};
 std::atomic<int> g_big_tpb{0};
 std::atomic<int> g_sample_tables{0};
 
+// Most sample rows one worker CTA can take: kMaxRowsPerCta, and the label
+// buckets of a Lloyd run (4 bytes per row) must fit beside the worker's
+// shared memory.
+long long rows_cap(int np, int k) {
+    const long long room = ((long long)kSmemLimit - (long long)worker_smem(np, k)) / 4 - 16;
+    return std::max<long long>(0, std::min<long long>(kMaxRowsPerCta, room));
+}
+
 // CTAs per worker cluster: about rows_per_cta sample rows per CTA, at most
-// max_cs, and never more than kMaxRowsPerCta rows per CTA (0 = impossible).
-int cluster_size(long long s_cap, int max_cs, int rows_per_cta = 0) {
+// max_cs, and never more than `cap` rows per CTA (0 = impossible).
+int cluster_size(long long s_cap, int max_cs, int rows_per_cta, long long cap) {
     const long long rpc = rows_per_cta > 0 ? rows_per_cta : g_rows_per_cta.load();
     long long cs = std::max<long long>(1, (s_cap + rpc - 1) / rpc);
     cs = std::min<long long>(cs, max_cs);
-    while (cs < max_cs && (s_cap + cs - 1) / cs > kMaxRowsPerCta) ++cs;
-    if ((s_cap + cs - 1) / cs > kMaxRowsPerCta) return 0;
+    while (cs < max_cs && (s_cap + cs - 1) / cs > cap) ++cs;
+    if ((s_cap + cs - 1) / cs > cap) return 0;
     return (int)cs;
 }
 
@@ -572,7 +580,8 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         a.round_end = r1;
         a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
         a.worker_base = w;
-        a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta);
+        a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta, rows_cap(c->np, c->k));
+        a.rows_cta = (int)((smax + a.cs - 1) / a.cs);
         // clusters at the size cap with more rows per CTA than the tile get
         // 512-thread CTAs (one per SM) when the big-cluster option is on
         a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
@@ -694,10 +703,11 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
     c->s_lo = s_lo; c->s_hi = s_hi; c->s_cap = s_hi;
     c->max_cs = worker_max_cluster(c->np, k);
     c->rows_per_cta = g_rows_per_cta.load();
-    c->cs = cluster_size(s_hi, c->max_cs, c->rows_per_cta);
+    c->cs = cluster_size(s_hi, c->max_cs, c->rows_per_cta, rows_cap(c->np, k));
     if (c->cs == 0) {
+        const long long most = (long long)c->max_cs * rows_cap(c->np, k);
         delete c;
-        return fail(BM_EINVAL, "s_max = %lld above %lld", s_hi, (long long)c->max_cs * kMaxRowsPerCta);
+        return fail(BM_EINVAL, "s_max = %lld above %lld", s_hi, most);
     }
     c->Tcap = draw_cap(m, s_hi);
     if (c->Tcap >= (1ll << 32) - 1) { delete c; return fail(BM_EINVAL, "sample size too close to m"); }
@@ -972,9 +982,10 @@ static bm_status step_ctx(bm_fit_ctx* c, const float* X, long long m, int n, int
     c->seed = seed;
     c->s_lo = c->s_hi = c->s_cap = std::max<long long>(s_cap, 1);
     c->max_cs = worker_max_cluster(c->np, k);
-    c->cs = cluster_size(c->s_cap, c->max_cs);
+    c->cs = cluster_size(c->s_cap, c->max_cs, 0, rows_cap(c->np, k));
     if (c->cs == 0)
-        return fail(BM_EINVAL, "sample of %lld rows above %lld", c->s_cap, (long long)c->max_cs * kMaxRowsPerCta);
+        return fail(BM_EINVAL, "sample of %lld rows above %lld", c->s_cap,
+                    (long long)c->max_cs * rows_cap(c->np, k));
     c->Tcap = m > 0 ? draw_cap(m, std::min<long long>(c->s_cap, m)) : 1024;
     c->H = next_pow2(2 * c->Tcap);
     c->L_cap = 1;
@@ -1073,6 +1084,7 @@ bm_status bm_lloyd(const float* S_dev, int64_t s, int32_t n, float* C_inout_dev,
     CU(cudaMemsetAsync(c->deg, 0, k, c->st));
     WorkerArgs a = make_args(c, kModeStepLloyd);
     a.max_lloyd = max_iter; a.tol = tol; a.step_s = s;
+    a.rows_cta = (int)((s + c->cs - 1) / c->cs);
     a.step_f = c->f_final; a.step_iters = (int*)c->L_buf;
     a.step_empty = empty_out_dev ? empty_out_dev : c->deg;
     CU(launch_worker(c->np, a, 1, c->st));

@@ -2,10 +2,10 @@
 //
 // * Philox4x64-10 (Salmon et al., SC'11) and Lemire's bounded draw: the
 //   random stream contract of include/bigmeans.h.
-// * Exact sums in integer fixed point.  Coordinates are added as signed
-//   32-bit chunks into three int64 words (value = w0 + w1*2^32 + w2*2^64 in
-//   units of 2^gx); squared distances into an unsigned 128-bit accumulator in
-//   units of 2^gf.  Integer addition is associative, so the result does not
+// * Exact sums in integer fixed point.  Coordinates are converted to signed
+//   128-bit integers in units of 2^gx and summed in three int64 words
+//   (value = w0 + w1*2^32 + w2*2^64); squared distances into an unsigned
+//   128-bit accumulator in units of 2^gf.  Integer addition is associative, so the result does not
 //   depend on thread, block or cluster order; it is rounded to double once.
 // * The FP32 direct-form squared distance that defines labels (Eq. 1).
 #pragma once
@@ -40,7 +40,8 @@ struct Globals {
     // times, 5 longest worker kernel, 6 Lloyd assignments, 7 worker kernels,
     // 8 assignment main loop, 9 assignment block reductions, 10 first cluster
     // barrier, 11 owner update + objective, 12 second cluster barrier,
-    // 13 centroid pull + prep, 14-15 spare
+    // 13 centroid copy + prep, 14 first assignment of a Lloyd run (whole),
+    // 15 its labelling loop (the rest is the bucketed sums)
     unsigned long long trace[16];
     unsigned long long obj_words[4];   // full-pass objective, 32-bit chunks
     double f_full;                     // last full-pass objective
@@ -214,18 +215,14 @@ __device__ __forceinline__ void acc_obj(unsigned __int128& acc, float d, int gf,
     }
 }
 
-// Add a signed float to six int32 words of 16-bit chunks (unit 2^gx):
-// value = sum_i w[i] * 2^(16 i).  Native 32-bit shared-memory atomics; a word
-// absorbs up to 2^15 additions, so a CTA adds at most kMaxRowsPerCta rows
-// between flushes.  Returns false if the value exceeded the 96-bit range.
-constexpr int kDigits = 6;
+// A coordinate on the grid of the exact sums (unit 2^gx) as a signed 128-bit
+// integer.  Bits below the grid are truncated (counted in `inexact`); returns
+// false if |x| / 2^gx needs more than 96 bits (outside the grid's range; the
+// grid is set from the largest |x|, so data values never are).  Sums of such
+// integers are exact and independent of their order.
 constexpr long long kMaxRowsPerCta = 32767;
-// The digit chunks of x on grid gx: x = sign (c0 + c1 2^16 + c2 2^32) 2^(16 i + gx)
-// (signed chunks).  Returns false if x needs digits beyond kDigits; i = -1
-// when x contributes nothing.
-__device__ __forceinline__ bool digits_of(float x, int gx, unsigned int& inexact, int& i, int& c0, int& c1,
-                                          int& c2) {
-    i = -1; c0 = c1 = c2 = 0;
+__device__ __forceinline__ bool fixed_of(float x, int gx, unsigned int& inexact, __int128& v) {
+    v = 0;
     const uint32_t bits = __float_as_uint(x);
     const uint32_t mag = bits & 0x7fffffffu;
     if (mag == 0) return true;
@@ -240,23 +237,39 @@ __device__ __forceinline__ bool digits_of(float x, int gx, unsigned int& inexact
         sh = 0;
         if (!mant) return true;
     }
-    const int ii = sh >> 4, intra = sh & 15;
-    const uint64_t v = (uint64_t)mant << intra;                 // < 2^39
-    c0 = (int)(v & 0xffffu); c1 = (int)((v >> 16) & 0xffffu); c2 = (int)(v >> 32);
-    if (ii + (c2 ? 2 : (c1 ? 1 : 0)) >= kDigits) { c0 = c1 = c2 = 0; return false; }
-    if (bits >> 31) { c0 = -c0; c1 = -c1; c2 = -c2; }
-    i = ii;
+    if (sh + (32 - __clz((int)mant)) > 96) return false;
+    const unsigned __int128 u = (unsigned __int128)mant << sh;
+    v = (bits >> 31) ? -(__int128)u : (__int128)u;
     return true;
 }
 
-__device__ __forceinline__ bool acc_digits(int* w, float x, int gx, unsigned int& inexact) {
-    int i, c0, c1, c2;
-    const bool ok = digits_of(x, gx, inexact, i, c0, c1, c2);
-    if (i < 0) return ok;
-    if (c0) atomicAdd(&w[i], c0);
-    if (c1) atomicAdd(&w[i + 1], c1);
-    if (c2) atomicAdd(&w[i + 2], c2);
-    return ok;
+// The same integer in two signed parts, x / 2^gx = hi 2^48 + lo with
+// |hi|, |lo| < 2^48 (both with the sign of x): sums of up to 2^15 of them
+// stay exact in int64 registers.
+__device__ __forceinline__ bool fixed48_of(float x, int gx, unsigned int& inexact, long long& hi, long long& lo) {
+    hi = lo = 0;
+    const uint32_t bits = __float_as_uint(x);
+    const uint32_t mag = bits & 0x7fffffffu;
+    if (mag == 0) return true;
+    uint32_t mant; int e2;
+    f32_parts(mag, mant, e2);
+    int sh = e2 - gx;
+    if (sh < 0) {
+        const int r = -sh;
+        if (r >= 24) { inexact++; return true; }
+        if (mant & ((1u << r) - 1u)) inexact++;
+        mant >>= r;
+        sh = 0;
+        if (!mant) return true;
+    }
+    if (sh + (32 - __clz((int)mant)) > 96) return false;
+    const unsigned long long m = mant;
+    unsigned long long h, l;
+    if (sh >= 48) { h = m << (sh - 48); l = 0; }
+    else { l = (m << sh) & ((1ull << 48) - 1ull); h = sh ? (m >> (48 - sh)) : 0ull; }
+    hi = (bits >> 31) ? -(long long)h : (long long)h;
+    lo = (bits >> 31) ? -(long long)l : (long long)l;
+    return true;
 }
 
 // Correctly rounded double of a (signed) 128-bit integer times 2^g.

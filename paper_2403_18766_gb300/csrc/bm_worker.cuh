@@ -31,6 +31,8 @@ struct WorkerArgs {
     unsigned long long deadline_ns;   // %globaltimer deadline, 0 = none
     int mode;
     int cs;                           // CTAs per cluster
+    int rows_cta;                     // most sample rows of one CTA in a Lloyd run of this launch
+                                      // (sizes the label buckets in shared memory; 0: no Lloyd)
     int tpb;                          // threads per CTA: 256, or 512 (largest clusters)
     Globals* glob;
     // samples drawn by the sampling kernel: job (w, slot) = w * (P + 1) + slot
@@ -67,21 +69,38 @@ struct Xch {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Words per cluster in the shared accumulator: odd, so that lanes adding to
-// the same (dimension, digit) of different clusters fall in different banks.
-template <int NP>
-__host__ __device__ constexpr int acc_stride() { return NP * kDigits + 1; }
+// Objective partial of one CTA, pushed into rank 0's inbox (one slot per CTA).
+struct ObjPart {
+    unsigned long long f_lo, f_hi;     // 128-bit exact partial of the objective
+    unsigned long long inexact, rescored;
+};
+// Rank 0's decision, pushed to every CTA of the cluster.
+struct Decision {
+    double f;
+    int stop;
+    int pad_;
+};
+
+// Exact coordinate sums: three int64 words per (cluster, dimension), value =
+// w0 + w1 2^32 + w2 2^64 in units of 2^gx.  Each CTA holds the words of the
+// clusters it owns (j % cs == rank, slot j / cs); every CTA adds its rows'
+// contributions to the owner's words through distributed shared memory.
+constexpr int kAccWords = 3;
 
 template <int NP>
 __host__ __device__ inline size_t worker_smem_bytes(int k) {
     size_t b = 0;
     b += align16((size_t)k * NP * 4);           // Ccur
-    b += align16((size_t)k * NP * 4);           // Cnew
+    b += align16((size_t)k * NP * 4);           // Cnext (pushed by the owners)
     b += align16((size_t)k * 4);                // CC
-    b += align16((size_t)k * acc_stride<NP>() * 4);  // ACC
-    b += align16((size_t)k * 4);                // cnt
-    b += align16((size_t)k) * 3;                // deg, empty, emptyall
+    b += align16((size_t)k * NP * kAccWords * 8);  // OACC (owned slots; k of them when cs = 1)
+    b += align16((size_t)k * 4);                // ocnt (owned counts)
+    b += align16((size_t)k * 4);                // lcnt (this CTA's counts / bucket cursors)
+    b += align16((size_t)(k + 1) * 4);          // lstart (bucket starts)
+    b += align16((size_t)k) * 2;                // deg, emptyall
     b += align16(sizeof(Xch));
+    b += align16(sizeof(ObjPart) * kMaxCluster);   // inbox (rank 0)
+    b += align16(sizeof(Decision));
     b += align16(sizeof(unsigned __int128) * kMaxWarps);
     b += align16(8 * (kMaxWarps + 1));
     b += align16(4 * kMaxWarps);
@@ -89,6 +108,10 @@ __host__ __device__ inline size_t worker_smem_bytes(int k) {
     b += align16(8 * 16);
     return b;
 }
+
+// Shared memory of the label buckets of a Lloyd run: a 16-bit label and a
+// 16-bit row offset per sample row of the CTA.
+__host__ __device__ inline size_t bucket_smem_bytes(int rows_cta) { return align16((size_t)rows_cta * 4); }
 
 cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
 size_t worker_smem(int np, int k);

@@ -23,41 +23,51 @@ namespace bm {
 template <int NP>
 struct Sm {
     float* Ccur;          // k * NP  centroids of the current step
-    float* Cnew;          // k * NP  owner-computed updates
+    float* Cnext;         // k * NP  next centroids, pushed by their owners
     float* CC;            // k       fl(||c||^2) FMA chain
-    int* ACC;             // k * acc_stride fixed-point coordinate sums
-    int* cnt;             // k
+    long long* OACC;      // owned slots * NP * kAccWords: exact coordinate sums of owned clusters
+    int* ocnt;            // owned slots: member counts of owned clusters
+    int* lcnt;            // k: this CTA's member counts, then bucket cursors
+    int* lstart;          // k + 1: bucket starts of this CTA's rows sorted by label
     unsigned char* deg;   // k       worker's degenerate flags (identical copies)
-    unsigned char* empty; // k       owner-computed empties of the last assignment
-    unsigned char* emptyall;  // k   gathered empties
+    unsigned char* emptyall;  // k   empties of the last assignment, pushed by the owners
     Xch* x;
+    ObjPart* inbox;       // kMaxCluster: objective partials of every CTA (used on rank 0)
+    Decision* dec;        // rank 0's decision of the current step
     unsigned __int128* red128;    // one per warp (kMaxWarps)
     long long* red64;             // one per warp, + 1
     unsigned int* redu;           // one per warp
     CertC* cert;
     long long* bcast;             // broadcast slots: 0 f, 1 stop, 2 M/pick, 3 base,
                                   // 4 total, 5-7 candidates, 8 deadline flag
+    unsigned short* labs;         // rows_cta: label of each row of the CTA (first assignment)
+    unsigned short* rowlist;      // rows_cta: the CTA's row offsets sorted by label
 };
 
 template <int NP>
-__device__ inline Sm<NP> carve(int k) {
+__device__ inline Sm<NP> carve(int k, int rows_cta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* p = smem_raw;
     Sm<NP> s;
     s.Ccur = (float*)p;            p += align16((size_t)k * NP * 4);
-    s.Cnew = (float*)p;            p += align16((size_t)k * NP * 4);
+    s.Cnext = (float*)p;           p += align16((size_t)k * NP * 4);
     s.CC = (float*)p;              p += align16((size_t)k * 4);
-    s.ACC = (int*)p;               p += align16((size_t)k * acc_stride<NP>() * 4);
-    s.cnt = (int*)p;               p += align16((size_t)k * 4);
+    s.OACC = (long long*)p;        p += align16((size_t)k * NP * kAccWords * 8);
+    s.ocnt = (int*)p;              p += align16((size_t)k * 4);
+    s.lcnt = (int*)p;              p += align16((size_t)k * 4);
+    s.lstart = (int*)p;            p += align16((size_t)(k + 1) * 4);
     s.deg = p;                     p += align16((size_t)k);
-    s.empty = p;                   p += align16((size_t)k);
     s.emptyall = p;                p += align16((size_t)k);
     s.x = (Xch*)p;                 p += align16(sizeof(Xch));
+    s.inbox = (ObjPart*)p;         p += align16(sizeof(ObjPart) * kMaxCluster);
+    s.dec = (Decision*)p;          p += align16(sizeof(Decision));
     s.red128 = (unsigned __int128*)p; p += align16(sizeof(unsigned __int128) * kMaxWarps);
     s.red64 = (long long*)p;       p += align16(8 * (kMaxWarps + 1));
     s.redu = (unsigned int*)p;     p += align16(4 * kMaxWarps);
     s.cert = (CertC*)p;            p += align16(sizeof(CertC));
-    s.bcast = (long long*)p;
+    s.bcast = (long long*)p;       p += align16(8 * 16);
+    s.labs = (unsigned short*)p;
+    s.rowlist = s.labs + rows_cta;
     return s;
 }
 
@@ -83,7 +93,7 @@ struct Worker {
         w = a.worker_base + blockIdx.x / cs;
         k = a.k;
         n = a.n;
-        sm = carve<NP>(k);
+        sm = carve<NP>(k, a.rows_cta);
         g = grids_from_maxbits(a.glob->maxbits);
         S = a.S;
         D2 = a.D2 + (long long)w * a.D2_stride;
@@ -148,26 +158,165 @@ struct Worker {
         __syncthreads();
     }
 
+    // ------------------------------------------- exact sums at the owners
+    // Additions to another CTA's shared memory are fire-and-forget reductions
+    // (red, relaxed, cluster scope) on its shared::cluster address; the
+    // cluster barrier that follows orders them before the owner reads.
+    __device__ static unsigned cluster_addr(const void* local, int q) {
+        unsigned r;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(local)), "r"(q));
+        return r;
+    }
+    __device__ static void red_u64(unsigned addr, unsigned long long v) {
+        asm volatile("red.relaxed.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+    }
+    __device__ static void red_s32(unsigned addr, int v) {
+        asm volatile("red.relaxed.cluster.shared::cluster.add.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+    }
+    // Words of (cluster j, dimension d) in the owner CTA's shared memory.
+    __device__ unsigned owner_words(int j, int d) {
+        return cluster_addr(sm.OACC + ((size_t)(j / cs) * NP + d) * kAccWords, j % cs);
+    }
+    __device__ unsigned owner_count(int j) { return cluster_addr(sm.ocnt + j / cs, j % cs); }
+    // Add a signed 128-bit value to three int64 words (w0 + w1 2^32 + w2 2^64).
+    __device__ static void add_words(unsigned wd, __int128 v) {
+        if (v == 0) return;
+        const unsigned long long lo = (unsigned long long)v;
+        const unsigned long long w0 = lo & 0xffffffffull, w1 = lo >> 32;
+        const unsigned long long w2 = (unsigned long long)(long long)(v >> 64);
+        if (w0) red_u64(wd, w0);
+        if (w1) red_u64(wd + 8, w1);
+        if (w2) red_u64(wd + 16, w2);
+    }
+    // Move one row (held as m2x = -2 x) from cluster `from` (-1: none) to
+    // `to` at their owners, this lane alone.
+    __device__ bool move_row_lane(const float2 (&m2x)[NP / 2], int from, int to, unsigned int& inex) {
+        bool ok = true;
+        red_s32(owner_count(to), 1);
+        if (from >= 0) red_s32(owner_count(from), -1);
+#pragma unroll
+        for (int d = 0; d < NP; ++d) {
+            if (d < n) {
+                __int128 v;
+                ok &= fixed_of(-0.5f * ((d & 1) ? m2x[d >> 1].y : m2x[d >> 1].x), g.gx, inex, v);
+                add_words(owner_words(to, d), v);
+                if (from >= 0) add_words(owner_words(from, d), -v);
+            }
+        }
+        return ok;
+    }
+
+    // The CTA's rows of the first assignment of a Lloyd run, summed per
+    // cluster without per-element atomics: the rows are bucketed by label
+    // (counting sort of 16-bit row offsets in shared memory), each warp walks
+    // an equal share of the sorted rows with its lanes over (row, dimension),
+    // keeps the exact sum in registers (two int64 parts of 48-bit-aligned
+    // pieces) and adds it to the owner's words once per cluster it meets.
+    __device__ bool bucket_sums(long long lo, long long hi, unsigned int& inex) {
+        const int nrows = (int)(hi - lo);
+        __syncthreads();                                   // labs and lcnt complete
+        // counts to the owners; exclusive scan of the counts (warp 0)
+        for (int j = threadIdx.x; j < k; j += TPB)
+            if (sm.lcnt[j]) red_s32(owner_count(j), sm.lcnt[j]);
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int run = 0;
+            for (int j0 = 0; j0 < k; j0 += 32) {
+                const int j = j0 + lane;
+                const int c = j < k ? sm.lcnt[j] : 0;
+                int x = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (j < k) sm.lstart[j] = run + x - c;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) sm.lstart[k] = run;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < k; j += TPB) sm.lcnt[j] = sm.lstart[j];   // cursors
+        __syncthreads();
+        for (int i = threadIdx.x; i < nrows; i += TPB)
+            sm.rowlist[atomicAdd(&sm.lcnt[sm.labs[i]], 1)] = (unsigned short)i;
+        __syncthreads();
+        constexpr int LPR = NP < 32 ? NP : 32;             // lanes per row
+        constexpr int RPS = 32 / LPR;                      // rows per warp step
+        constexpr int DPL = NP / LPR;                      // dimensions per lane (2 for NP = 64)
+        constexpr int U = 4;                               // steps whose loads are issued together
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int sub = lane / LPR, d0 = lane % LPR;
+        const int b0 = (int)((long long)nrows * wid / (TPB / 32));
+        const int b1 = (int)((long long)nrows * (wid + 1) / (TPB / 32));
+        const float* Sl = S + lo * NP;
+        bool ok = true;
+        int j = 0;                                         // cluster of this lane's current row
+        int cur = -1;
+        long long shi[DPL], slo[DPL];
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) shi[t] = slo[t] = 0;
+        for (int p0 = b0 + sub; p0 < b1; p0 += U * RPS) {
+            float xv[U][DPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * RPS;
+                const int r = p < b1 ? sm.rowlist[p] : 0;
+#pragma unroll
+                for (int t = 0; t < DPL; ++t) {
+                    const int d = d0 + t * LPR;
+                    xv[u][t] = (p < b1 && d < n) ? Sl[(long long)r * NP + d] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int p = p0 + u * RPS;
+                if (p >= b1) break;
+                while (sm.lstart[j + 1] <= p) ++j;
+                if (j != cur) {
+                    if (cur >= 0)
+#pragma unroll
+                        for (int t = 0; t < DPL; ++t) {
+                            add_words(owner_words(cur, d0 + t * LPR),
+                                      ((__int128)shi[t] << 48) + (__int128)slo[t]);
+                            shi[t] = slo[t] = 0;
+                        }
+                    cur = j;
+                }
+#pragma unroll
+                for (int t = 0; t < DPL; ++t) {
+                    long long h, l;
+                    ok &= fixed48_of(xv[u][t], g.gx, inex, h, l);
+                    shi[t] += h;
+                    slo[t] += l;
+                }
+            }
+        }
+        if (cur >= 0)
+#pragma unroll
+            for (int t = 0; t < DPL; ++t)
+                add_words(owner_words(cur, d0 + t * LPR), ((__int128)shi[t] << 48) + (__int128)slo[t]);
+        return ok;
+    }
+
     // --------------------------------------------- a4/a5: assign + accumulate
-    // Assign the CTA's rows against Ccur and leave the CTA partial objective
-    // in sm.x.  mode 0: no sums (objective only); mode 1: first assignment of
-    // a Lloyd run, sums and counts rebuilt from zero; mode 2: incremental --
-    // the sums are exact integers, so only rows whose label changed since the
-    // previous assignment move from their old cluster to the new one.
+    // Assign the CTA's rows against Ccur and push the CTA partial objective to
+    // rank 0's inbox.  mode 0: no sums (objective only); mode 1: first
+    // assignment of a Lloyd run (the owners' sums start from zero, see
+    // lloyd); mode 2: incremental -- the sums are exact integers, so only rows
+    // whose label changed since the previous assignment move from their old
+    // cluster to the new one.
     __device__ void assign_slice(long long s, int mode) {
         constexpr int RT = RowsPerThread<NP>::v;
-        const bool acc = mode != 0;
         long long lo, hi;
         slice(s, lo, hi);
-        if (mode == 1) {
-            for (int e = threadIdx.x; e < k * acc_stride<NP>(); e += TPB) sm.ACC[e] = 0;
-            for (int e = threadIdx.x; e < k; e += TPB) sm.cnt[e] = 0;
-        }
+        if (mode == 1)
+            for (int e = threadIdx.x; e < k; e += TPB) sm.lcnt[e] = 0;
         __syncthreads();
         const long long t_loop = clock64();
         const CertC cc = *sm.cert;
         const float gB = a.gB, gp2 = a.gp2;
-        const int gx = g.gx, gf = g.gf;
+        const int gf = g.gf;
         unsigned __int128 facc = 0;
         unsigned int inex = 0, resc = 0;
         bool ok = true;
@@ -263,34 +412,24 @@ struct Worker {
                     }
                     acc_obj(facc, dv, gf, inex);
                 }
-                if (acc) {
+                if (mode == 1) {
+                    if (valid) {
+                        lab_prev[row] = lab;
+                        sm.labs[row - lo] = (unsigned short)lab;
+                        atomicAdd(&sm.lcnt[lab], 1);
+                    }
+                } else if (mode == 2) {
                     // Move rows whose label changed between clusters.  Many
-                    // movers (first assignment): each lane moves its own row.
-                    // Few movers (later iterations): the warp moves them one
-                    // at a time, lanes over dimensions, so the warp does not
-                    // walk the move path with one or two lanes active.
+                    // movers: each lane moves its own row.  Few movers (later
+                    // iterations): the warp moves them one at a time, lanes
+                    // over dimensions, so the warp does not walk the move path
+                    // with one or two lanes active.
                     const bool moved = valid && oldlab[r] != lab;
                     const unsigned mv = __ballot_sync(0xffffffffu, moved);
                     if (__popc(mv) > 8) {
                         if (moved) {
-                            // the row is in registers (x = -m2x / 2, exact): no
-                            // reload from the sample
-                            atomicAdd(&sm.cnt[lab], 1);
-                            int* wb = sm.ACC + (size_t)lab * acc_stride<NP>();
-#pragma unroll
-                            for (int d = 0; d < NP; ++d)
-                                if (d < n)
-                                    ok &= acc_digits(wb + d * kDigits,
-                                                     -0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x), gx, inex);
-                            if (oldlab[r] >= 0) {
-                                atomicSub(&sm.cnt[oldlab[r]], 1);
-                                int* wo = sm.ACC + (size_t)oldlab[r] * acc_stride<NP>();
-#pragma unroll
-                                for (int d = 0; d < NP; ++d)
-                                    if (d < n)
-                                        ok &= acc_digits(wo + d * kDigits,
-                                                         0.5f * ((d & 1) ? m2x[r][d >> 1].y : m2x[r][d >> 1].x), gx, inex);
-                            }
+                            // the row is in registers (x = -m2x / 2, exact)
+                            ok &= move_row_lane(m2x[r], oldlab[r], lab, inex);
                             lab_prev[row] = lab;
                         }
                     } else {
@@ -302,27 +441,31 @@ struct Worker {
                             const int snew = __shfl_sync(0xffffffffu, lab, src);
                             const int sold = __shfl_sync(0xffffffffu, oldlab[r], src);
                             if (lane == src) {
-                                atomicAdd(&sm.cnt[snew], 1);
-                                if (sold >= 0) atomicSub(&sm.cnt[sold], 1);
+                                red_s32(owner_count(snew), 1);
+                                red_s32(owner_count(sold), -1);
                                 lab_prev[srow] = snew;
                             }
                             const float* xr = S + srow * NP;
-                            int* wb = sm.ACC + (size_t)snew * acc_stride<NP>();
-                            int* wo = sm.ACC + (size_t)(sold >= 0 ? sold : 0) * acc_stride<NP>();
                             for (int d = lane; d < n; d += 32) {
-                                const float xv = xr[d];
-                                ok &= acc_digits(wb + d * kDigits, xv, gx, inex);
-                                if (sold >= 0) ok &= acc_digits(wo + d * kDigits, -xv, gx, inex);
+                                __int128 v;
+                                ok &= fixed_of(xr[d], g.gx, inex, v);
+                                add_words(owner_words(snew, d), v);
+                                add_words(owner_words(sold, d), -v);
                             }
                         }
                     }
                 }
             }
         }
+        if (mode == 1) {
+            if (tracer()) atomicAdd(&a.glob->trace[15], (unsigned long long)(clock64() - t_loop));
+            ok &= bucket_sums(lo, hi, inex);
+        }
         if (!ok) atomicOr(&a.glob->err, kErrDigits);
         const long long t_red = clock64();
-        if (acc) trace_add(mode == 1 ? 14 : 8, t_loop);   // 14: first assignment of a run
-        // one fused CTA reduction: objective (128-bit) and the two counters
+        if (mode) trace_add(mode == 1 ? 14 : 8, t_loop);   // 14: first assignment of a run
+        // one fused CTA reduction: objective (128-bit) and the two counters,
+        // pushed into rank 0's inbox
         unsigned __int128 F = warp_sum_u128(facc);
         const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
         const int wid = threadIdx.x >> 5;
@@ -334,27 +477,27 @@ struct Worker {
             F = warp_sum_u128(F);
             ir = warp_sum(ir);
             if (lane == 0) {
-                sm.x->f_lo = (unsigned long long)F;
-                sm.x->f_hi = (unsigned long long)(F >> 64);
-                sm.x->inexact = ir >> 32;
-                sm.x->rescored = ir & 0xffffffffull;
+                ObjPart* dst = cl.map_shared_rank(sm.inbox, 0) + rank;
+                dst->f_lo = (unsigned long long)F;
+                dst->f_hi = (unsigned long long)(F >> 64);
+                dst->inexact = ir >> 32;
+                dst->rescored = ir & 0xffffffffull;
             }
         }
-        __syncthreads();
-        if (acc) trace_add(9, t_red);
+        if (mode) trace_add(9, t_red);
     }
 
-    // After a barrier: warp 0 of rank 0 combines the CTA partials into f
-    // (exact sum, rounded once) and records the counters.  Call from warp 0.
+    // After a barrier, on rank 0, warp 0: the CTA partials of the inbox
+    // combined into f (exact sum, rounded once); the counters recorded.
     __device__ double combine_objective_warp() {
         const int lane = threadIdx.x & 31;
         unsigned __int128 F = 0;
         unsigned long long I = 0, R = 0;
         for (int q = lane; q < cs; q += 32) {
-            const Xch* p = rx(q);
-            F += ((unsigned __int128)p->f_hi << 64) | (unsigned __int128)p->f_lo;
-            I += p->inexact;
-            R += p->rescored;
+            const ObjPart& p = sm.inbox[q];
+            F += ((unsigned __int128)p.f_hi << 64) | (unsigned __int128)p.f_lo;
+            I += p.inexact;
+            R += p.rescored;
         }
         F = warp_sum_u128(F);
         I = warp_sum(I);
@@ -365,94 +508,58 @@ struct Worker {
         }
         return u128_to_double(F, g.gf);       // valid in lane 0
     }
+    // Rank 0, one thread: the decision to every CTA of the cluster.
+    __device__ void push_decision(double f, int stop) {
+        for (int q = 0; q < cs; ++q) {
+            Decision* d = cl.map_shared_rank(sm.dec, q);
+            d->f = f;
+            d->stop = stop;
+        }
+    }
+
+    // Zero the owned sums and counts (before a Lloyd run; a cluster barrier
+    // must follow before any CTA adds to them).
+    __device__ void zero_owned() {
+        const int nOwned = (k - rank + cs - 1) / cs;
+        for (int e = threadIdx.x; e < nOwned * NP * kAccWords; e += TPB) sm.OACC[e] = 0;
+        for (int e = threadIdx.x; e < nOwned; e += TPB) sm.ocnt[e] = 0;
+    }
 
     // a6 (owner part): new centroid of each owned cluster j (j % cs == rank):
     // float(double(exact sum) / count); an empty cluster keeps its centroid.
-    // A group of G >= cs lanes handles one owned (cluster, dimension)
-    // element: lane q of the group reads CTA q's digits and count, a
-    // segmented shuffle reduction combines them, and the group leader does
-    // the double conversion and division (many elements in parallel).
+    // The sums are complete in this CTA's shared memory; the new centroids
+    // and the empty flags are pushed into every CTA's Cnext / emptyall.
     __device__ void owner_update() {
         const int nOwned = (k - rank + cs - 1) / cs;
-        const int G = cs <= 1 ? 1 : cs <= 2 ? 2 : cs <= 4 ? 4 : cs <= 8 ? 8 : 16;
-        const int q = threadIdx.x % G;
-        const int groups = TPB / G;
         const int total = nOwned * NP;
-        // all threads run the same trip count so the shuffles stay converged
-        for (int base = 0; base < total; base += groups) {
-            const int e = base + (int)threadIdx.x / G;
-            const bool valid = e < total;
-            const int j = rank + (valid ? e / NP : 0) * cs;
-            const int d = valid ? e % NP : 0;
-            __int128 V = 0;
-            long long cntj = 0;
-            if (valid && q < cs) {
-                const int* wq = cl.map_shared_rank(sm.ACC, q) + (size_t)j * acc_stride<NP>() + d * kDigits;
-                int dg[kDigits];
-#pragma unroll
-                for (int i = 0; i < kDigits; ++i) dg[i] = wq[i];
-                cntj = cl.map_shared_rank(sm.cnt, q)[j];
-#pragma unroll
-                for (int i = 0; i < kDigits; ++i) V += (__int128)dg[i] * ((__int128)1 << (16 * i));
+        for (int e = threadIdx.x; e < total; e += TPB) {
+            const int slot = e / NP, d = e % NP;
+            const int j = rank + slot * cs;
+            const long long* wd = sm.OACC + (size_t)e * kAccWords;
+            const long long cntj = sm.ocnt[slot];
+            float c = sm.Ccur[(size_t)j * NP + d];
+            if (cntj > 0 && d < n) {
+                const __int128 V = (__int128)wd[0] + ((__int128)wd[1] << 32) + ((__int128)wd[2] << 64);
+                c = __double2float_rn(__ddiv_rn(i128_to_double(V, g.gx), (double)cntj));
             }
-            for (int o = G >> 1; o > 0; o >>= 1) {
-                const unsigned long long lo = __shfl_down_sync(0xffffffffu, (unsigned long long)V, o, G);
-                const long long hi = __shfl_down_sync(0xffffffffu, (long long)(V >> 64), o, G);
-                V += (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
-                cntj += __shfl_down_sync(0xffffffffu, cntj, o, G);
-            }
-            if (valid && q == 0) {
-                float c = sm.Ccur[(size_t)j * NP + d];
-                if (cntj > 0 && d < n) {
-                    const double sum = i128_to_double(V, g.gx);
-                    c = __double2float_rn(__ddiv_rn(sum, (double)cntj));
-                }
-                sm.Cnew[(size_t)j * NP + d] = c;
-                if (d == 0) sm.empty[j] = (cntj == 0) ? 1 : 0;
+            const unsigned char em = (cntj == 0) ? 1 : 0;
+            for (int q = 0; q < cs; ++q) {
+                cl.map_shared_rank(sm.Cnext, q)[(size_t)j * NP + d] = c;
+                if (d == 0) cl.map_shared_rank(sm.emptyall, q)[j] = em;
             }
         }
-    }
-
-    __device__ void pull_new_centroids() {
-        for (int e = threadIdx.x; e < k * NP; e += TPB) {
-            const int j = e / NP;
-            sm.Ccur[e] = cl.map_shared_rank(sm.Cnew, j % cs)[e];
-        }
-        __syncthreads();
-    }
-    __device__ void pull_empty() {
-        for (int j = threadIdx.x; j < k; j += TPB)
-            sm.emptyall[j] = cl.map_shared_rank(sm.empty, j % cs)[j];
-        __syncthreads();
-    }
-
-    // Broadcast rank 0's decision to every thread of this CTA.
-    __device__ void read_decision(double& f, int& stop) {
-        if (threadIdx.x == 0) {
-            const Xch* p0 = rx(0);
-            sm.bcast[0] = __double_as_longlong(p0->fval);
-            sm.bcast[1] = p0->stop;
-        }
-        __syncthreads();
-        f = __longlong_as_double(sm.bcast[0]);
-        stop = (int)sm.bcast[1];
-        __syncthreads();
     }
 
     // f(Ccur, S) without updating centroids (recompute of f_hat_w, recheck).
     __device__ double eval(long long s) {
         assign_slice(s, 0);
-        cl.sync();
+        cl.sync();                                       // partials in rank 0's inbox
         if (rank == 0 && threadIdx.x < 32) {
             const double f = combine_objective_warp();
-            if (threadIdx.x == 0) {
-                sm.x->fval = f;
-                sm.x->stop = 1;
-            }
+            if (threadIdx.x == 0) push_decision(f, 1);
         }
-        cl.sync();
-        double f; int stop;
-        read_decision(f, stop);
+        cl.sync();                                       // decision in every CTA
+        const double f = sm.dec->f;
         if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->eval_rows, (unsigned long long)s);
         return f;
     }
@@ -460,6 +567,8 @@ struct Worker {
     // Lloyd from Ccur (Sec. 4.1; Sec. 5 stop rule).  On return Ccur holds the
     // result C_a, emptyall its empty clusters, `iters` the number of updates.
     __device__ double lloyd(long long s, int& iters) {
+        zero_owned();
+        cl.sync();                                       // no CTA adds before the owners cleared
         double f_prev = 0.0;
         int it = 0;
         for (;;) {
@@ -468,34 +577,33 @@ struct Worker {
             trace_add(1, t_a);
             if (tracer()) atomicAdd(&a.glob->trace[6], 1ull);
             const long long t_x = clock64();
-            cl.sync();                                       // partials ready
+            cl.sync();                                       // sums and partials at their owners
             trace_add(10, t_x);
             const long long t_o = clock64();
             owner_update();
-            double fw = 0.0;
-            if (rank == 0 && threadIdx.x < 32) fw = combine_objective_warp();
-            if (rank == 0 && threadIdx.x == 0) {
-                const double f = fw;
-                int stop;
-                if (it == 0) stop = (a.max_lloyd <= 0);
-                else stop = (__dsub_rn(f_prev, f) <= __dmul_rn(a.tol, f_prev)) || (it >= a.max_lloyd);
-                sm.x->fval = f;
-                sm.x->stop = stop;
+            if (rank == 0 && threadIdx.x < 32) {
+                const double f = combine_objective_warp();
+                if (threadIdx.x == 0) {
+                    int stop;
+                    if (it == 0) stop = (a.max_lloyd <= 0);
+                    else stop = (__dsub_rn(f_prev, f) <= __dmul_rn(a.tol, f_prev)) || (it >= a.max_lloyd);
+                    push_decision(f, stop);
+                }
             }
             trace_add(11, t_o);
             const long long t_b2 = clock64();
-            cl.sync();                                       // updates + decision ready
+            cl.sync();                                       // updates + decision in every CTA
             trace_add(12, t_b2);
             const long long t_p = clock64();
-            double f; int stop;
-            read_decision(f, stop);
+            const double f = sm.dec->f;
+            const int stop = sm.dec->stop;
             if (stop) {
-                pull_empty();
                 trace_add(2, t_x);
                 iters = it;
                 return f;
             }
-            pull_new_centroids();
+            for (int e = threadIdx.x; e < k * NP; e += TPB) sm.Ccur[e] = sm.Cnext[e];
+            __syncthreads();
             prep_centroids();
             trace_add(13, t_p);
             trace_add(2, t_x);
@@ -835,7 +943,7 @@ int worker_max_cluster_t(int k) {
 
 template <int NP, int TPB>
 cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st) {
-    const size_t smem = worker_smem_bytes<NP>(a.k);
+    const size_t smem = worker_smem_bytes<NP>(a.k) + bucket_smem_bytes(a.rows_cta);
     cudaError_t e = allow_max_smem((const void*)worker_kernel<NP, TPB>);
     if (e != cudaSuccess) return e;
     if (a.cs > 8) {
