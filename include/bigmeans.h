@@ -336,12 +336,33 @@ bm_status bm_set_fullpass_impl(int32_t impl);
 int32_t bm_last_fullpass_impl(void);
 
 /* ---------------------------------------------------------------------------
+ * How the competing workers of a round (Sec. 4.2, Alg. 1) map onto the GPU.
+ * Every round is one launch of the worker kernel for all workers of the fit.
+ *   Worker groups (default): when every worker gets a cluster of 8 CTAs and
+ *   the whole launch can be resident at once (a cooperative launch), the
+ *   clusters the device can hold beyond one per worker go to the workers
+ *   with the most sample rows per CTA, so a large sample spans up to 8
+ *   clusters (64 CTAs) that add up their exact partial sums in global memory
+ *   with a barrier among the group's CTAs; rows per CTA then stay about
+ *   equal across workers.  Each such barrier is bounded (a few seconds):
+ *   when one runs out the round returns BM_ETIMEOUT.
+ *   Otherwise (bm_set_worker_groups(0), more workers than resident clusters,
+ *   or bm_set_big_clusters(1)): one cluster per worker, all of the size the
+ *   largest sample needs (the cluster tile below), in the same launch.
+ * Results are identical either way (all reductions are exact).
+ * bm_set_worker_groups: 1 (default) allows groups, 0 disables them; other
+ * values are BM_EINVAL.  Process-wide, read at each round's launch.
+ * ------------------------------------------------------------------------- */
+bm_status bm_set_worker_groups(int32_t on);
+int32_t bm_get_worker_groups(void);
+
+/* ---------------------------------------------------------------------------
  * Cluster tile of the worker kernel and its autotuner.
- * A worker runs as one thread-block cluster of up to 16 CTAs with about
- * `rows_per_cta` sample rows per CTA (default 1024).  The value changes only
- * speed: labels, centroids and objectives are identical for every value (all
- * reductions are exact).  The setting is process-wide and read when a fit is
- * created.
+ * Without groups a worker runs as one thread-block cluster of up to 16 CTAs
+ * with about `rows_per_cta` sample rows per CTA (default 1024).  The value
+ * changes only speed: labels, centroids and objectives are identical for
+ * every value (all reductions are exact).  The setting is process-wide and
+ * read when a fit is created.
  * bm_set_rows_per_cta: 0 restores the default; otherwise 256 .. 32767.
  * bm_autotune_rows_per_cta: for each candidate, creates a 2-round fit of the
  * given arguments, runs round 0 as warm-up and times round 1 with CUDA

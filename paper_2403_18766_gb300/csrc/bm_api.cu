@@ -93,6 +93,8 @@ bm_status fail(bm_status s, const char* fmt, ...) {
 
 constexpr size_t kSmemLimit = 227 * 1024;
 constexpr int kRowsPerCta = 1024;
+constexpr int kMaxGroupWorkers = 64;     // workers of a fit that may form groups
+constexpr int kGroupCs = 8;              // CTAs per cluster of a grouped launch
 
 int padded_dim(int n) {
     if (n <= 4) return 4;
@@ -190,6 +192,12 @@ std::atomic<int> g_rows_per_cta{kRowsPerCta};
 // with 512-thread CTAs (twice the warps per SM for the longest workers).
 std::atomic<int> g_big_tpb{0};
 std::atomic<int> g_sample_tables{0};
+// 1: no groups (every worker is one cluster, as in a non-cooperative launch)
+std::atomic<int> g_no_groups{0};
+// Fits created on this thread may use groups (the serving runners turn it
+// off: a cooperative launch sized for the whole device would wait for the
+// other jobs' kernels to drain, which defeats running jobs side by side).
+thread_local bool t_groups_ok = true;
 
 // Most sample rows one worker CTA can take: kMaxRowsPerCta, and the label
 // buckets of a Lloyd run (4 bytes per row) must fit beside the worker's
@@ -217,6 +225,10 @@ long long next_pow2(long long v) {
 }
 
 }  // namespace
+
+namespace bm {
+void set_thread_groups(bool ok) { t_groups_ok = ok; }
+}  // namespace bm
 
 struct bm_fit_ctx {
     cudaStream_t st = nullptr;
@@ -248,10 +260,11 @@ struct bm_fit_ctx {
     float* Cw = nullptr; float* Cw_cta = nullptr; unsigned char* deg = nullptr;
     double* fhat = nullptr; double* f_final = nullptr; long long* L_buf = nullptr;
     unsigned long long* timer = nullptr;
+    // group exchange of workers that span several clusters (null: no groups)
+    long long* xpart = nullptr; int* xcnt = nullptr; unsigned long long* xobj = nullptr;
+    unsigned* xbar = nullptr; float* xC = nullptr; int* xflag = nullptr;
     int max_cs = 8;
-    std::vector<cudaStream_t> wst;          // worker streams (fork/join with st)
     cudaEvent_t ev_fork = nullptr;
-    std::vector<cudaEvent_t> ev_join;
     // phase timing: event pairs around each launch, summed when the stream syncs
     struct Span { cudaEvent_t a, b; int kind; cudaStream_t st; };
     std::vector<Span> spans;
@@ -259,6 +272,8 @@ struct bm_fit_ctx {
     double t_worker = 0, t_full = 0, t_sample = 0;
     long long n_worker = 0, n_full = 0;
     long long n_kernels = 0;                // kernels of this library launched so far
+    int last_groups = 0;                    // clusters of the last grouped round launch (0: not grouped)
+    bool groups_ok = true;                  // groups allowed for this fit (creating thread's setting)
 };
 
 namespace {
@@ -295,6 +310,9 @@ WorkerArgs make_args(const bm_fit_ctx* c, int mode, int parity = 0) {
     a.Cw = c->Cw; a.Cw_cta = c->Cw_cta; a.deg = c->deg; a.fhat = c->fhat;
     a.L_buf = c->L_buf; a.L_cap = c->L_cap; a.f_final = c->f_final;
     a.gB = c->gB; a.gp2 = c->gp2;
+    a.xpart = c->xpart; a.xcnt = c->xcnt; a.xobj = c->xobj;
+    a.xbar = c->xbar; a.xabort = c->xbar ? reinterpret_cast<int*>(c->xbar + c->pol.workers) : nullptr;
+    a.xC = c->xC; a.xflag = c->xflag;
     return a;
 }
 
@@ -372,11 +390,28 @@ void collect_spans(bm_fit_ctx* c) {
 // runs) the padded sample, its indices, draws and sampler table; per worker
 // the K-means++ D^2, labels, centroids and state.
 // Device bytes of a fit's workspace (the layout of alloc_workspace).
+// Bytes of the group exchange buffers, 0 when the fit cannot use groups
+// (more workers than a cooperative launch can hold clusters, or too large).
+size_t group_bytes(const bm_fit_ctx* c, int W) {
+    if (W > kMaxGroupWorkers) return 0;
+    const size_t part = (size_t)W * 2 * kMaxGroup * c->k * c->np * kAccWords * 8;
+    if (part > ((size_t)256 << 20)) return 0;
+    return part;
+}
+
 size_t workspace_bytes(const bm_fit_ctx* c, int W) {
     const long long k = c->k, np = c->np;
     const long long J = 2ll * W * (c->pol.passes + 1);
     size_t off = 0;
     auto take = [&](size_t bytes) { off += (bytes + 255) & ~(size_t)255; };
+    if (const size_t gb = group_bytes(c, W)) {
+        take(gb);
+        take((size_t)W * 2 * kMaxGroup * k * 4);
+        take((size_t)W * 2 * kMaxGroup * 4 * 8);
+        take((size_t)W * 2 * 4);
+        take((size_t)W * k * np * 4);
+        take((size_t)W * 2 * 4);
+    }
     take(sizeof(Globals));
     take((size_t)J * c->s_cap * np * 4);
     take((size_t)J * c->s_cap * 8);
@@ -416,6 +451,16 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     const size_t o_ff = take((size_t)W * 8);
     const size_t o_L = take((size_t)c->L_cap * 8);
     const size_t o_t = take(8);
+    const size_t gb = group_bytes(c, W);
+    size_t o_xp = 0, o_xc = 0, o_xo = 0, o_xb = 0, o_xC = 0, o_xf = 0;
+    if (gb) {
+        o_xp = take(gb);
+        o_xc = take((size_t)W * 2 * kMaxGroup * k * 4);
+        o_xo = take((size_t)W * 2 * kMaxGroup * 4 * 8);
+        o_xb = take((size_t)W * 2 * 4);
+        o_xC = take((size_t)W * k * np * 4);
+        o_xf = take((size_t)W * 2 * 4);
+    }
     cudaError_t e = lib_alloc(&c->base, off, c->st);
     if (e != cudaSuccess) {
         c->base = nullptr;
@@ -429,6 +474,11 @@ bm_status alloc_workspace(bm_fit_ctx* c, int W) {
     c->D2 = (float*)(b + o_D2); c->lab = (int*)(b + o_lab); c->Cw = (float*)(b + o_Cw); c->Cw_cta = (float*)(b + o_Cwc);
     c->deg = (unsigned char*)(b + o_deg); c->fhat = (double*)(b + o_fhat); c->f_final = (double*)(b + o_ff);
     c->L_buf = (long long*)(b + o_L); c->timer = (unsigned long long*)(b + o_t);
+    if (gb) {
+        c->xpart = (long long*)(b + o_xp); c->xcnt = (int*)(b + o_xc);
+        c->xobj = (unsigned long long*)(b + o_xo); c->xbar = (unsigned*)(b + o_xb);
+        c->xC = (float*)(b + o_xC); c->xflag = (int*)(b + o_xf);
+    }
     CU(cudaMemsetAsync(c->glob, 0, sizeof(Globals), c->st));
     CU(cudaMemsetAsync(c->Cw, 0, (size_t)W * k * np * 4, c->st));
     CU(cudaMemsetAsync(c->table, 0, (size_t)J * c->H * 8, c->st));
@@ -512,27 +562,89 @@ long long size_of(const bm_fit_ctx* c, int w, int t) {
 }
 
 bm_status ensure_streams(bm_fit_ctx* c) {
-    if (!c->wst.empty()) return BM_OK;
-    const int ns = std::min(c->pol.workers, 16);
+    if (c->sst) return BM_OK;
     int lo_prio = 0, hi_prio = 0;
     CU(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
     CU(cudaStreamCreateWithPriority(&c->sst, cudaStreamNonBlocking, lo_prio));
     CU(cudaEventCreateWithFlags(&c->ev_sdone, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    for (int i = 0; i < ns; ++i) {
-        cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr;
-        CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-        c->wst.push_back(s);
-        CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        c->ev_join.push_back(e);
-    }
     return BM_OK;
 }
 
-// Rounds [r0, r1) for every worker: one launch per worker on the worker
-// streams, each with a cluster sized for that worker's largest s_w, so the
-// rows per CTA (and the time per Lloyd iteration) stay balanced.
+// The launch plan of one round: every worker of the fit in one launch.
+//  * Groups (cooperative launch, clusters of kGroupCs CTAs): when every
+//    worker gets a cluster and the whole grid can be resident at once, the
+//    clusters left over go, one at a time, to the worker with the most
+//    sample rows per CTA, so a large sample spreads over several clusters
+//    (up to kMaxGroup) that add up their exact partial sums in global
+//    memory; rows per CTA then stay about equal across workers.
+//  * Otherwise (more workers than resident clusters, groups disabled, or
+//    512-thread CTAs requested): one cluster per worker, all of one size
+//    (for the largest sample), launched together; clusters that do not fit
+//    at once start as others finish (they never wait on one another).
+// Clusters are ordered by decreasing sample size.  Returns the clusters.
+int plan_round(bm_fit_ctx* c, const std::vector<long long>& sz, WorkerArgs& a) {
+    const int W = c->pol.workers;
+    std::vector<int> order(W);
+    for (int w = 0; w < W; ++w) order[w] = w;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sz[x] > sz[y]; });
+    const long long smax = sz[order[0]];
+    const long long cap = rows_cap(c->np, c->k);
+    if (c->xpart && c->groups_ok && W <= kMaxLaunchClusters && !g_big_tpb.load() && !g_no_groups.load()) {
+        std::vector<int> G(W, 1);
+        int total = W;
+        const size_t base = worker_smem(c->np, c->k);
+        auto rows_of = [&](int w) { return (sz[w] + (long long)G[w] * kGroupCs - 1) / ((long long)G[w] * kGroupCs); };
+        // capacity with the bucket memory of the current plan (it only
+        // shrinks as groups grow, so the capacity only grows)
+        int capacity = 0;
+        for (int pass = 0; pass < 3; ++pass) {
+            long long rows = 0;
+            for (int w = 0; w < W; ++w) rows = std::max(rows, rows_of(w));
+            capacity = std::min(worker_active_clusters(c->np, kGroupCs, base + bucket_smem_bytes((int)rows)),
+                                kMaxLaunchClusters);
+            while (total < capacity) {
+                int best = -1;
+                for (int w = 0; w < W; ++w)
+                    if (G[w] < kMaxGroup && (best < 0 || rows_of(w) > rows_of(best))) best = w;
+                if (best < 0 || rows_of(best) <= 256) break;
+                G[best]++;
+                total++;
+            }
+        }
+        long long rows = 0;
+        for (int w = 0; w < W; ++w) rows = std::max(rows, rows_of(w));
+        if (W <= capacity && total <= capacity && rows <= cap) {
+            int ci = 0;
+            for (int w : order)
+                for (int q = 0; q < G[w]; ++q)
+                    a.cmap[ci++] = (unsigned)w | ((unsigned)q << 16) | ((unsigned)G[w] << 24);
+            a.ncl = ci;
+            a.cs = kGroupCs;
+            a.coop = 1;
+            a.rows_cta = (int)rows;
+            a.tpb = 256;
+            return ci;
+        }
+    }
+    a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta, cap);
+    a.rows_cta = (int)((smax + a.cs - 1) / a.cs);
+    a.coop = 0;
+    a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
+    if (W <= kMaxLaunchClusters) {
+        for (int i = 0; i < W; ++i) a.cmap[i] = (unsigned)order[i] | (1u << 24);
+        a.ncl = W;
+    } else {
+        a.ncl = 0;                                  // worker = cluster index
+        a.worker_base = 0;
+    }
+    return W;
+}
+
+// Rounds [r0, r1) for every worker: the round's samples (drawn ahead on the
+// sampling stream, or now), then one launch of the worker kernel for all
+// workers (plan_round), then the next round's samples on the sampling stream
+// while the workers run.
 bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     bm_status s;
     if ((s = ensure_streams(c))) return s;
@@ -557,45 +669,19 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         c->n_kernels++;
     }
     c->prefetched = -1;
+    std::vector<long long> sz(c->pol.workers, 0);
+    for (int w = 0; w < c->pol.workers; ++w)
+        for (int t = r0; t < r1; ++t) sz[w] = std::max(sz[w], size_of(c, w, t));
+    WorkerArgs a = make_args(c, kModeRounds, parity);
+    a.round_begin = r0;
+    a.round_end = r1;
+    a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
+    const int clusters = plan_round(c, sz, a);
+    if (a.coop) CU(cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, c->st));   // barriers, aborts
     CU(cudaEventRecord(c->ev_fork, c->st));
-    const int ns = (int)c->wst.size();
-    for (int i = 0; i < ns; ++i) CU(cudaStreamWaitEvent(c->wst[i], c->ev_fork, 0));
-    // A failed launch must not return before the workers already launched
-    // are joined into c->st: the caller frees the workspace on c->st.
-    cudaError_t launch_err = cudaSuccess;
-    // largest samples first: the longest workers start earliest (the order
-    // of independent workers changes no result)
-    std::vector<std::pair<long long, int>> order;
-    for (int w = 0; w < c->pol.workers; ++w) {
-        long long smax = 0;
-        for (int t = r0; t < r1; ++t) smax = std::max(smax, size_of(c, w, t));
-        order.push_back({-smax, w});
-    }
-    std::sort(order.begin(), order.end());
-    for (int oi = 0; oi < c->pol.workers && launch_err == cudaSuccess; ++oi) {
-        const int w = order[oi].second;
-        const long long smax = -order[oi].first;
-        WorkerArgs a = make_args(c, kModeRounds, parity);
-        a.round_begin = r0;
-        a.round_end = r1;
-        a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
-        a.worker_base = w;
-        a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta, rows_cap(c->np, c->k));
-        a.rows_cta = (int)((smax + a.cs - 1) / a.cs);
-        // clusters at the size cap with more rows per CTA than the tile get
-        // 512-thread CTAs (one per SM) when the big-cluster option is on
-        a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
-        launch_err = launch_worker(c->np, a, 1, c->wst[oi % ns]);
-        if (launch_err == cudaSuccess) c->n_kernels++;
-    }
-    if (launch_err != cudaSuccess) {
-        for (int i = 0; i < ns; ++i) {
-            cudaEventRecord(c->ev_join[i], c->wst[i]);
-            cudaStreamWaitEvent(c->st, c->ev_join[i], 0);
-        }
-        span_end(c, sp);
-        return fail(BM_ECUDA, "worker launch: %s", cudaGetErrorString(launch_err));
-    }
+    CU(launch_worker(c->np, a, clusters, c->st));
+    c->n_kernels++;
+    c->last_groups = a.coop ? clusters : 0;
     // Draw the next round's samples into the other half while the workers
     // run; that half was last read by the previous round, which finished
     // before ev_fork.
@@ -609,10 +695,6 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         CU(cudaEventRecord(c->ev_sdone, c->sst));
         c->n_kernels++;
         c->prefetched = r0 + 1;
-    }
-    for (int i = 0; i < ns; ++i) {
-        CU(cudaEventRecord(c->ev_join[i], c->wst[i]));
-        CU(cudaStreamWaitEvent(c->st, c->ev_join[i], 0));
     }
     span_end(c, sp);
     return BM_OK;
@@ -697,6 +779,7 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
 
     bm_fit_ctx* c = new bm_fit_ctx();
     c->t0 = std::chrono::steady_clock::now();
+    c->groups_ok = t_groups_ok;
     c->st = (cudaStream_t)stream;
     c->X = X_dev; c->m = m; c->n = n; c->k = k; c->np = padded_dim(n);
     c->pol = pol; c->bud = bud; c->seed = seed;
@@ -749,6 +832,13 @@ bm_status bm_set_big_clusters(int32_t on) {
     return BM_OK;
 }
 int32_t bm_get_big_clusters(void) { return g_big_tpb.load(); }
+
+bm_status bm_set_worker_groups(int32_t on) {
+    if (on != 0 && on != 1) return fail(BM_EINVAL, "worker groups = %d must be 0 or 1", on);
+    g_no_groups.store(on ? 0 : 1);
+    return BM_OK;
+}
+int32_t bm_get_worker_groups(void) { return g_no_groups.load() ? 0 : 1; }
 
 bm_status bm_set_sampler_impl(int32_t impl) {
     if (impl != 0 && impl != 1) return fail(BM_EINVAL, "sampler impl = %d must be 0 or 1", impl);
@@ -900,7 +990,6 @@ void bm_fit_destroy(bm_fit_ctx* c) {
     if (c->prefetched >= 0 && c->ev_sdone) cudaStreamWaitEvent(c->st, c->ev_sdone, 0);
     // nothing of this fit may still run when its workspace is released (the
     // stream-ordered allocator may hand the memory to another stream at once)
-    for (cudaStream_t s : c->wst) cudaStreamSynchronize(s);
     if (c->sst) cudaStreamSynchronize(c->sst);
     if (c->base) {
         cudaFreeAsync(c->base, c->st);
@@ -910,10 +999,8 @@ void bm_fit_destroy(bm_fit_ctx* c) {
     collect_spans(c);
     for (auto& sp : c->spans) { cudaEventDestroy(sp.a); cudaEventDestroy(sp.b); }
     for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
-    for (cudaStream_t s : c->wst) cudaStreamDestroy(s);
     if (c->sst) cudaStreamDestroy(c->sst);
     if (c->ev_sdone) cudaEventDestroy(c->ev_sdone);
-    for (cudaEvent_t e : c->ev_join) cudaEventDestroy(e);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     delete c;
 }

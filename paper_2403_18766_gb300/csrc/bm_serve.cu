@@ -30,6 +30,7 @@
 
 namespace bm {
 bm_status set_error(bm_status s, const char* msg);
+void set_thread_groups(bool ok);
 }
 using bm::set_error;
 
@@ -88,6 +89,9 @@ struct bm_ctx {
 
     void runner() {
         if (device >= 0) cudaSetDevice(device);
+        // jobs run side by side: no worker groups (their cooperative
+        // launches would wait for the other jobs' kernels)
+        bm::set_thread_groups(false);
         cudaStream_t st = nullptr;
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {

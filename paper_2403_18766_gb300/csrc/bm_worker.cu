@@ -7,6 +7,19 @@ template <int NP>
 cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st);
 template <int NP>
 int worker_max_cluster_t(int k);
+template <int NP>
+int worker_active_clusters_t(int cs, size_t smem);
+
+int worker_active_clusters(int np, int cs, size_t smem) {
+    switch (np) {
+        case 4: return worker_active_clusters_t<4>(cs, smem);
+        case 8: return worker_active_clusters_t<8>(cs, smem);
+        case 16: return worker_active_clusters_t<16>(cs, smem);
+        case 32: return worker_active_clusters_t<32>(cs, smem);
+        case 64: return worker_active_clusters_t<64>(cs, smem);
+    }
+    return 0;
+}
 
 int worker_max_cluster(int np, int k) {
     switch (np) {

@@ -13,6 +13,13 @@ enum WorkerMode : int {
     kModeStepLloyd = 5,   // a4-a6 on a given sample
 };
 
+// A worker whose sample is large may span several clusters of one launch (a
+// group): the clusters exchange their partial sums through global memory and
+// a barrier among the group's CTAs, which needs every CTA of the launch to be
+// resident at once (a cooperative launch).
+constexpr int kMaxGroup = 8;               // clusters per worker
+constexpr int kMaxLaunchClusters = 160;    // entries of the cluster map
+
 struct WorkerArgs {
     // data
     const float* X;
@@ -33,6 +40,21 @@ struct WorkerArgs {
     int cs;                           // CTAs per cluster
     int rows_cta;                     // most sample rows of one CTA in a Lloyd run of this launch
                                       // (sizes the label buckets in shared memory; 0: no Lloyd)
+    // cluster map (ncl > 0): cluster c of the launch works for worker
+    // cmap[c] & 0xffff, as cluster (cmap[c] >> 16) & 0xff of a group of
+    // cmap[c] >> 24 clusters; ncl = 0: cluster c is worker worker_base + c
+    // alone
+    int ncl;
+    int coop;                         // host: launch cooperatively (all CTAs resident at once)
+    unsigned cmap[kMaxLaunchClusters];
+    // group exchange in global memory (per worker; two parity halves)
+    long long* xpart;                 // W x 2 x kMaxGroup x k x NP x 3 words
+    int* xcnt;                        // W x 2 x kMaxGroup x k counts
+    unsigned long long* xobj;         // W x 2 x kMaxGroup x 4 (objective partial, counters)
+    unsigned* xbar;                   // W barrier counters (zero at launch)
+    int* xabort;                      // W abort flags (zero at launch)
+    float* xC;                        // W x k x NP centroids re-seeded by cluster 0
+    int* xflag;                       // W x 2 deadline decisions
     int tpb;                          // threads per CTA: 256, or 512 (largest clusters)
     Globals* glob;
     // samples drawn by the sampling kernel: job (w, slot) = w * (P + 1) + slot
@@ -114,6 +136,9 @@ __host__ __device__ inline size_t worker_smem_bytes(int k) {
 __host__ __device__ inline size_t bucket_smem_bytes(int rows_cta) { return align16((size_t)rows_cta * 4); }
 
 cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_t st);
+// Clusters of `cs` CTAs (256 threads, `smem` bytes each) that can be resident
+// at once on the device (0 on error).
+int worker_active_clusters(int np, int cs, size_t smem);
 size_t worker_smem(int np, int k);
 int worker_max_cluster(int np, int k);   // 16 if 16-CTA clusters fit, else 8
 

@@ -14,6 +14,9 @@
 // and on values every CTA reads after a barrier from the same place, so all
 // CTAs execute the same sequence of barriers.
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "bm_device.cuh"
 #include "bm_worker.cuh"
@@ -82,6 +85,9 @@ struct Worker {
     cg::cluster_group cl;
     Sm<NP> sm;
     int rank, cs, w, k, n;
+    int gi, G, ctaW, nW;    // cluster gi of the worker's G clusters; CTA ctaW of its nW
+    int xpar = 0;           // parity of the next group exchange
+    unsigned gepoch = 0;    // group barriers passed (thread 0)
     Grids g;
     float* S;               // current sample (padded rows), set per pass
     float* D2; float* Cw_mine;
@@ -90,7 +96,19 @@ struct Worker {
     __device__ Worker(const WorkerArgs& args, cg::cluster_group c) : a(args), cl(c) {
         cs = a.cs;
         rank = (int)cl.block_rank();
-        w = a.worker_base + blockIdx.x / cs;
+        const int ci = blockIdx.x / cs;
+        if (a.ncl > 0) {
+            const unsigned e = a.cmap[ci];
+            w = (int)(e & 0xffffu);
+            gi = (int)((e >> 16) & 0xffu);
+            G = (int)(e >> 24);
+        } else {
+            w = a.worker_base + ci;
+            gi = 0;
+            G = 1;
+        }
+        ctaW = gi * cs + rank;
+        nW = G * cs;
         k = a.k;
         n = a.n;
         sm = carve<NP>(k, a.rows_cta);
@@ -104,7 +122,7 @@ struct Worker {
     __device__ Xch* rx(int q) { return cl.map_shared_rank(sm.x, q); }
 
     // Phase trace: rank 0, thread 0 adds elapsed SM cycles to glob->trace[i].
-    __device__ bool tracer() const { return rank == 0 && threadIdx.x == 0; }
+    __device__ bool tracer() const { return gi == 0 && rank == 0 && threadIdx.x == 0; }
     __device__ void trace_add(int i, long long t0) const {
         if (tracer()) atomicAdd(&a.glob->trace[i], (unsigned long long)(clock64() - t0));
     }
@@ -116,10 +134,51 @@ struct Worker {
         return a.job_s[job];
     }
 
+    // Rows of this CTA: its share of the worker's G * cs CTAs.
     __device__ void slice(long long s, long long& lo, long long& hi) const {
+        lo = s * ctaW / nW;
+        hi = s * (ctaW + 1) / nW;
+    }
+    // Rows of this CTA in K-means++, which cluster 0 of the group runs alone.
+    __device__ void kslice(long long s, long long& lo, long long& hi) const {
         lo = s * rank / cs;
         hi = s * (rank + 1) / cs;
     }
+    __device__ bool lead() const { return gi == 0 && rank == 0; }     // records the worker's counters
+
+    // ------------------------------------------------ group of clusters
+    // Barrier among every CTA of the worker's G clusters (G > 1): a counter
+    // in global memory that each CTA increments once per barrier; a CTA waits
+    // until it reaches (barriers passed) x (CTAs of the group).  The wait is
+    // bounded: when it runs out, or when another CTA of the group gave up,
+    // the group's abort flag is raised, every later wait of the group returns
+    // at once and the launch reports a timeout (results are then discarded).
+    __device__ void gsync() {
+        if (G == 1) return;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ++gepoch;
+            __threadfence();
+            atomicAdd(a.xbar + w, 1u);
+            const unsigned target = gepoch * (unsigned)nW;
+            const volatile unsigned* bar = a.xbar + w;
+            const volatile int* ab = a.xabort + w;
+            for (unsigned polls = 0; *bar < target; ++polls) {
+                if (*ab) break;
+                if (polls >= (1u << 22)) {
+                    atomicExch(a.xabort + w, 1);
+                    atomicOr(&a.glob->err, kErrTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+    __device__ bool group_aborted() const { return G > 1 && *(const volatile int*)(a.xabort + w) != 0; }
+    // Offsets of this worker's exchange slots (parity par, cluster q).
+    __device__ size_t xslot(int par, int q) const { return ((size_t)w * 2 + par) * kMaxGroup + q; }
 
     // cluster barrier that also orders global-memory writes
     __device__ void csync_global() {
@@ -488,11 +547,10 @@ struct Worker {
     }
 
     // After a barrier, on rank 0, warp 0: the CTA partials of the inbox
-    // combined into f (exact sum, rounded once); the counters recorded.
-    __device__ double combine_objective_warp() {
+    // combined into the cluster's partial (exact; valid in lane 0).
+    __device__ void cluster_objective_warp(unsigned __int128& F, unsigned long long& I, unsigned long long& R) {
         const int lane = threadIdx.x & 31;
-        unsigned __int128 F = 0;
-        unsigned long long I = 0, R = 0;
+        F = 0; I = 0; R = 0;
         for (int q = lane; q < cs; q += 32) {
             const ObjPart& p = sm.inbox[q];
             F += ((unsigned __int128)p.f_hi << 64) | (unsigned __int128)p.f_lo;
@@ -502,11 +560,50 @@ struct Worker {
         F = warp_sum_u128(F);
         I = warp_sum(I);
         R = warp_sum(R);
-        if (lane == 0) {
+    }
+    // The worker's objective from partials (F, I, R) of every cluster: with
+    // one cluster these are the partials themselves; with a group, rank 0 of
+    // each cluster publishes its partial (before the group barrier) and adds
+    // up all of them (after it).  f = the exact sum rounded once (lane 0);
+    // the counters are recorded once per worker.
+    __device__ void publish_objective(const unsigned __int128& F, unsigned long long I, unsigned long long R) {
+        if (G > 1 && (threadIdx.x & 31) == 0) {
+            unsigned long long* o = a.xobj + xslot(xpar, gi) * 4;
+            o[0] = (unsigned long long)F;
+            o[1] = (unsigned long long)(F >> 64);
+            o[2] = I;
+            o[3] = R;
+        }
+    }
+    __device__ double total_objective(unsigned __int128 F, unsigned long long I, unsigned long long R) {
+        if (G > 1) {
+            F = 0; I = 0; R = 0;
+            for (int q = 0; q < G; ++q) {
+                const volatile unsigned long long* o = a.xobj + xslot(xpar, q) * 4;
+                F += ((unsigned __int128)o[1] << 64) | (unsigned __int128)o[0];
+                I += o[2];
+                R += o[3];
+            }
+        }
+        if ((threadIdx.x & 31) == 0 && gi == 0) {
             if (I) atomicAdd(&a.glob->inexact, I);
             if (R) atomicAdd(&a.glob->rescored, R);
         }
-        return u128_to_double(F, g.gf);       // valid in lane 0
+        return u128_to_double(F, g.gf);
+    }
+    // Owners publish their clusters' partial sums and counts (group only).
+    __device__ void publish_sums() {
+        if (G == 1) return;
+        const int nOwned = (k - rank + cs - 1) / cs;
+        long long* dst = a.xpart + xslot(xpar, gi) * (size_t)k * NP * kAccWords;
+        int* dcnt = a.xcnt + xslot(xpar, gi) * (size_t)k;
+        for (int e = threadIdx.x; e < nOwned * NP; e += TPB) {
+            const int slot = e / NP, d = e % NP, j = rank + slot * cs;
+            const long long* wd = sm.OACC + (size_t)e * kAccWords;
+            long long* o = dst + ((size_t)j * NP + d) * kAccWords;
+            o[0] = wd[0]; o[1] = wd[1]; o[2] = wd[2];
+            if (d == 0) dcnt[j] = sm.ocnt[slot];
+        }
     }
     // Rank 0, one thread: the decision to every CTA of the cluster.
     __device__ void push_decision(double f, int stop) {
@@ -535,11 +632,22 @@ struct Worker {
         for (int e = threadIdx.x; e < total; e += TPB) {
             const int slot = e / NP, d = e % NP;
             const int j = rank + slot * cs;
-            const long long* wd = sm.OACC + (size_t)e * kAccWords;
-            const long long cntj = sm.ocnt[slot];
+            __int128 V = 0;
+            long long cntj = 0;
+            if (G == 1) {
+                const long long* wd = sm.OACC + (size_t)e * kAccWords;
+                V = (__int128)wd[0] + ((__int128)wd[1] << 32) + ((__int128)wd[2] << 64);
+                cntj = sm.ocnt[slot];
+            } else {                                 // the group's partials, in global memory
+                for (int q = 0; q < G; ++q) {
+                    const volatile long long* wd =
+                        a.xpart + (xslot(xpar, q) * (size_t)k * NP + (size_t)j * NP + d) * kAccWords;
+                    V += (__int128)wd[0] + ((__int128)wd[1] << 32) + ((__int128)wd[2] << 64);
+                    cntj += ((const volatile int*)a.xcnt)[xslot(xpar, q) * (size_t)k + j];
+                }
+            }
             float c = sm.Ccur[(size_t)j * NP + d];
             if (cntj > 0 && d < n) {
-                const __int128 V = (__int128)wd[0] + ((__int128)wd[1] << 32) + ((__int128)wd[2] << 64);
                 c = __double2float_rn(__ddiv_rn(i128_to_double(V, g.gx), (double)cntj));
             }
             const unsigned char em = (cntj == 0) ? 1 : 0;
@@ -554,13 +662,21 @@ struct Worker {
     __device__ double eval(long long s) {
         assign_slice(s, 0);
         cl.sync();                                       // partials in rank 0's inbox
+        unsigned __int128 F = 0;
+        unsigned long long I = 0, R = 0;
         if (rank == 0 && threadIdx.x < 32) {
-            const double f = combine_objective_warp();
+            cluster_objective_warp(F, I, R);
+            publish_objective(F, I, R);
+        }
+        gsync();                                         // every cluster's partial published
+        if (rank == 0 && threadIdx.x < 32) {
+            const double f = total_objective(F, I, R);
             if (threadIdx.x == 0) push_decision(f, 1);
         }
+        xpar ^= 1;
         cl.sync();                                       // decision in every CTA
         const double f = sm.dec->f;
-        if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->eval_rows, (unsigned long long)s);
+        if (lead() && threadIdx.x == 0) atomicAdd(&a.glob->eval_rows, (unsigned long long)s);
         return f;
     }
 
@@ -580,16 +696,30 @@ struct Worker {
             cl.sync();                                       // sums and partials at their owners
             trace_add(10, t_x);
             const long long t_o = clock64();
+            unsigned __int128 F = 0;
+            unsigned long long I = 0, R = 0;
+            if (G > 1) {                                     // partials of every cluster of the group
+                publish_sums();
+                if (rank == 0 && threadIdx.x < 32) {
+                    cluster_objective_warp(F, I, R);
+                    publish_objective(F, I, R);
+                }
+                gsync();
+            } else if (rank == 0 && threadIdx.x < 32) {
+                cluster_objective_warp(F, I, R);
+            }
             owner_update();
             if (rank == 0 && threadIdx.x < 32) {
-                const double f = combine_objective_warp();
+                const double f = total_objective(F, I, R);
                 if (threadIdx.x == 0) {
                     int stop;
                     if (it == 0) stop = (a.max_lloyd <= 0);
                     else stop = (__dsub_rn(f_prev, f) <= __dmul_rn(a.tol, f_prev)) || (it >= a.max_lloyd);
+                    if (group_aborted()) stop = 1;
                     push_decision(f, stop);
                 }
             }
+            xpar ^= 1;
             trace_add(11, t_o);
             const long long t_b2 = clock64();
             cl.sync();                                       // updates + decision in every CTA
@@ -640,7 +770,7 @@ struct Worker {
 
     __device__ void kmeanspp(long long s, unsigned long long k1) {
         long long lo, hi;
-        slice(s, lo, hi);
+        kslice(s, lo, hi);
         bool any_live = false;
         for (int j = 0; j < k; ++j) any_live |= (sm.deg[j] == 0);
         unsigned int mloc = 0;
@@ -764,7 +894,7 @@ struct Worker {
                 }
             }
             // centroid j = S[pick]
-            if (rank == 0 && threadIdx.x == 0) atomicAdd(&a.glob->reseeded, 1ull);
+            if (lead() && threadIdx.x == 0) atomicAdd(&a.glob->reseeded, 1ull);
             for (int d = threadIdx.x; d < NP; d += TPB) sm.Ccur[(size_t)j * NP + d] = S[pick * NP + d];
             __syncthreads();
             mloc = 0;
@@ -850,13 +980,23 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs
         }
         for (int p = 0; p < a.P; ++p) {
             if (a.deadline_ns) {
-                if (W.rank == 0 && threadIdx.x == 0) {
+                // the lead CTA reads the clock; its decision reaches every CTA
+                // of the cluster (and, for a group, every cluster)
+                if (W.lead() && threadIdx.x == 0) {
                     unsigned long long now;
                     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-                    W.sm.x->flag = (now >= a.deadline_ns) ? 1 : 0;
+                    const int late = (now >= a.deadline_ns) ? 1 : 0;
+                    W.sm.x->flag = late;
+                    if (W.G > 1) a.xflag[(size_t)w * 2 + W.xpar] = late;
                 }
-                W.cl.sync();
-                if (threadIdx.x == 0) W.sm.bcast[8] = W.rx(0)->flag;
+                if (W.G > 1) {
+                    W.gsync();
+                    if (threadIdx.x == 0) W.sm.bcast[8] = *(const volatile int*)(a.xflag + (size_t)w * 2 + W.xpar);
+                    W.xpar ^= 1;
+                } else {
+                    W.cl.sync();
+                    if (threadIdx.x == 0) W.sm.bcast[8] = W.rx(0)->flag;
+                }
                 __syncthreads();
                 const bool late = W.sm.bcast[8] != 0;
                 W.cl.sync();
@@ -867,9 +1007,16 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs
             bool any_deg = false;
             for (int j = 0; j < W.k; ++j) any_deg |= (W.sm.deg[j] != 0);
             if (any_deg) {
+                // re-seeding is in place (Alg. 1); a group's cluster 0 runs it
+                // over the whole sample and hands the centroids to the others
                 const long long t_k = clock64();
-                W.kmeanspp(s_w, stream_k1(kPurposeKpp, w, t, p));
-                W.store_centroids(W.Cw_mine);            // re-seeding is in place (Alg. 1)
+                if (W.gi == 0) W.kmeanspp(s_w, stream_k1(kPurposeKpp, w, t, p));
+                if (W.G > 1) {
+                    if (W.gi == 0 && W.rank == 0) W.store_centroids(a.xC + (size_t)w * W.k * NP);
+                    W.gsync();
+                    if (W.gi > 0) W.load_centroids(a.xC + (size_t)w * W.k * NP);
+                }
+                W.store_centroids(W.Cw_mine);
                 W.trace_add(0, t_k);
             }
             W.prep_centroids();
@@ -879,14 +1026,14 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs
                 fhat = f;
                 for (int j = threadIdx.x; j < W.k; j += TPB) W.sm.deg[j] = W.sm.emptyall[j];
                 W.store_centroids(W.Cw_mine);
-                if (W.rank == 0 && threadIdx.x == 0) {
+                if (W.lead() && threadIdx.x == 0) {
                     const unsigned long long pos = atomicAdd(&a.glob->accepts, 1ull);
                     atomicAdd(&a.glob->L_sum, (unsigned long long)s_w);
                     if ((long long)pos < a.L_cap) a.L_buf[pos] = s_w;
                 }
             }
             __syncthreads();
-            if (W.rank == 0 && threadIdx.x == 0) {
+            if (W.lead() && threadIdx.x == 0) {
                 atomicAdd(&a.glob->passes, 1ull);
                 atomicAdd(&a.glob->lloyd_iters, (unsigned long long)iters);
                 atomicAdd(&a.glob->assign_rows, (unsigned long long)(s_w * (iters + 1)));
@@ -894,9 +1041,9 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs
         }
         if (!failed && !out_of_time) ++rounds_completed;
     }
-    if (failed && W.rank == 0 && threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
+    if (failed && W.lead() && threadIdx.x == 0) atomicOr(&a.glob->err, kErrSample);
     // persist worker state
-    if (W.rank == 0) {
+    if (W.lead()) {
         for (int e = threadIdx.x; e < W.k * NP; e += TPB)
             a.Cw[(long long)w * W.k * NP + e] = W.Cw_mine[e];
         for (int j = threadIdx.x; j < W.k; j += TPB) a.deg[(long long)w * W.k + j] = W.sm.deg[j];
@@ -941,6 +1088,40 @@ int worker_max_cluster_t(int k) {
     return nclusters > 0 ? 16 : 8;
 }
 
+template <int NP>
+int worker_active_clusters_t(int cs, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::pair<int, size_t>, int> memo;
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(cs, smem);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    if (allow_max_smem((const void*)worker_kernel<NP, 256>) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(worker_kernel<NP, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                       cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, worker_kernel<NP, 256>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        ncl = 0;
+    }
+    memo[key] = ncl;
+    return ncl;
+}
+
 template <int NP, int TPB>
 cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st) {
     const size_t smem = worker_smem_bytes<NP>(a.k) + bucket_smem_bytes(a.rows_cta);
@@ -955,13 +1136,15 @@ cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st
     cfg.blockDim = dim3(TPB, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)a.cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = a.coop ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, worker_kernel<NP, TPB>, a);
 }
 

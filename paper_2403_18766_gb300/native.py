@@ -115,6 +115,8 @@ SIGNATURES = {
     "bm_set_rows_per_cta": (_i32, [_i32]),
     "bm_trim_memory": (_i32, []),
     "bm_set_big_clusters": (_i32, [_i32]),
+    "bm_set_worker_groups": (_i32, [_i32]),
+    "bm_get_worker_groups": (_i32, []),
     "bm_get_big_clusters": (_i32, []),
     "bm_set_sampler_impl": (_i32, [_i32]),
     "bm_get_sampler_impl": (_i32, []),
@@ -451,6 +453,15 @@ def autotune_rows_per_cta(X, k, policy, budget, seed=0, candidates=(1024, 2048, 
 def set_big_clusters(on):
     """bm_set_big_clusters: 512-thread CTAs for the workers whose cluster is at the cap."""
     _check(lib.bm_set_big_clusters(int(bool(on))))
+
+
+def set_worker_groups(on):
+    """bm_set_worker_groups: 1 = large samples may span several clusters (cooperative launch), 0 = never."""
+    _check(lib.bm_set_worker_groups(int(bool(on))))
+
+
+def get_worker_groups():
+    return int(lib.bm_get_worker_groups())
 
 
 def get_big_clusters():

@@ -344,3 +344,37 @@ def test_results_do_not_depend_on_big_cluster_ctas():
     assert r0["f_full"] == r1["f_full"] and r0["lloyd_iters"] == r1["lloyd_iters"]
     ref = obm.bigmeans(X, 10, pol, bud, seed=4)
     _assert_same(C1.cpu().numpy(), Y1.cpu().numpy(), r1, ref)
+
+
+# --------------------------------------------- worker groups (one launch)
+def test_results_do_not_depend_on_worker_groups():
+    """Large samples spread over several clusters that add up their exact
+    partial sums in global memory (cooperative launch), or one cluster per
+    worker: the same bits, equal to the oracle."""
+    X = gaussian_mixture(150_000, 16, 12, seed=34, cov="aniso")
+    pol = dict(s_min=2000, s_max=70_000, workers=5, passes=3)
+    bud = dict(rounds=3, max_lloyd=300, tol=1e-4, kpp_candidates=3, eval_full_each_round=True)
+    outs = []
+    try:
+        for on in (1, 0):
+            native.set_worker_groups(on)
+            outs.append(native.fit(_t(X), 12, native.make_policy(**pol), native.make_budget(**bud), seed=6))
+    finally:
+        native.set_worker_groups(1)
+    (C0, Y0, r0), (C1, Y1, r1) = outs
+    assert torch.equal(C0.view(torch.int32), C1.view(torch.int32)) and torch.equal(Y0, Y1)
+    assert r0["f_full"] == r1["f_full"] and r0["lloyd_iters"] == r1["lloyd_iters"]
+    assert r0["f_incumbent"] == r1["f_incumbent"]
+    ref = obm.bigmeans(X, 12, pol, bud, seed=6)
+    _assert_same(C0.cpu().numpy(), Y0.cpu().numpy(), r0, ref)
+
+
+def test_time_budget_with_worker_groups():
+    """A wall-clock budget: the lead CTA of each group decides when to stop
+    and every cluster of the group follows; the fit ends with a valid result."""
+    X = torch.from_numpy(gaussian_mixture(200_000, 8, 6, seed=35)).cuda()
+    pol = native.make_policy(s_min=5000, s_max=80_000, workers=4, passes=10)
+    bud = native.make_budget(rounds=0, seconds=0.3)
+    C, Y, rep = native.fit(X, 6, pol, bud, seed=2)
+    assert rep["rounds_done"] >= 1 and np.isfinite(rep["f_full"]) and rep["f_full"] > 0
+    assert int(Y.min()) >= 0 and int(Y.max()) < 6
