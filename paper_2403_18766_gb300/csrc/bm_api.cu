@@ -332,11 +332,10 @@ SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs, int parity = 0) {
     a.H = c->H; a.table_stride = c->H; a.table = c->table + J * a.table_stride;
     a.gen_base = c->gen;
     c->gen += (unsigned int)jobs;
-    // shared-memory bitmap of the m values when it fits beside a worker CTA
+    // shared-memory bitmap of the m values when it fits in one CTA
     const long long words = (c->m + 31) / 32;
     const size_t sb = sample_smem_bytes((int)std::min<long long>(words, 1 << 30));
-    if (mode != kSampleGather && !g_sample_tables.load() && words <= (1 << 30) && sb <= 144 * 1024 &&
-        sb + worker_smem(c->np, c->k) <= 200 * 1024)
+    if (mode != kSampleGather && !g_sample_tables.load() && words <= (1 << 30) && sb <= 200 * 1024)
         a.bitmap_words = (int)words;
     a.job_s = c->job_s + J; a.glob = c->glob;
     return a;

@@ -72,7 +72,7 @@ __device__ __forceinline__ long long pow2_at_least(long long v) {
 }
 
 // The same sample with a shared-memory bitmap of the m values (used when it
-// fits): the draws are taken in chunks of kThreads in counter order.  A draw
+// fits): the draws are taken in chunks of kSampleThreads in counter order.  A draw
 // t of value r is the first occurrence of r when r's bit is clear at the
 // start of t's chunk and t is the least draw of r inside the chunk (a small
 // shared hash table keyed by r keeps that least t).  The chunk's first
@@ -84,12 +84,12 @@ __device__ long long sample_by_bitmap(const SampleArgs& a, long long s, unsigned
     unsigned long long* mini = reinterpret_cast<unsigned long long*>(smem_raw);   // kMiniSlots
     unsigned int* bits = reinterpret_cast<unsigned int*>(mini + kMiniSlots);      // bitmap_words
     const long long m = a.m;
-    for (int i = threadIdx.x; i < a.bitmap_words; i += kThreads) bits[i] = 0u;
-    for (int i = threadIdx.x; i < kMiniSlots; i += kThreads) mini[i] = ~0ull;
+    for (int i = threadIdx.x; i < a.bitmap_words; i += kSampleThreads) bits[i] = 0u;
+    for (int i = threadIdx.x; i < kMiniSlots; i += kSampleThreads) mini[i] = ~0ull;
     __syncthreads();
     const unsigned long long thr = lemire_thr((unsigned long long)m);
     long long got = 0;
-    for (long long t0 = 0; t0 < cap && got < s; t0 += kThreads) {     // block-uniform
+    for (long long t0 = 0; t0 < cap && got < s; t0 += kSampleThreads) {     // block-uniform
         const long long t = t0 + threadIdx.x;
         unsigned int r = 0, h = 0;
         bool cand = false;
@@ -99,7 +99,7 @@ __device__ long long sample_by_bitmap(const SampleArgs& a, long long s, unsigned
             cand = ((bits[r >> 5] >> (r & 31)) & 1u) == 0u;
         }
         const unsigned long long key = ((unsigned long long)r << 32) | (unsigned int)t;
-        if (cand) {   // at most kThreads keys in 4 kThreads slots: a free slot always exists
+        if (cand) {   // at most kSampleThreads keys in 2 kSampleThreads slots: a free slot always exists
             h = tab_hash(r) & (kMiniSlots - 1);
             for (int p = 0; p < kMiniSlots; ++p) {
                 unsigned long long cur = mini[h];
@@ -126,8 +126,8 @@ __device__ long long sample_by_bitmap(const SampleArgs& a, long long s, unsigned
 }
 
 template <int NP>
-__global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
-    __shared__ long long red64[kWarps + 1];
+__global__ void __launch_bounds__(kSampleThreads, 1) sample_kernel(const SampleArgs a) {
+    __shared__ long long red64[kSampleThreads / 32 + 1];
     __shared__ int fail;
     const int job = blockIdx.x;
     int purpose = a.purpose, worker = a.worker, rnd = a.rnd, pss = a.pss;
@@ -178,19 +178,19 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
         if (threadIdx.x == 0) fail = 1;
         __syncthreads();
         for (int batch = 0; batch < 64 && s > 0; ++batch) {
-            for (long long t = T_done + threadIdx.x; t < T; t += kThreads) {
+            for (long long t = T_done + threadIdx.x; t < T; t += kSampleThreads) {
                 const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
                 draws[t] = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
             }
             __threadfence_block();
             __syncthreads();
             bool ok = true;
-            for (long long t = T_done + threadIdx.x; t < T; t += kThreads)
+            for (long long t = T_done + threadIdx.x; t < T; t += kSampleThreads)
                 ok &= tab_insert(tab, mask, gen, draws[t], (unsigned int)t, draws);
             if (!ok) atomicOr(&a.glob->err, kErrSample);
             __threadfence_block();
             __syncthreads();
-            const long long ch = (T + kThreads - 1) / kThreads;
+            const long long ch = (T + kSampleThreads - 1) / kSampleThreads;
             const long long c0 = ch * threadIdx.x, c1 = min(T, c0 + ch);
             long long mine = 0;
             for (long long t = c0; t < c1; ++t) mine += tab_is_first(tab, mask, gen, draws[t], (unsigned int)t, draws);
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) sample_kernel(const SampleArgs a) {
     const int n = a.n;
     const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
     const long long items = s * (NP / 4);
-    for (long long e = threadIdx.x; e < items; e += kThreads) {
+    for (long long e = threadIdx.x; e < items; e += kSampleThreads) {
         const long long i = e / (NP / 4);
         const int q = (int)(e % (NP / 4));
         const long long row = idx[i];
@@ -256,7 +256,7 @@ static cudaError_t launch_sample_t(const SampleArgs& a, int jobs, cudaStream_t s
         const cudaError_t e = allow_max_smem((const void*)sample_kernel<NP>);
         if (e != cudaSuccess) return e;
     }
-    sample_kernel<NP><<<jobs, kThreads, smem, st>>>(a);
+    sample_kernel<NP><<<jobs, kSampleThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

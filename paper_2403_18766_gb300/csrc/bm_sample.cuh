@@ -90,8 +90,11 @@ struct SampleArgs {
     Globals* glob;
 };
 
-// Slots of the per-chunk hash table of the bitmap path (4 per thread).
-constexpr int kMiniSlots = 4 * kThreads;
+// Threads of a sampling CTA (one CTA per sample): the draws are taken in
+// chunks of this many, in counter order.
+constexpr int kSampleThreads = 1024;
+// Slots of the per-chunk hash table of the bitmap path (2 per thread).
+constexpr int kMiniSlots = 2 * kSampleThreads;
 // Dynamic shared memory of a sampling launch.
 inline size_t sample_smem_bytes(int bitmap_words) {
     return bitmap_words > 0 ? (size_t)kMiniSlots * 8 + (((size_t)bitmap_words * 4 + 15) & ~(size_t)15) : 0;
