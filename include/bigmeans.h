@@ -184,6 +184,19 @@ bm_status bm_fit_create(const float* X_dev, int64_t m, int32_t n, int32_t k,
                         const bm_sample_policy* policy, const bm_budget* budget,
                         uint64_t seed, void* stream, bm_fit_ctx** out);
 bm_status bm_fit_rounds(bm_fit_ctx* ctx, int32_t rounds);
+/* bm_fit_rounds for several fits at once (Alg. 1 rounds of independent
+ * Big-means problems, e.g. groups of competing workers with different k over
+ * the same data): every round of every fit runs in ONE launch of the worker
+ * kernel, each fit's workers planned together (see bm_set_worker_groups), so
+ * workers of different fits share the GPU in one persistent grid.  Each fit's
+ * results are identical to running it alone.  Requirements: 1 <= nfits <= 16
+ * distinct fits on the current device whose n round up to the same padded
+ * width (4, 8, 16, 32 or 64), no wall-clock budget, at most 160 workers in
+ * all (else BM_EINVAL).  The work is enqueued on fits[0]'s stream; the other
+ * fits' streams are ordered before it at the start and after it at the end.
+ * Returns after the rounds have completed, with the first failing fit's
+ * status. */
+bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t rounds);
 bm_status bm_fit_finish(bm_fit_ctx* ctx, float* C_out_dev, int32_t* labels_out_dev,
                         bm_report* report_out);
 /* Counters and phase times so far (no final recheck); f_full and

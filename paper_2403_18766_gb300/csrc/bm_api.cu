@@ -266,7 +266,7 @@ struct bm_fit_ctx {
     int max_cs = 8;
     cudaEvent_t ev_fork = nullptr;
     // phase timing: event pairs around each launch, summed when the stream syncs
-    struct Span { cudaEvent_t a, b; int kind; cudaStream_t st; };
+    struct Span { cudaEvent_t a, b; int kind; cudaStream_t st; bool ended; };
     std::vector<Span> spans;
     std::vector<cudaEvent_t> pool;
     double t_worker = 0, t_full = 0, t_sample = 0;
@@ -354,18 +354,26 @@ cudaEvent_t take_event(bm_fit_ctx* c) {
 // Record the start of a timed launch; returns the span index.
 size_t span_begin(bm_fit_ctx* c, int kind, cudaStream_t st = nullptr) {
     if (!st) st = c->st;
-    bm_fit_ctx::Span sp{take_event(c), take_event(c), kind, st};
+    bm_fit_ctx::Span sp{take_event(c), take_event(c), kind, st, false};
     cudaEventRecord(sp.a, st);
     c->spans.push_back(sp);
     return c->spans.size() - 1;
 }
-void span_end(bm_fit_ctx* c, size_t i) { cudaEventRecord(c->spans[i].b, c->spans[i].st); }
+void span_end(bm_fit_ctx* c, size_t i) {
+    if (i >= c->spans.size()) return;
+    cudaEventRecord(c->spans[i].b, c->spans[i].st);
+    c->spans[i].ended = true;
+}
 // After a stream sync: fold the finished spans into the phase totals.
 // Spans on other streams (the sampling stream) may still be running: those
 // stay queued until they complete.
 void collect_spans(bm_fit_ctx* c) {
     std::vector<bm_fit_ctx::Span> pending;
     for (auto& sp : c->spans) {
+        if (!sp.ended) {                       // still open (its end is not recorded yet)
+            pending.push_back(sp);
+            continue;
+        }
         float ms = 0.f;
         const cudaError_t e = cudaEventElapsedTime(&ms, sp.a, sp.b);
         if (e == cudaErrorNotReady) {
@@ -373,6 +381,7 @@ void collect_spans(bm_fit_ctx* c) {
             pending.push_back(sp);
             continue;
         }
+        if (e != cudaSuccess) cudaGetLastError();   // a span that cannot be timed is dropped
         if (e == cudaSuccess) {
             if (sp.kind == 0) { c->t_worker += ms * 1e-3; c->n_worker++; }
             else if (sp.kind == 2) { c->t_sample += ms * 1e-3; }
@@ -570,84 +579,94 @@ bm_status ensure_streams(bm_fit_ctx* c) {
     return BM_OK;
 }
 
-// The launch plan of one round: every worker of the fit in one launch.
-//  * Groups (cooperative launch, clusters of kGroupCs CTAs): when every
-//    worker gets a cluster and the whole grid can be resident at once, the
-//    clusters left over go, one at a time, to the worker with the most
-//    sample rows per CTA, so a large sample spreads over several clusters
-//    (up to kMaxGroup) that add up their exact partial sums in global
-//    memory; rows per CTA then stay about equal across workers.
-//  * Otherwise (more workers than resident clusters, groups disabled, or
-//    512-thread CTAs requested): one cluster per worker, all of one size
-//    (for the largest sample), launched together; clusters that do not fit
-//    at once start as others finish (they never wait on one another).
+// The launch plan of one round: every worker of the fits in one launch.
+//  * Groups (cooperative launch, clusters of 8 CTAs, or 4 when there are
+//    more workers than resident clusters of 8): when every worker gets a
+//    cluster and the whole grid can be resident at once, the clusters left
+//    over go, one at a time, to the worker with the most sample rows per
+//    CTA, so a large sample spreads over several clusters (up to kMaxGroup)
+//    that add up their exact partial sums in global memory; rows per CTA
+//    then stay about equal across workers.
+//  * Otherwise (more workers than resident clusters, groups disabled or
+//    unavailable, or 512-thread CTAs requested): one cluster per worker, all
+//    of one size (for the largest sample), launched together; clusters that
+//    do not fit at once start as others finish (they never wait on one
+//    another).
 // Clusters are ordered by decreasing sample size.  Returns the clusters.
-int plan_round(bm_fit_ctx* c, const std::vector<long long>& sz, WorkerArgs& a) {
-    const int W = c->pol.workers;
-    std::vector<int> order(W);
-    for (int w = 0; w < W; ++w) order[w] = w;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sz[x] > sz[y]; });
-    const long long smax = sz[order[0]];
-    const long long cap = rows_cap(c->np, c->k);
-    if (c->xpart && c->groups_ok && W <= kMaxLaunchClusters && !g_big_tpb.load() && !g_no_groups.load()) {
-        std::vector<int> G(W, 1);
-        int total = W;
-        const size_t base = worker_smem(c->np, c->k);
-        auto rows_of = [&](int w) { return (sz[w] + (long long)G[w] * kGroupCs - 1) / ((long long)G[w] * kGroupCs); };
+struct PlanItem { int fit; int w; long long s; };
+
+int plan_launch(const std::vector<bm_fit_ctx*>& fits, std::vector<PlanItem> items, WorkerArgs& a) {
+    const int nw = (int)items.size();
+    std::stable_sort(items.begin(), items.end(), [](const PlanItem& x, const PlanItem& y) { return x.s > y.s; });
+    const bm_fit_ctx* c0 = fits[0];
+    int kmax = 0;
+    bool groups = !g_big_tpb.load() && !g_no_groups.load() && nw <= kMaxLaunchClusters;
+    for (const bm_fit_ctx* c : fits) {
+        kmax = std::max(kmax, c->k);
+        groups = groups && c->xpart && c->groups_ok;
+    }
+    const long long smax = items[0].s;
+    const long long cap = rows_cap(c0->np, kmax);
+    const size_t base = worker_smem(c0->np, kmax);
+    a.k_smem = kmax;
+    for (int gcs = kGroupCs; groups && gcs >= 4; gcs /= 2) {
+        std::vector<int> G(nw, 1);
+        int total = nw;
+        auto rows_of = [&](int i) { return (items[i].s + (long long)G[i] * gcs - 1) / ((long long)G[i] * gcs); };
         // capacity with the bucket memory of the current plan (it only
         // shrinks as groups grow, so the capacity only grows)
         int capacity = 0;
         for (int pass = 0; pass < 3; ++pass) {
             long long rows = 0;
-            for (int w = 0; w < W; ++w) rows = std::max(rows, rows_of(w));
-            capacity = std::min(worker_active_clusters(c->np, kGroupCs, base + bucket_smem_bytes((int)rows)),
+            for (int i = 0; i < nw; ++i) rows = std::max(rows, rows_of(i));
+            capacity = std::min(worker_active_clusters(c0->np, gcs, base + bucket_smem_bytes((int)rows)),
                                 kMaxLaunchClusters);
             while (total < capacity) {
                 int best = -1;
-                for (int w = 0; w < W; ++w)
-                    if (G[w] < kMaxGroup && (best < 0 || rows_of(w) > rows_of(best))) best = w;
+                for (int i = 0; i < nw; ++i)
+                    if (G[i] < kMaxGroup && (best < 0 || rows_of(i) > rows_of(best))) best = i;
                 if (best < 0 || rows_of(best) <= 256) break;
                 G[best]++;
                 total++;
             }
         }
         long long rows = 0;
-        for (int w = 0; w < W; ++w) rows = std::max(rows, rows_of(w));
-        if (W <= capacity && total <= capacity && rows <= cap) {
+        for (int i = 0; i < nw; ++i) rows = std::max(rows, rows_of(i));
+        if (nw <= capacity && total <= capacity && rows <= cap) {
             int ci = 0;
-            for (int w : order)
-                for (int q = 0; q < G[w]; ++q)
-                    a.cmap[ci++] = (unsigned)w | ((unsigned)q << 16) | ((unsigned)G[w] << 24);
+            for (int i = 0; i < nw; ++i)
+                for (int q = 0; q < G[i]; ++q)
+                    a.cmap[ci++] = (unsigned)items[i].w | ((unsigned)items[i].fit << 12) | ((unsigned)q << 16) |
+                                   ((unsigned)G[i] << 24);
             a.ncl = ci;
-            a.cs = kGroupCs;
+            a.cs = gcs;
             a.coop = 1;
             a.rows_cta = (int)rows;
             a.tpb = 256;
             return ci;
         }
     }
-    a.cs = cluster_size(smax, c->max_cs, c->rows_per_cta, cap);
+    a.cs = cluster_size(smax, c0->max_cs, c0->rows_per_cta, cap);
     a.rows_cta = (int)((smax + a.cs - 1) / a.cs);
     a.coop = 0;
-    a.tpb = (g_big_tpb.load() && a.cs == c->max_cs && smax > (long long)a.cs * c->rows_per_cta) ? 512 : 256;
-    if (W <= kMaxLaunchClusters) {
-        for (int i = 0; i < W; ++i) a.cmap[i] = (unsigned)order[i] | (1u << 24);
-        a.ncl = W;
+    a.tpb = (fits.size() == 1 && g_big_tpb.load() && a.cs == c0->max_cs && smax > (long long)a.cs * c0->rows_per_cta)
+                ? 512 : 256;
+    if (nw <= kMaxLaunchClusters) {
+        for (int i = 0; i < nw; ++i) a.cmap[i] = (unsigned)items[i].w | ((unsigned)items[i].fit << 12) | (1u << 24);
+        a.ncl = nw;
     } else {
-        a.ncl = 0;                                  // worker = cluster index
+        a.ncl = 0;                                  // worker = cluster index (one fit)
         a.worker_base = 0;
     }
-    return W;
+    return nw;
 }
 
-// Rounds [r0, r1) for every worker: the round's samples (drawn ahead on the
-// sampling stream, or now), then one launch of the worker kernel for all
-// workers (plan_round), then the next round's samples on the sampling stream
-// while the workers run.
-bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
+// The samples of round r0 of fit c ready on c->st: drawn ahead on the
+// sampling stream, or drawn now (and L read back first for the exploit
+// policy, whose sizes depend on it).
+bm_status round_samples(bm_fit_ctx* c, int r0) {
     bm_status s;
     if ((s = ensure_streams(c))) return s;
-    if (r1 != r0 + 1) return fail(BM_EINTERNAL, "one round per launch");
     const int parity = r0 & 1;
     if (c->pol.exploit > 0) {                   // sizes of this round depend on L so far
         Globals h;
@@ -655,7 +674,6 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         c->L_sum0 = (long long)h.L_sum;
         c->L_len0 = (long long)h.accepts;
     }
-    const size_t sp = span_begin(c, 0);
     if (c->prefetched == r0) {
         CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));           // drawn ahead on the sampling stream
     } else {
@@ -668,25 +686,17 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         c->n_kernels++;
     }
     c->prefetched = -1;
-    std::vector<long long> sz(c->pol.workers, 0);
-    for (int w = 0; w < c->pol.workers; ++w)
-        for (int t = r0; t < r1; ++t) sz[w] = std::max(sz[w], size_of(c, w, t));
-    WorkerArgs a = make_args(c, kModeRounds, parity);
-    a.round_begin = r0;
-    a.round_end = r1;
-    a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
-    const int clusters = plan_round(c, sz, a);
-    if (a.coop) CU(cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, c->st));   // barriers, aborts
-    CU(cudaEventRecord(c->ev_fork, c->st));
-    CU(launch_worker(c->np, a, clusters, c->st));
-    c->n_kernels++;
-    c->last_groups = a.coop ? clusters : 0;
-    // Draw the next round's samples into the other half while the workers
-    // run; that half was last read by the previous round, which finished
-    // before ev_fork.
+    return BM_OK;
+}
+
+// After the worker launch of round r0 (already enqueued on c->st): draw the
+// next round's samples into the other half on the sampling stream while the
+// workers run; that half was last read by the previous round, which finished
+// before ev_fork.
+bm_status round_prefetch(bm_fit_ctx* c, int r0) {
     if (r0 + 1 < c->rounds_planned && c->pol.exploit == 0) {
         CU(cudaStreamWaitEvent(c->sst, c->ev_fork, 0));
-        SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, parity ^ 1);
+        SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, (r0 + 1) & 1);
         sa.rnd = r0 + 1;
         const size_t sp_s = span_begin(c, 2, c->sst);
         CU(launch_sample(c->np, sa, c->jobs, c->sst));
@@ -695,6 +705,31 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
         c->n_kernels++;
         c->prefetched = r0 + 1;
     }
+    return BM_OK;
+}
+
+// Round r0 of every worker of fit c: the round's samples, one launch of the
+// worker kernel for all workers (plan_launch), the next round's samples.
+bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
+    bm_status s;
+    if (r1 != r0 + 1) return fail(BM_EINTERNAL, "one round per launch");
+    // (round_samples may read the globals back, which folds the finished
+    // timing spans: no span of this round is open before it)
+    if ((s = round_samples(c, r0))) return s;
+    const size_t sp = span_begin(c, 0);
+    std::vector<PlanItem> items;
+    for (int w = 0; w < c->pol.workers; ++w) items.push_back({0, w, size_of(c, w, r0)});
+    WorkerArgs a = make_args(c, kModeRounds, r0 & 1);
+    a.round_begin = r0;
+    a.round_end = r1;
+    a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
+    const int clusters = plan_launch({c}, items, a);
+    if (a.coop) CU(cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, c->st));   // barriers, aborts
+    CU(cudaEventRecord(c->ev_fork, c->st));
+    CU(launch_worker(c->np, a, clusters, c->st));
+    c->n_kernels++;
+    c->last_groups = a.coop ? clusters : 0;
+    if ((s = round_prefetch(c, r0))) return s;
     span_end(c, sp);
     return BM_OK;
 }
@@ -948,6 +983,103 @@ bm_status bm_fit_rounds(bm_fit_ctx* c, int32_t rounds) {
     Globals h;
     if ((s = read_globals(c, &h))) return s;
     return status_from_flags(h);
+}
+
+bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t rounds) {
+    if (!fits || nfits < 1 || nfits > 16) return fail(BM_EINVAL, "nfits = %d out of range [1, 16]", nfits);
+    if (rounds < 0) return fail(BM_EINVAL, "rounds < 0");
+    int total = 0;
+    for (int i = 0; i < nfits; ++i) {
+        if (!fits[i]) return fail(BM_EINVAL, "fits[%d] is NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (fits[j] == fits[i]) return fail(BM_EINVAL, "fits[%d] repeats fits[%d]", i, j);
+        if (fits[i]->np != fits[0]->np)
+            return fail(BM_EINVAL, "fits[%d] has another padded width (n = %d vs %d)", i, fits[i]->n, fits[0]->n);
+        if (fits[i]->bud.seconds > 0) return fail(BM_EINVAL, "fits[%d] has a wall-clock budget", i);
+        total += fits[i]->pol.workers;
+    }
+    if (nfits == 1) return bm_fit_rounds(fits[0], rounds);
+    if (total > kMaxLaunchClusters) return fail(BM_EINVAL, "%d workers in all above %d", total, kMaxLaunchClusters);
+    if (rounds == 0) return BM_OK;
+    // Everything runs on the first fit's stream: the other fits' streams are
+    // joined into it now and wait for it at the end.
+    cudaStream_t st = fits[0]->st;
+    std::vector<cudaStream_t> own(nfits);
+    cudaEvent_t ev = nullptr;
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    struct EvGuard { cudaEvent_t e; ~EvGuard() { cudaEventDestroy(e); } } evg{ev};
+    for (int i = 0; i < nfits; ++i) {
+        own[i] = fits[i]->st;
+        if (i > 0) {
+            CU(cudaEventRecord(ev, own[i]));
+            CU(cudaStreamWaitEvent(st, ev, 0));
+        }
+        fits[i]->st = st;
+    }
+    void* dargs = nullptr;
+    bm_status s = BM_OK;
+    if (lib_alloc(&dargs, sizeof(WorkerArgs) * nfits, st) != cudaSuccess) {
+        cudaGetLastError();
+        s = fail(BM_ENOMEM, "arguments of a batched launch");
+    }
+    std::vector<WorkerArgs> hargs(nfits);
+    for (int r = 0; r < rounds && s == BM_OK; ++r) {
+        std::vector<PlanItem> items;
+        for (int i = 0; i < nfits && s == BM_OK; ++i) {
+            bm_fit_ctx* c = fits[i];
+            if ((s = round_samples(c, c->rounds_run))) break;
+            for (int w = 0; w < c->pol.workers; ++w) items.push_back({i, w, size_of(c, w, c->rounds_run)});
+        }
+        if (s) break;
+        WorkerArgs plan;
+        memset(&plan, 0, sizeof plan);
+        std::vector<bm_fit_ctx*> fv(fits, fits + nfits);
+        const int clusters = plan_launch(fv, items, plan);
+        for (int i = 0; i < nfits; ++i) {
+            bm_fit_ctx* c = fits[i];
+            WorkerArgs& a = hargs[i];
+            a = make_args(c, kModeRounds, c->rounds_run & 1);
+            a.round_begin = c->rounds_run;
+            a.round_end = c->rounds_run + 1;
+            a.cs = plan.cs; a.rows_cta = plan.rows_cta; a.ncl = plan.ncl; a.coop = plan.coop;
+            a.tpb = 256; a.k_smem = plan.k_smem;
+            memcpy(a.cmap, plan.cmap, sizeof a.cmap);
+            a.batch = (const WorkerArgs*)dargs;
+            if (a.coop && cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, st) != cudaSuccess)
+                s = fail(BM_ECUDA, "barrier reset");
+        }
+        if (s) break;
+        // pageable source: the call returns once the arguments are staged,
+        // and the copy runs after the previous round's launch on st
+        if (cudaMemcpyAsync(dargs, hargs.data(), sizeof(WorkerArgs) * nfits, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess) { s = fail(BM_ECUDA, "arguments of a batched launch"); break; }
+        const size_t sp = span_begin(fits[0], 0);
+        for (int i = 0; i < nfits; ++i) cudaEventRecord(fits[i]->ev_fork, st);
+        const cudaError_t e = launch_worker(fits[0]->np, hargs[0], clusters, st);
+        span_end(fits[0], sp);
+        if (e != cudaSuccess) { s = fail(BM_ECUDA, "batched worker launch: %s", cudaGetErrorString(e)); break; }
+        fits[0]->n_kernels++;
+        for (int i = 0; i < nfits && s == BM_OK; ++i) {
+            bm_fit_ctx* c = fits[i];
+            c->last_groups = plan.coop ? clusters : 0;
+            if ((s = round_prefetch(c, c->rounds_run))) break;
+            c->rounds_run += 1;
+            if (c->bud.eval_full_each_round) s = run_fullpass(c, c->fhat, nullptr, 1);
+        }
+    }
+    if (dargs) cudaFreeAsync(dargs, st);
+    cudaEventRecord(ev, st);
+    for (int i = 0; i < nfits; ++i) {
+        fits[i]->st = own[i];
+        if (i > 0) cudaStreamWaitEvent(own[i], ev, 0);
+    }
+    if (s) return s;
+    for (int i = 0; i < nfits; ++i) {
+        Globals h;
+        if ((s = read_globals(fits[i], &h))) return s;
+        if ((s = status_from_flags(h))) return s;
+    }
+    return BM_OK;
 }
 
 bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep) {

@@ -41,12 +41,17 @@ struct WorkerArgs {
     int rows_cta;                     // most sample rows of one CTA in a Lloyd run of this launch
                                       // (sizes the label buckets in shared memory; 0: no Lloyd)
     // cluster map (ncl > 0): cluster c of the launch works for worker
-    // cmap[c] & 0xffff, as cluster (cmap[c] >> 16) & 0xff of a group of
-    // cmap[c] >> 24 clusters; ncl = 0: cluster c is worker worker_base + c
-    // alone
+    // cmap[c] & 0xfff of fit (cmap[c] >> 12) & 0xf, as cluster
+    // (cmap[c] >> 16) & 0xff of a group of cmap[c] >> 24 clusters; ncl = 0:
+    // cluster c is worker worker_base + c alone
     int ncl;
     int coop;                         // host: launch cooperatively (all CTAs resident at once)
+    int k_smem;                       // host: k that sizes the launch's shared memory (0: k)
     unsigned cmap[kMaxLaunchClusters];
+    // a launch for several fits (same padded width): the arguments of fit f
+    // are batch[f] (device memory, each with this launch's cs, rows_cta,
+    // ncl and cmap); null: a launch for this fit alone
+    const WorkerArgs* batch;
     // group exchange in global memory (per worker; two parity halves)
     long long* xpart;                 // W x 2 x kMaxGroup x k x NP x 3 words
     int* xcnt;                        // W x 2 x kMaxGroup x k counts

@@ -99,7 +99,7 @@ struct Worker {
         const int ci = blockIdx.x / cs;
         if (a.ncl > 0) {
             const unsigned e = a.cmap[ci];
-            w = (int)(e & 0xffffu);
+            w = (int)(e & 0xfffu);
             gi = (int)((e >> 16) & 0xffu);
             G = (int)(e >> 24);
         } else {
@@ -914,8 +914,11 @@ struct Worker {
 
 // trials > 3 would need more broadcast slots; the host caps it at 3.
 
-template <int NP, int TPB>
-__global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs a) {
+// BATCH: a launch for several fits, whose arguments are read from device
+// memory (p.batch[fit of the cluster]); otherwise the kernel parameter itself.
+template <int NP, int TPB, bool BATCH>
+__global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const __grid_constant__ WorkerArgs p) {
+    const WorkerArgs& a = BATCH ? p.batch[(p.cmap[blockIdx.x / p.cs] >> 12) & 0xfu] : p;
     Worker<NP, TPB> W(a, cg::this_cluster());
     if (a.glob->nonfinite) return;            // uniform: read before any barrier
     const int w = W.w;
@@ -1062,10 +1065,10 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const WorkerArgs
 template <int NP>
 int worker_max_cluster_t(int k) {
     const size_t smem = worker_smem_bytes<NP>(k);
-    if (allow_max_smem((const void*)worker_kernel<NP, 256>) != cudaSuccess ||
-        allow_max_smem((const void*)worker_kernel<NP, 512>) != cudaSuccess ||
-        cudaFuncSetAttribute(worker_kernel<NP, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-        cudaFuncSetAttribute(worker_kernel<NP, 512>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (allow_max_smem((const void*)worker_kernel<NP, 256, false>) != cudaSuccess ||
+        allow_max_smem((const void*)worker_kernel<NP, 512, false>) != cudaSuccess ||
+        cudaFuncSetAttribute(worker_kernel<NP, 256, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+        cudaFuncSetAttribute(worker_kernel<NP, 512, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -1081,7 +1084,7 @@ int worker_max_cluster_t(int k) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, worker_kernel<NP, 256>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, worker_kernel<NP, 256, false>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 8;
     }
@@ -1096,8 +1099,8 @@ int worker_active_clusters_t(int cs, size_t smem) {
     const auto key = std::make_pair(cs, smem);
     const auto it = memo.find(key);
     if (it != memo.end()) return it->second;
-    if (allow_max_smem((const void*)worker_kernel<NP, 256>) != cudaSuccess ||
-        (cs > 8 && cudaFuncSetAttribute(worker_kernel<NP, 256>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+    if (allow_max_smem((const void*)worker_kernel<NP, 256, false>) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(worker_kernel<NP, 256, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                        cudaSuccess)) {
         cudaGetLastError();
         return 0;
@@ -1114,7 +1117,7 @@ int worker_active_clusters_t(int cs, size_t smem) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, worker_kernel<NP, 256>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&ncl, worker_kernel<NP, 256, false>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         ncl = 0;
     }
@@ -1122,13 +1125,13 @@ int worker_active_clusters_t(int cs, size_t smem) {
     return ncl;
 }
 
-template <int NP, int TPB>
+template <int NP, int TPB, bool BATCH>
 cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st) {
-    const size_t smem = worker_smem_bytes<NP>(a.k) + bucket_smem_bytes(a.rows_cta);
-    cudaError_t e = allow_max_smem((const void*)worker_kernel<NP, TPB>);
+    const size_t smem = worker_smem_bytes<NP>(a.k_smem > 0 ? a.k_smem : a.k) + bucket_smem_bytes(a.rows_cta);
+    cudaError_t e = allow_max_smem((const void*)worker_kernel<NP, TPB, BATCH>);
     if (e != cudaSuccess) return e;
     if (a.cs > 8) {
-        e = cudaFuncSetAttribute(worker_kernel<NP, TPB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(worker_kernel<NP, TPB, BATCH>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -1145,13 +1148,15 @@ cudaError_t launch_worker_tpb(const WorkerArgs& a, int clusters, cudaStream_t st
     attr[1].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = a.coop ? 2 : 1;
-    return cudaLaunchKernelEx(&cfg, worker_kernel<NP, TPB>, a);
+    return cudaLaunchKernelEx(&cfg, worker_kernel<NP, TPB, BATCH>, a);
 }
 
 // a.tpb = 512 runs the worker with 512-thread CTAs (one per SM), else 256.
 template <int NP>
 cudaError_t launch_worker_t(const WorkerArgs& a, int clusters, cudaStream_t st) {
-    return a.tpb == 512 ? launch_worker_tpb<NP, 512>(a, clusters, st) : launch_worker_tpb<NP, 256>(a, clusters, st);
+    if (a.batch) return launch_worker_tpb<NP, 256, true>(a, clusters, st);
+    return a.tpb == 512 ? launch_worker_tpb<NP, 512, false>(a, clusters, st)
+                        : launch_worker_tpb<NP, 256, false>(a, clusters, st);
 }
 
 }  // namespace bm

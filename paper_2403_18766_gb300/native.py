@@ -92,6 +92,7 @@ SIGNATURES = {
     "bigmeans_fit_host": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
     "bm_fit_create": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_p)]),
     "bm_fit_rounds": (_i32, [_p, _i32]),
+    "bm_fit_rounds_batch": (_i32, [ctypes.POINTER(_p), _i32, _i32]),
     "bm_fit_finish": (_i32, [_p, _p, _p, _RP]),
     "bm_fit_destroy": (None, [_p]),
     "bm_fit_report": (_i32, [_p, _RP]),
@@ -251,6 +252,13 @@ class FitSession:
 
     def __del__(self):
         self.close()
+
+
+def rounds_batch(sessions, r):
+    """bm_fit_rounds_batch: the next r rounds of several FitSessions, every
+    round of all of them in one worker launch (on the first session's stream)."""
+    arr = (ctypes.c_void_p * len(sessions))(*[sess.ctx.value for sess in sessions])
+    _check(lib.bm_fit_rounds_batch(arr, len(sessions), int(r)))
 
 
 def sample(seed, purpose, worker, rnd, pss, m, s, device="cuda", stream=None):

@@ -378,3 +378,38 @@ def test_time_budget_with_worker_groups():
     C, Y, rep = native.fit(X, 6, pol, bud, seed=2)
     assert rep["rounds_done"] >= 1 and np.isfinite(rep["f_full"]) and rep["f_full"] > 0
     assert int(Y.min()) >= 0 and int(Y.max()) < 6
+
+
+def test_batched_fits_in_one_launch_equal_the_oracle():
+    """Workload-3 shape, reduced: three groups of competing workers with
+    k = 10 / 25 / 50 on one data set (4e6 x 32 rows cut to 2e5), octave-uniform
+    sample sizes; every round of all three fits runs in one worker launch
+    (bm_fit_rounds_batch).  Each group equals its own oracle run."""
+    X = workload("gmm_4m_n32_k50o", m=200_000)
+    Xd = _t(X)
+    groups = ((10, 3), (25, 2), (50, 2))
+    bud = dict(rounds=2, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    pols = {k: dict(s_min=2000, s_max=20_000, workers=W, passes=2, kind=1) for k, W in groups}
+    sess = [native.FitSession(Xd, k, native.make_policy(**pols[k]), native.make_budget(**bud), seed=300 + k)
+            for k, _ in groups]
+    native.rounds_batch(sess, 1)
+    native.rounds_batch(sess, 1)
+    for s_, (k, _) in zip(sess, groups):
+        C, Y, rep = s_.finish()
+        s_.close()
+        ref = obm.bigmeans(X, k, pols[k], bud, seed=300 + k)
+        _assert_same(C.cpu().numpy(), Y.cpu().numpy(), rep, ref)
+        assert rep["lloyd_iters"] == ref["log"]["lloyd_iters"]
+
+
+def test_batched_fits_reject_mixed_widths():
+    X = _t(gaussian_mixture(20_000, 8, 4, seed=36))
+    X2 = _t(gaussian_mixture(20_000, 20, 4, seed=37))
+    pol = native.make_policy(s_min=500, s_max=4000, workers=2, passes=1)
+    a = native.FitSession(X, 4, pol, native.make_budget(rounds=1), seed=1)
+    b = native.FitSession(X2, 4, pol, native.make_budget(rounds=1), seed=1)
+    with pytest.raises(native.BigmeansError) as e:
+        native.rounds_batch([a, b], 1)
+    assert e.value.status == native.BM_EINVAL
+    a.close()
+    b.close()
