@@ -138,10 +138,29 @@ def _traffic_for(kernel_sources):
     return (ent if ent else None), digest
 
 
-def cpu_baseline(X, seconds_target=20.0):
-    """The oracle as it stands, on a bounded sample of the same workload: one
-    worker, p passes per round, rounds doubled until about seconds_target/2."""
+def _oracle_worker_run(args):
+    """One 1-worker oracle fit of the headline workload (spawned process)."""
+    rounds, seed = args
+    import time as _t
     from oracle import bigmeans as obm
+    from paper_2403_18766_gb300.synthetic import workload
+    X = workload(WORKLOAD)
+    t0 = _t.perf_counter()
+    res = obm.bigmeans(X, K_CLUSTERS, dict(POLICY, workers=1),
+                       dict(BUDGET, rounds=rounds, eval_full_each_round=False), seed=seed)
+    return res["log"]["pts_k"], _t.perf_counter() - t0
+
+
+def cpu_baseline(X, seconds_target=20.0, multi=True, checks=None):
+    """The oracle as it stands, on a bounded sample of the same workload: one
+    worker, p passes per round, rounds doubled until about seconds_target/2,
+    on one core; then (multi) one spawned process per worker, up to the
+    host's cores, each a 1-worker fit of that many rounds, timed together.
+    `checks` (optional) are GPU results to compare with the oracle's all-FP64
+    mode (pure64): the headline fit's final C, labels and f(C, X), and the
+    precision form on a slice of the 10^7 x 64 workload."""
+    from oracle import bigmeans as obm
+    from oracle import kmeans as okm
     rounds, res, dt = 1, None, 0.0
     while True:
         pol = dict(POLICY, workers=1)
@@ -153,10 +172,44 @@ def cpu_baseline(X, seconds_target=20.0):
             break
         rounds *= 2
     ptsk = res["log"]["pts_k"]
-    return {"value": ptsk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 worker x {rounds} rounds x {POLICY['passes']} passes of the same workload "
-                      f"({res['log']['lloyd_iters']} Lloyd updates, {ptsk:.3g} pts*k; time includes "
-                      f"sampling, K-means++, the recheck and the final full pass) in {dt:.1f} s"}
+    out = {"value": ptsk / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"1 worker x {rounds} rounds x {POLICY['passes']} passes of the same workload "
+                     f"({res['log']['lloyd_iters']} Lloyd updates, {ptsk:.3g} pts*k; time includes "
+                     f"sampling, K-means++, the recheck and the final full pass) in {dt:.1f} s"}
+    if multi:
+        import multiprocessing as mp
+        procs = max(1, min(POLICY["workers"], os.cpu_count() or 1))
+        r_each = max(1, rounds // 2)
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(procs) as pool:
+            parts = pool.map(_oracle_worker_run, [(r_each, 1 + i) for i in range(procs)])
+        wall = time.perf_counter() - t0
+        tot = sum(p[0] for p in parts)
+        out["multi"] = {"value": tot / wall, "unit": UNIT, "cores": procs, "kind": "oracle",
+                        "sample": f"{procs} spawned processes (one per worker, up to the host's cores), each a "
+                                  f"1-worker fit of {r_each} rounds x {POLICY['passes']} passes; wall time "
+                                  f"{wall:.1f} s including process start and data generation"}
+    if checks:
+        err = {}
+        h = checks.get("headline")
+        if h:
+            lab64, d64 = okm.assign(X, h["C"], mode="pure64")
+            f64 = okm.exact_sum(d64)
+            err["headline"] = {"f_rel": abs(h["f"] - f64) / f64,
+                               "label_mismatch": int((h["labels"] != lab64).sum()), "rows": int(X.shape[0]),
+                               "what": "final C of the timed fit: GPU f(C, X) and labels (exact mode) against "
+                                       "the FP64 oracle on the same C, all rows"}
+        pr = checks.get("precision")
+        if pr:
+            _, d64 = okm.assign(pr["X"], pr["C"], mode="pure64")
+            f64 = okm.exact_sum(d64)
+            err["precision"] = {k2: abs(v - f64) / f64 for k2, v in pr["f"].items()}
+            err["precision"]["rows"] = int(pr["X"].shape[0])
+            err["precision"]["what"] = ("f(C, X) on the first rows of the 10^7 x 64 workload (C of a short fit "
+                                        "on all rows) from each GPU form, against the FP64 oracle")
+        out["err_vs_pure64"] = err
+    return out
 
 
 def run_reference(args):
@@ -236,7 +289,7 @@ def run_ours(args):
     f_end = trace[-1][1]
     tto = next(((t, i + 1) for i, (t, f) in enumerate(trace) if f <= f_end * (1 + 1e-4)), (None, None))
     clk = clocks.stop()
-    C, _, rep_fin = sess.finish(labels=False)
+    C, Y_fin, rep_fin = sess.finish(labels=True)
     sess.close()
 
     t_local = sum(step_ms) / 1e3
@@ -244,7 +297,7 @@ def run_ours(args):
     ptsk_local = rows * K_CLUSTERS
     launches = rep1["kernel_launches"] - rep0["kernel_launches"]
     t_worker = rep1["t_worker_s"] - rep0["t_worker_s"]
-    n_worker = args.steps                       # one sampling + W worker launches per step
+    n_worker = args.steps                       # one worker launch (all W workers) per step
     t_full = rep1["t_fullpass_s"] - rep0["t_fullpass_s"]
     n_full = rep1["fullpass_launches"] - rep0["fullpass_launches"]
     if ws > 1:
@@ -264,11 +317,12 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak if alu_peak else None,
                 "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
-                "kernel": "round phase: sample_kernel<16> (all samples of the round) + "
-                          "worker_kernel<16> x W (K-means++, Lloyd, incumbent rule), timed together "
-                          "from fork to join",
+                "kernel": "worker_kernel<16>: one launch per round for all W workers (K-means++, Lloyd, "
+                          "incumbent rule; large samples as groups of clusters), CUDA events around the "
+                          "launch on its stream; the next round's sample_kernel<16> runs beside it on a "
+                          "second stream",
                 "algorithmic": "2*n*k flops per row assigned inside Lloyd; "
-                               f"{flops / max(n_worker, 1):.4g} flops per round phase",
+                               f"{flops / max(n_worker, 1):.4g} flops per launch",
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "source_digest": digest}
     bytes_full = m * n * 4.0
@@ -311,9 +365,22 @@ def run_ours(args):
                        "labels) from pinned host memory: copies, workspace setup, K-means++ of round 0 and "
                        "the final full pass inside; median of 3 calls"}
 
+    # the other configurations, one sub-object each (rank 0 of a 1-GPU run)
+    extras, checks = {}, {"headline": {"C": C.cpu().numpy(), "labels": Y_fin.cpu().numpy(),
+                                       "f": rep_fin["f_full"]}}
+    if rank == 0 and ws == 1 and not args.no_extras:
+        del Xd
+        torch.cuda.empty_cache()
+        extras["precision"], checks["precision"] = precision_bench(steps=5, warmup=3)
+        torch.cuda.empty_cache()
+        extras["batched"] = batched_bench(steps=5, warmup=3)
+        torch.cuda.empty_cache()
+        extras["serve"] = serve_bench(rate=20.0, n_jobs=40, warmup=3)
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(X)
+        cpu = cpu_baseline(X, checks=checks)
 
     if rank == 0:
         line = {"metric": METRIC, "value": ptsk / t_job, "unit": UNIT, "n_gpus": ws,
@@ -335,7 +402,11 @@ def run_ours(args):
                                                                    rep1["trace_cycles"])],
                            "inexact_terms": rep1["inexact_terms"],
                            "f_incumbent": rep1["f_incumbent"], "f_final": rep_fin["f_full"],
-                           "s_opt": rep_fin["s_opt"], "peaks": peak_src}}
+                           "s_opt": rep_fin["s_opt"], "peaks": peak_src,
+                           "worker_launches_per_round": 1}}
+        if cpu and "err_vs_pure64" in cpu:
+            line["err_vs_pure64"] = cpu["err_vs_pure64"]
+        line.update(extras)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -386,16 +457,36 @@ def run_kernel_mode(args):
     return 0
 
 
-def run_precision(args):
-    """Precision form of the full-data pass on the 10^7 x 64, k = 100 workload:
-    X packed once to BF16 (resident), then bm_assign_bf16 timed with CUDA
-    events (L2 flushed between calls) against the HBM roofline; the exact FP32
-    pass (bm_assign) on the same C is timed beside it, and the label
-    agreement and objective error of the precision form are reported."""
+def _timed(fn, steps, warmup, flush):
+    import torch
+    ts, out = [], None
+    for i in range(warmup + steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        if i >= warmup:
+            ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts), out
+
+
+def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
+    """Workload 4: precision form of the full-data pass on 10^7 x 64, k = 100
+    (100 Gaussians, Zipf(1.2) sizes): X packed once to BF16 (resident), then
+    bm_assign_bf16 (tau = 1e-3) timed with CUDA events (L2 flushed between
+    calls) against the HBM roofline; the exact FP32 pass (bm_assign) and the
+    certified variant on the same C are timed beside it, with the label
+    agreement and objective error against the exact pass.  Returns the
+    sub-object and, for the FP64 check of the CPU leg, each form's f on the
+    first `slice_rows` rows."""
     import torch
     from paper_2403_18766_gb300 import native
     from paper_2403_18766_gb300.synthetic import workload
-    X = workload("gmm_10m_n64_k100z", m=args.rows)
+    X = workload("gmm_10m_n64_k100z", m=rows)
     m, n = X.shape
     k = 100
     Xd = torch.from_numpy(X).cuda()
@@ -404,37 +495,31 @@ def run_precision(args):
                          native.make_budget(rounds=1), seed=3, labels=False)
     P = native.PackedBF16(Xd)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-
-    def timed(fn):
-        ts = []
-        for i in range(args.warmup + args.steps):
-            flush.fill_(1)
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            out = fn()
-            b.record()
-            torch.cuda.synchronize()
-            if i >= args.warmup:
-                ts.append(a.elapsed_time(b) / 1e3)
-        return statistics.median(ts), out
-
-    t_bf, (Yb, fb, rb) = timed(lambda: native.assign_bf16(P, C, tau=1e-3))
-    t_tc0, _ = timed(lambda: native.assign_bf16(P, C, tau=0.0))
-    t_ex, (Ye, fe, re_) = timed(lambda: native.assign(Xd, C))
-    t_ce, (Yc, fc, rc) = timed(lambda: native.assign_bf16(P, C, tau=1e-3, certified=True))
+    clocks = ClockSampler(0)
+    t_bf, (Yb, fb, rb) = _timed(lambda: native.assign_bf16(P, C, tau=1e-3), steps, warmup, flush)
+    t_tc0, _ = _timed(lambda: native.assign_bf16(P, C, tau=0.0), steps, warmup, flush)
+    t_ex, (Ye, fe, re_) = _timed(lambda: native.assign(Xd, C), steps, warmup, flush)
+    t_ce, (Yc, fc, rc) = _timed(lambda: native.assign_bf16(P, C, tau=1e-3, certified=True), steps, warmup, flush)
+    clk = clocks.stop()
+    # the same forms on the first rows, for the comparison with the FP64 oracle
+    ns = min(slice_rows, m)
+    Xs = Xd[:ns].contiguous()
+    Ps = native.PackedBF16(Xs)
+    fs = {"bf16_tau1e-3": native.assign_bf16(Ps, C, tau=1e-3)[1],
+          "bf16_certified": native.assign_bf16(Ps, C, tau=1e-3, certified=True)[1],
+          "exact_fp32": native.assign(Xs, C)[1]}
+    check = {"X": X[:ns].copy(), "C": C.cpu().numpy(), "f": fs}
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bytes_bf = m * (128 + 4 + 4)                 # packed row + norm + label
     line = {"metric": "precision-form full pass (labels + f)", "value": bytes_bf / t_bf / 1e9,
-            "unit": "GB/s", "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
+            "unit": "GB/s", "higher_is_better": True, "steps": steps, "warmup": warmup,
             "config": {"workload": f"gmm_10m_n64_k100z: m={m}, n=64, 100 Gaussians (Zipf 1.2), k=100",
                        "dtype": "bf16 distance tiles, FP32 accumulate (tcgen05), FP32 re-score",
                        "tau": 1e-3, "l2": "flushed between calls"},
             "roofline": {"bound": "hbm", "achieved": bytes_bf / t_bf / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": bytes_bf / t_bf / 1e9 / hbm, "traffic": None,
-                         "kernel": "tc_fullpass_kernel (tcgen05.mma kind::f16, 1-D TMA tiles)",
+                         "kernel": "tc_fullpass_kernel + rescore_kernel (tcgen05.mma kind::f16, 1-D bulk tiles)",
                          "algorithmic": "136 bytes per row (128 B packed row, 4 B norm, 4 B label)",
                          "peak_source": src},
             "ms_per_call": t_bf * 1e3, "exact_fp32_ms_per_call": t_ex * 1e3,
@@ -449,160 +534,205 @@ def run_precision(args):
             "certified": {"ms_per_call": t_ce * 1e3, "speedup_vs_exact_pass": t_ex / t_ce,
                           "rescored_rows": rc["rescored_rows"],
                           "label_mismatch_vs_exact": int((Yc != Ye).sum().item()),
-                          "f_rel_err_vs_exact": abs(fc - fe) / fe}}
+                          "f_rel_err_vs_exact": abs(fc - fe) / fe},
+            "clocks": clk}
+    del P, Ps, Xd, Xs
+    torch.cuda.empty_cache()
+    return line, check
+
+
+def run_precision(args):
+    line, _ = precision_bench(args.steps, args.warmup, args.rows)
     print(json.dumps(line))
     return 0
 
 
-def run_batched(args):
+def batched_bench(steps=5, warmup=3, rows=None):
     """Workload 3: 64 competing workers on one 4e6 x 32 mixture (50 Gaussians
     + 1% outliers), sample sizes octave-uniform (the integer stand-in for
     log-uniform) in [2000, 131072], k in {10, 25, 50} per worker.  Workers
     with different k cannot compete on one objective, so they form three
     Big-means groups (22 / 21 / 21 workers, k assigned round-robin), each its
-    own fit; the three fits run at once from three host threads (their
-    kernels overlap on the GPU).  The cluster tile is autotuned first.  A step
-    is one round of all 64 workers; the value is Lloyd pts*k/s over all
-    groups, device-resident X, L2 flushed between steps."""
-    import threading
+    own fit; every round of all three fits is one worker launch
+    (bm_fit_rounds_batch).  The cluster tile of the one-cluster-per-worker
+    plan is autotuned, then timed against the worker-group plan; the faster
+    runs the timed steps.  A step is one round of all 64 workers; the value
+    is Lloyd pts*k/s over all groups, device-resident X, L2 flushed between
+    steps."""
     import torch
     from paper_2403_18766_gb300 import native
     from paper_2403_18766_gb300.synthetic import workload
-    X = workload("gmm_4m_n32_k50o", m=args.rows)
+    X = workload("gmm_4m_n32_k50o", m=rows)
     m, n = X.shape
     Xd = torch.from_numpy(X).cuda()
     groups = [(10, 22), (25, 21), (50, 21)]
     pols = {k: native.make_policy(s_min=2000, s_max=131072, workers=w, passes=10, kind=1) for k, w in groups}
-    total_rounds = args.warmup + args.steps
-    tuned, tune_ms = native.autotune_rows_per_cta(Xd, 25, pols[25], native.make_budget(rounds=2), seed=5,
-                                                  candidates=(1024, 2048, 4096, 8192))
-    sess = {k: native.FitSession(Xd, k, pols[k], native.make_budget(rounds=total_rounds), seed=300 + k,
-                                 stream=torch.cuda.Stream()) for k, _ in groups}
+    native.set_worker_groups(0)
+    try:
+        tuned, tune_ms = native.autotune_rows_per_cta(Xd, 25, pols[25], native.make_budget(rounds=2), seed=5,
+                                                      candidates=(1024, 2048, 4096, 8192))
+    finally:
+        native.set_worker_groups(1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def one_round():
-        errs = []
+    def sessions(rounds):
+        return [native.FitSession(Xd, k, pols[k], native.make_budget(rounds=rounds), seed=300 + k)
+                for k, _ in groups]
 
-        def run(k):
-            try:
-                sess[k].rounds(1)
-            except Exception as e:               # noqa: BLE001 - reported below
-                errs.append(e)
-        th = [threading.Thread(target=run, args=(k,)) for k, _ in groups]
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
-        if errs:
-            raise errs[0]
+    def one_round(sess):
+        native.rounds_batch(sess, 1)
 
-    for _ in range(args.warmup):
-        one_round()
-    rep0 = {k: sess[k].report() for k, _ in groups}
-    clocks = ClockSampler(0)
-    step_ms = []
-    for _ in range(args.steps):
-        flush.fill_(1)
+    # plan choice: two rounds each (the second one timed)
+    plan_ms = {}
+    for on in (1, 0):
+        native.set_worker_groups(on)
+        sess = sessions(2)
+        one_round(sess)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        one_round()
+        one_round(sess)
         torch.cuda.synchronize()
-        step_ms.append((time.perf_counter() - t0) * 1e3)
-    clk = clocks.stop()
-    rep1 = {k: sess[k].report() for k, _ in groups}
-    ptsk = sum((rep1[k]["assign_rows"] - rep0[k]["assign_rows"]) * k for k, _ in groups)
-    flops = sum(2.0 * n * k * (rep1[k]["assign_rows"] - rep0[k]["assign_rows"]) for k, _ in groups)
-    fin = {}
-    for k, _ in groups:
-        C, _, r = sess[k].finish(labels=False)
-        fin[k] = {"f_full": r["f_full"], "s_opt": r["s_opt"]}
-        sess[k].close()
-    native.set_rows_per_cta(0)
+        plan_ms["groups" if on else f"tile_{tuned}"] = (time.perf_counter() - t0) * 1e3
+        for s_ in sess:
+            s_.close()
+    use_groups = plan_ms["groups"] <= plan_ms[f"tile_{tuned}"]
+    native.set_worker_groups(1 if use_groups else 0)
+    sess = sessions(warmup + steps)
+    try:
+        for _ in range(warmup):
+            one_round(sess)
+        rep0 = [s_.report() for s_ in sess]
+        clocks = ClockSampler(0)
+        step_ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            one_round(sess)
+            b.record()
+            torch.cuda.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        clk = clocks.stop()
+        rep1 = [s_.report() for s_ in sess]
+        fin = {}
+        for s_, (k, _) in zip(sess, groups):
+            C, _, r = s_.finish(labels=False)
+            fin[str(k)] = {"f_full": r["f_full"], "s_opt": r["s_opt"]}
+    finally:
+        for s_ in sess:
+            s_.close()
+        native.set_worker_groups(1)
+        native.set_rows_per_cta(0)
+    ptsk = sum((r1["assign_rows"] - r0["assign_rows"]) * k for r0, r1, (k, _) in zip(rep0, rep1, groups))
+    flops = sum(2.0 * n * k * (r1["assign_rows"] - r0["assign_rows"]) for r0, r1, (k, _) in zip(rep0, rep1, groups))
     t = sum(step_ms) / 1e3
     peaks, src = _peaks()
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", NOMINAL_MAX_MHZ))
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    line = {"metric": "Lloyd pts\u00b7k/s (batched workers, workload 3)", "value": ptsk / t, "unit": UNIT,
-            "higher_is_better": True, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3 / args.steps, "dtype": "f32", "data": "synthetic",
+    return {"metric": "Lloyd pts·k/s (batched workers, workload 3)", "value": ptsk / t, "unit": UNIT,
+            "higher_is_better": True, "steps": steps, "warmup": warmup,
+            "ms_per_step": t * 1e3 / steps, "dtype": "f32", "data": "synthetic",
             "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": flops / t / 1e12 / alu_peak,
-                         "kernel": "worker_kernel<32> x 64 + sample_kernel<32> x 3 per step (wall time of the step)",
+                         "kernel": "worker_kernel<32> (one launch for the 64 workers of the 3 fits) + "
+                                   "sample_kernel<32> x 3 per step, CUDA events around the step",
                          "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
-            "autotune": {"rows_per_cta": tuned, "round_ms": tune_ms},
-            "groups": {str(k): fin[k] for k, _ in groups}, "clocks": clk,
+            "plan": {"chosen": "groups" if use_groups else f"tile_{tuned}", "second_round_ms": plan_ms,
+                     "autotune_round_ms": tune_ms, "tuned_rows_per_cta": tuned,
+                     "worker_launches_per_step": 1},
+            "groups": fin, "clocks": clk,
             "config": {"workload": f"gmm_4m_n32_k50o: m={m}, n={n}, 50 Gaussians + 1% outliers; 64 workers "
-                                   "as 3 groups k=10/25/50 (22/21/21), s octave-uniform in [2000, 131072], p=10",
+                                   "as 3 fits k=10/25/50 (22/21/21), s octave-uniform in [2000, 131072], p=10, "
+                                   "all in one worker launch per round",
                        "l2": "flushed between timed steps", "step": "one round of all 64 workers"}}
-    print(json.dumps(line))
+
+
+def run_batched(args):
+    print(json.dumps(batched_bench(args.steps, args.warmup, args.rows)))
     return 0
 
 
-def run_serve(args):
-    """Serving: Poisson arrivals of clustering jobs of mixed m, n, k on one
-    serving context (continuous batching under a device-memory budget).
-    Job data is generated before the clock starts and kept in pinned host
-    memory; each job's latency runs from its arrival (submit) to its result
-    on the host (H2D copy, Algorithm 1, full-data pass, D2H copy included)."""
+SERVE_N = (8, 32, 64)        # the stream's widths (128 is beyond the library's n <= 64)
+SERVE_K = (5, 10, 25, 100)
+
+
+def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
+    """Serving (workload 5): a Poisson stream of clustering jobs on one
+    serving context (continuous batching under a device-memory budget).  Job
+    shapes follow the stream: m log-uniform in [1e5, 2e7], n in SERVE_N, k in
+    {5, 10, 25, 100}, a mixture of 2k Gaussians with 0.5% outliers, FP32 or
+    BF16 storage (half of the jobs), W = 16 workers, T = 3 rounds, p = 10,
+    s in [1000, min(64000, m)].  Jobs draw their data from a pool of
+    `pool_size` data sets of such shapes, generated on the device before the
+    clock starts and kept in pinned host memory; a job's latency runs from its
+    arrival (submit) to its result on the host (H2D copy, Algorithm 1, the
+    full-data pass -- BF16 for BF16 jobs -- and the D2H copy included)."""
     import torch
     from paper_2403_18766_gb300 import native
-    from paper_2403_18766_gb300.synthetic import gaussian_mixture
-    g = np.random.default_rng(5005)
+    from paper_2403_18766_gb300.synthetic import gaussian_mixture_device
+    g = np.random.default_rng(seed)
     pool = []
-    for i in range(6):                                   # data sets the jobs draw from
-        m = int(round(10 ** g.uniform(5.0, np.log10(2e6))))
-        n = int(g.choice([8, 16, 32]))
-        pool.append(torch.from_numpy(gaussian_mixture(m, n, 20, seed=700 + i, outliers=0.005)).pin_memory())
-    n_jobs = max(8, args.steps * 8)
-    rate = float(args.rate)                              # jobs per second
+    for i in range(pool_size):
+        m = int(round(10 ** g.uniform(5.0, np.log10(2e7))))
+        n = int(g.choice(SERVE_N))
+        k = int(g.choice(SERVE_K))
+        Xh = gaussian_mixture_device(m, n, 2 * k, seed=700 + i, outliers=0.005).cpu().pin_memory()
+        pool.append((Xh, k))
+    torch.cuda.synchronize()
     gaps = g.exponential(1.0 / rate, n_jobs)
     arrivals = np.cumsum(gaps) - gaps[0]
     jobs = []
     for i in range(n_jobs):
-        X = pool[int(g.integers(len(pool)))]
-        k = int(g.choice([5, 10, 25]))
-        m = X.shape[0]
-        pol = native.make_policy(s_min=max(1000, 2 * k), s_max=min(32000, m), workers=8, passes=5)
-        jobs.append((X, k, pol, native.make_budget(rounds=2), 9000 + i))
+        Xh, k = pool[int(g.integers(len(pool)))]
+        m = Xh.shape[0]
+        pol = native.make_policy(s_min=max(1000, 2 * k), s_max=min(64000, m), workers=16, passes=10)
+        jobs.append((Xh, k, pol, native.make_budget(rounds=3), 9000 + i, bool(g.integers(2))))
     free, total = torch.cuda.mem_get_info()
-    budget = int(min(free * 0.6, 40 << 30))
-    ctx = native.ServeContext(budget, 6)
-    for X, k, pol, bud, seed in jobs[:args.warmup]:      # warm-up jobs (not timed)
-        ctx.wait(ctx.submit(X, k, pol, bud, seed))
+    budget = int(min(free * 0.6, 120 << 30))
+    ctx = native.ServeContext(budget, 4)
+    for Xh, k, pol, bud, sd, bf in jobs[:warmup]:          # warm-up jobs (not timed)
+        ctx.wait(ctx.submit(Xh, k, pol, bud, sd, bf16=bf))
     clocks = ClockSampler(0)
     t0 = time.perf_counter()
     ids = []
-    for (X, k, pol, bud, seed), at in zip(jobs, arrivals):
+    for (Xh, k, pol, bud, sd, bf), at in zip(jobs, arrivals):
         dt = at - (time.perf_counter() - t0)
         if dt > 0:
             time.sleep(dt)
-        ids.append((ctx.submit(X, k, pol, bud, seed), time.perf_counter() - t0))
-    res = [(ctx.wait(j), t_arr) for j, t_arr in ids]
+        ids.append(ctx.submit(Xh, k, pol, bud, sd, bf16=bf))
+    res = [ctx.wait(j) for j in ids]
     t_end = time.perf_counter() - t0
     clk = clocks.stop()
     st = ctx.stats()
     ctx.close()
-    # latency on the context's clock: done - submit (submit happens at the arrival)
-    lat = np.array([r["t_done_s"] - r["t_submit_s"] for r, _ in res])
-    qwait = np.array([r["t_admit_s"] - r["t_submit_s"] for r, _ in res])
-    ok = all(r["status"] == native.BM_OK for r, _ in res)
-    errors = sorted({r.get("error", "") for r, _ in res if r["status"] != native.BM_OK})
-    ptsk = sum(r["report"]["assign_rows"] * jobs[i][1] for i, (r, _) in enumerate(res))
-    line = {"metric": "p50/p99 job latency (serving, continuous batching)",
+    lat = np.array([r["t_done_s"] - r["t_submit_s"] for r in res])
+    qwait = np.array([r["t_admit_s"] - r["t_submit_s"] for r in res])
+    ok = all(r["status"] == native.BM_OK for r in res)
+    errors = sorted({r.get("error", "") for r in res if r["status"] != native.BM_OK})
+    ptsk = sum(r["report"]["assign_rows"] * jobs[i][1] for i, r in enumerate(res))
+    shapes = sorted({(int(p[0].shape[0]), int(p[0].shape[1]), p[1]) for p in pool})
+    return {"metric": "p50/p99 job latency (serving, continuous batching)",
             "value": float(np.percentile(lat, 99)) * 1e3, "unit": "ms (p99)", "higher_is_better": False,
             "p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
             "queue_wait_p50_ms": float(np.percentile(qwait, 50)) * 1e3,
-            "jobs": n_jobs, "all_ok": ok, "errors": errors[:3], "makespan_s": t_end, "jobs_per_s": n_jobs / t_end,
+            "jobs": n_jobs, "bf16_jobs": int(sum(j[5] for j in jobs)), "all_ok": ok, "errors": errors[:3],
+            "makespan_s": t_end, "jobs_per_s": n_jobs / t_end,
             "lloyd_ptsk_per_s": ptsk / t_end, "arrival_rate_per_s": rate,
             "peak_active": st["peak_active"], "peak_in_use_gb": st["peak_in_use_bytes"] / 1e9,
-            "budget_gb": budget / 1e9, "clocks": clk,
-            "config": {"workload": f"Poisson({rate:g}/s) jobs over 6 Gaussian-mixture data sets (m log-uniform "
-                                   "in [1e5, 2e6], n in {8, 16, 32}, 20 components + 0.5% outliers); "
-                                   "k in {5, 10, 25}; W=8, p=5, T=2 rounds, s in [max(1000, 2k), min(32000, m)]",
-                       "max_active": 6, "data": "synthetic, pinned host memory"}}
+            "budget_gb": budget / 1e9, "clocks": clk, "pool_shapes_m_n_k": shapes,
+            "config": {"workload": f"Poisson({rate:g}/s) jobs; m log-uniform in [1e5, 2e7], n in {list(SERVE_N)}, "
+                                   "k in {5, 10, 25, 100}, 2k Gaussians + 0.5% outliers, FP32 or BF16 storage; "
+                                   "W=16, p=10, T=3 rounds, s in [max(1000, 2k), min(64000, m)]",
+                       "max_active": 4, "data": f"synthetic, {pool_size} data sets in pinned host memory"}}
+
+
+def run_serve(args):
+    line = serve_bench(rate=args.rate, n_jobs=max(8, args.steps * 2), warmup=args.warmup)
     print(json.dumps(line))
-    return 0 if ok else 1
+    return 0 if line["all_ok"] else 1
 
 
 def main():
@@ -612,7 +742,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--rate", type=float, default=150.0, help="serve mode: job arrivals per second")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve mode: job arrivals per second")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only (no precision / batched / serve sub-objects)")
     ap.add_argument("--big-clusters", type=int, default=None, choices=[0, 1],
                     help="512-thread CTAs for the workers whose cluster is at the size cap")
     ap.add_argument("--workload", default=None, help="kernel modes: workload name (default: the headline's)")

@@ -435,6 +435,11 @@ bm_status bm_fit_footprint(int64_t m, int32_t n, int32_t k, const bm_sample_poli
  * asynchronous).  Times in bm_result are seconds since bm_ctx_create.
  * The runner threads start at the first bm_submit on the device current in
  * the submitting thread; bm_ctx_create itself makes no CUDA call.
+ * A job with storage = 1 (BF16) keeps, beside its FP32 master, X packed in
+ * BF16 on the device and takes its labels and f(C, X) from the tensor-core
+ * precision pass (bm_assign_bf16 with its tau); bm_result.f_full is that
+ * objective and report.f_full the exact-mode one of the same C.  Its
+ * footprint includes the packed copy (128 + 4 bytes per row, n <= 64).
  * Errors: BM_EINVAL for bad arguments or shapes (checked at submit),
  * BM_ENOMEM at submit for a job larger than the whole budget; a job's own
  * failure is its bm_result.status (message via bm_job_error).
@@ -451,6 +456,12 @@ typedef struct {
     uint64_t seed;
     float* C_out_host;           /* k x n                                      */
     int32_t* labels_out_host;    /* m, or NULL                                 */
+    int32_t storage;             /* 0: FP32; 1: X also held packed in BF16 for
+                                    the full-data pass (bm_pack_bf16), whose
+                                    labels and f come from bm_assign_bf16 with
+                                    the re-score bound `tau`; the samples and the
+                                    centroids still come from the FP32 master  */
+    float tau;                   /* storage 1: re-score rule of bm_assign_bf16  */
 } bm_job;
 typedef struct {
     int32_t status;              /* the job's status; BM_EAGAIN until done      */

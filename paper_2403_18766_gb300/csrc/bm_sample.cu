@@ -252,10 +252,11 @@ __global__ void __launch_bounds__(kSampleThreads, 1) sample_kernel(const SampleA
 template <int NP>
 static cudaError_t launch_sample_t(const SampleArgs& a, int jobs, cudaStream_t st) {
     const size_t smem = sample_smem_bytes(a.bitmap_words);
-    if (smem > 48 * 1024) {
-        const cudaError_t e = allow_max_smem((const void*)sample_kernel<NP>);
-        if (e != cudaSuccess) return e;
-    }
+    // every launch goes through allow_max_smem (which raises the limit once,
+    // under a lock): a launch from one host thread must not race with the
+    // attribute being set from another
+    const cudaError_t e = allow_max_smem((const void*)sample_kernel<NP>);
+    if (e != cudaSuccess) return e;
     sample_kernel<NP><<<jobs, kSampleThreads, smem, st>>>(a);
     return cudaGetLastError();
 }

@@ -45,11 +45,55 @@ struct Job {
     bm_status status = BM_OK;
     std::string error;
     bm_report report{};
+    double f_result = 0;           // f(C, X) of the job's full-data pass
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
 double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+namespace {
+
+// A BF16-stored job: the fit on the FP32 master (exact mode), then its
+// labels and objective from the BF16 tensor-core pass over the packed copy.
+bm_status run_bf16_job(const bm_job& s, cudaStream_t st, bm_report* rep, double* f_out) {
+    const int64_t m = s.m, m_pad = (m + 127) / 128 * 128;
+    float* Xd = nullptr; float* Cd = nullptr; int32_t* Ld = nullptr; float* norms = nullptr;
+    unsigned char* raw = nullptr;
+    bm_status r = BM_OK;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (r == BM_OK && cudaMallocAsync(p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            r = set_error(BM_ENOMEM, "device buffers of a BF16-stored job");
+        }
+    };
+    alloc((void**)&Xd, (size_t)m * s.n * 4);
+    alloc((void**)&Cd, (size_t)s.k * s.n * 4 + 16);
+    alloc((void**)&raw, (size_t)m_pad * 128 + 1024);
+    alloc((void**)&norms, (size_t)(m_pad + 1) * 4);
+    alloc((void**)&Ld, (size_t)m * 4);
+    if (r == BM_OK && cudaMemcpyAsync(Xd, s.X_host, (size_t)m * s.n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        r = set_error(BM_ECUDA, "copy of X");
+    if (r == BM_OK) r = bigmeans_fit(Xd, m, s.n, s.k, &s.policy, &s.budget, s.seed, st, Cd, nullptr, rep);
+    void* Xb = raw ? (void*)(raw + ((1024 - ((uintptr_t)raw & 1023)) & 1023)) : nullptr;
+    if (r == BM_OK) r = bm_pack_bf16(Xd, m, s.n, Xb, norms, st);
+    bm_report rb{};
+    if (r == BM_OK) r = bm_assign_bf16(Xb, norms, Xd, m, s.n, Cd, s.k, s.tau, Ld, f_out, &rb, st);
+    if (r == BM_OK && cudaMemcpyAsync(s.C_out_host, Cd, (size_t)s.k * s.n * 4, cudaMemcpyDeviceToHost, st) !=
+                          cudaSuccess)
+        r = set_error(BM_ECUDA, "copy of C");
+    if (r == BM_OK && s.labels_out_host &&
+        cudaMemcpyAsync(s.labels_out_host, Ld, (size_t)m * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        r = set_error(BM_ECUDA, "copy of labels");
+    for (void* p : {(void*)Xd, (void*)Cd, (void*)raw, (void*)norms, (void*)Ld})
+        if (p) cudaFreeAsync(p, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && r == BM_OK) r = set_error(BM_ECUDA, "job stream");
+    if (rep) rep->rescored_rows += rb.rescored_rows;
+    return r;
 }
 
 }  // namespace
@@ -109,8 +153,11 @@ struct bm_ctx {
             }
             const bm_job& s = j->spec;
             bm_report rep{};
-            const bm_status st_fit = bigmeans_fit_host(s.X_host, s.m, s.n, s.k, &s.policy, &s.budget, s.seed, st,
-                                                      s.C_out_host, s.labels_out_host, &rep);
+            double f_bf16 = 0.0;
+            const bm_status st_fit = s.storage == 1
+                                         ? run_bf16_job(s, st, &rep, &f_bf16)
+                                         : bigmeans_fit_host(s.X_host, s.m, s.n, s.k, &s.policy, &s.budget, s.seed,
+                                                             st, s.C_out_host, s.labels_out_host, &rep);
             const std::string err = st_fit ? std::string(bm_last_error()) : std::string();
             {
                 std::lock_guard<std::mutex> lk(mu);
@@ -119,6 +166,7 @@ struct bm_ctx {
                 j->status = st_fit;
                 j->error = err;
                 j->report = rep;
+                j->f_result = (s.storage == 1) ? f_bf16 : rep.f_full;
                 j->state = 2;
                 j->t_done = now_s(t0);
                 done_count++;
@@ -136,7 +184,7 @@ void fill_result(const Job& j, bm_result* r) {
     memset(r, 0, sizeof *r);
     r->status = (j.state == 2) ? j.status : BM_EAGAIN;
     r->state = j.state;
-    r->f_full = j.report.f_full;
+    r->f_full = j.f_result;
     r->s_opt = j.report.s_opt;
     r->t_submit_s = j.t_submit;
     r->t_admit_s = j.t_admit;
@@ -164,14 +212,23 @@ bm_status bm_ctx_create(int64_t hbm_budget_bytes, int32_t max_active, bm_ctx** o
 
 bm_status bm_job_footprint(const bm_job* job, int64_t* bytes_out) {
     if (!job || !bytes_out) return set_error(BM_EINVAL, "job and bytes_out are required");
+    if (job->storage != 0 && job->storage != 1) return set_error(BM_EINVAL, "storage must be 0 (FP32) or 1 (BF16)");
+    if (job->storage == 1 && (job->n > 64 || !(job->tau >= 0.f)))
+        return set_error(BM_EINVAL, "BF16 storage needs n <= 64 and tau >= 0");
     int64_t ws = 0;
     const bm_status s = bm_fit_footprint(job->m, job->n, job->k, &job->policy, &job->budget, &ws);
     if (s) return s;
-    const int64_t dev = job->m * job->n * 4 + (job->k * (int64_t)job->n * 4 + 16) +
-                        (job->labels_out_host ? job->m * 4 : 0);
-    *bytes_out = ws + dev + 3 * 256;                          // allocation rounding
+    int64_t dev = job->m * job->n * 4 + (job->k * (int64_t)job->n * 4 + 16) +
+                  (job->labels_out_host ? job->m * 4 : 0);
+    if (job->storage == 1) {
+        const int64_t m_pad = (job->m + 127) / 128 * 128;
+        dev += m_pad * 128 + 1024 + (m_pad + 1) * 4 + job->m * 4;    // packed rows, norms, labels
+    }
+    *bytes_out = ws + dev + 6 * 256;                          // allocation rounding
     return BM_OK;
 }
+
+
 
 bm_status bm_submit(bm_ctx* c, const bm_job* job, bm_job_id* id_out) {
     if (!c || !job || !id_out) return set_error(BM_EINVAL, "ctx, job and id_out are required");

@@ -55,7 +55,7 @@ class Job(ctypes.Structure):
     _fields_ = [("X_host", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("policy", SamplePolicy), ("budget", Budget),
                 ("seed", ctypes.c_uint64), ("C_out_host", ctypes.c_void_p),
-                ("labels_out_host", ctypes.c_void_p)]
+                ("labels_out_host", ctypes.c_void_p), ("storage", ctypes.c_int32), ("tau", ctypes.c_float)]
 
 
 class JobResult(ctypes.Structure):
@@ -378,8 +378,9 @@ class ServeContext:
         _check(lib.bm_ctx_create(int(hbm_budget_bytes), int(max_active), ctypes.byref(self.ctx)))
         self._keep = {}
 
-    def submit(self, X, k, policy, budget, seed=0, labels=True):
-        """X: host float32 array (numpy or CPU tensor, pinned preferred). Returns the job id."""
+    def submit(self, X, k, policy, budget, seed=0, labels=True, bf16=False, tau=1e-3):
+        """X: host float32 array (numpy or CPU tensor, pinned preferred). bf16: also hold X packed
+        in BF16 and take labels and f from the precision pass (tau). Returns the job id."""
         if isinstance(X, torch.Tensor):
             Xt = X.contiguous()
             assert Xt.device.type == "cpu" and Xt.dtype == torch.float32
@@ -393,7 +394,8 @@ class ServeContext:
         C = torch.empty((k, n), dtype=torch.float32, pin_memory=pin)
         Y = torch.empty(m, dtype=torch.int32, pin_memory=pin) if labels else None
         job = Job(X_host=xptr, m=m, n=n, k=k, policy=policy, budget=budget, seed=seed,
-                  C_out_host=C.data_ptr(), labels_out_host=(Y.data_ptr() if Y is not None else 0))
+                  C_out_host=C.data_ptr(), labels_out_host=(Y.data_ptr() if Y is not None else 0),
+                  storage=1 if bf16 else 0, tau=float(tau))
         jid = ctypes.c_int64(0)
         _check(lib.bm_submit(self.ctx, ctypes.byref(job), ctypes.byref(jid)))
         self._keep[jid.value] = (Xt, C, Y, job)

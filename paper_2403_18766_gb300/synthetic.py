@@ -100,3 +100,25 @@ def workload(name, seed=None, m=None):
         seed = 1000 + list(WORKLOADS).index(name) + 1
     return gaussian_mixture(p["m"], p["n"], p["components"], seed, cov=p["cov"],
                             weights=p["weights"], outliers=p["outliers"])
+
+
+def gaussian_mixture_device(m, n, components, seed, outliers=0.0, device="cuda"):
+    """float32 (m, n) rows of an isotropic Gaussian mixture drawn on a CUDA
+    device with torch (fast enough for the serving stream's large data sets):
+    means uniform in [-10, 10]^n, sigma = 1, equal weights (component of a row
+    uniform), a fraction `outliers` of rows uniform over the inliers' bounding
+    box.  Seeded by a torch generator on the device, so its stream differs
+    from the numpy recipe above; it draws data only."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    means = torch.rand((components, n), generator=g, device=device) * 20.0 - 10.0
+    comp = torch.randint(0, components, (m,), generator=g, device=device)
+    X = means[comp] + torch.randn((m, n), generator=g, device=device)
+    n_out = int(round(outliers * m))
+    if n_out:
+        lo = X[n_out:].min(dim=0).values
+        hi = X[n_out:].max(dim=0).values
+        X[:n_out] = lo + (hi - lo) * torch.rand((n_out, n), generator=g, device=device)
+        X = X[torch.randperm(m, generator=g, device=device)]
+    return X.contiguous()

@@ -149,3 +149,23 @@ def test_many_concurrent_jobs_of_different_shapes():
         X, k, pol, bud, seed = specs[i]
         _same(ctx.wait(ctx.submit(X, k, pol, bud, seed)), mixed[i])
     ctx.close()
+
+
+def test_bf16_stored_job_takes_labels_and_f_from_the_precision_pass():
+    """A job with BF16 storage fits on the FP32 master (same centroids as the
+    FP32 job), then takes its labels and f(C, X) from the BF16 tensor-core
+    pass over its packed copy."""
+    X, k, pol, bud, seed = _spec(JOBS[1])
+    ctx = native.ServeContext(64 << 30, 2)
+    rb = ctx.wait(ctx.submit(X, k, pol, bud, seed, bf16=True, tau=1e-3))
+    r32 = ctx.wait(ctx.submit(X, k, pol, bud, seed))
+    st = ctx.stats()
+    ctx.close()
+    assert rb["status"] == native.BM_OK, rb.get("error")
+    assert torch.equal(rb["C"].view(torch.int32), r32["C"].view(torch.int32))
+    assert rb["report"]["f_full"] == r32["f_full"]            # exact objective of the same C
+    Xd = X.cuda()
+    Y, f, _ = native.assign_bf16(native.PackedBF16(Xd), rb["C"].cuda(), tau=1e-3)
+    assert torch.equal(rb["labels"], Y.cpu()) and rb["f_full"] == f
+    assert abs(rb["f_full"] - r32["f_full"]) <= 1e-3 * r32["f_full"]
+    assert st["in_use_bytes"] == 0

@@ -52,7 +52,8 @@ def test_struct_layouts_match_c(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = {"bm_sample_policy": native.SamplePolicy, "bm_budget": native.Budget, "bm_report": native.Report}
+    structs = {"bm_sample_policy": native.SamplePolicy, "bm_budget": native.Budget, "bm_report": native.Report,
+               "bm_job": native.Job, "bm_result": native.JobResult, "bm_ctx_info": native.CtxInfo}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "bigmeans.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
