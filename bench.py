@@ -56,8 +56,30 @@ def _dist():
 
 
 def rank_seed(rank):
-    """Seed of the independent fit a rank runs (weak scaling: one problem per rank)."""
-    return 1000 + int(rank)
+    """Seed of the fit: on N ranks one fit of N x 16 workers (each rank runs
+    its 16 workers), so every rank uses the same seed."""
+    return 1000
+
+
+def finish_sharded(sess, Xd, k, policy, rank, world):
+    """The end of a fit sharded over the ranks (paper_2403_18766_gb300.shard):
+    the global mean of L, the common recheck of each rank's workers, the
+    least f_hat over all ranks, the winner's centroids broadcast, and the
+    full-data pass.  Returns (C, labels, report-like dict)."""
+    from paper_2403_18766_gb300 import native, shard
+    rep = sess.report()
+    m = Xd.shape[0]
+    w0, w1 = shard.worker_range(policy["workers"], rank, world)
+    L_sum, L_len = shard.global_L(rep["L_sum"], rep["accepts"], None, Xd.device)
+    s_opt = shard.s_opt_from(L_sum, L_len, *shard.size_range(policy, m))
+    f_best, w_best = shard.pick_best(sess.recheck(s_opt), w0, None, Xd.device)
+    owner = next(r for r in range(world)
+                 if shard.worker_range(policy["workers"], r, world)[0] <= w_best
+                 < shard.worker_range(policy["workers"], r, world)[1])
+    C = sess.worker_centroids(w_best) if owner == rank else None
+    C = shard.broadcast_centroids(C, owner, (k, Xd.shape[1]), None, Xd.device)
+    Y, f, _ = native.assign(Xd, C)
+    return C, Y, dict(rep, f_full=f, s_opt=s_opt, best_worker=w_best)
 
 
 def aggregate(t_local, work_local, device="cpu"):
@@ -251,12 +273,16 @@ def run_ours(args):
     m, n = X.shape
     Xd = torch.from_numpy(X).to(dev)
     stream = torch.cuda.current_stream(dev)
-    pol = native.make_policy(**POLICY)
+    # on N ranks: one fit of N x W workers, rank r running workers [W r, W (r + 1))
+    fit_policy = dict(POLICY, workers=POLICY["workers"] * ws)
+    pol = native.make_policy(**fit_policy)
     total_rounds = args.warmup + args.steps
     bud = native.make_budget(rounds=total_rounds, **BUDGET)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     sess = native.FitSession(Xd, K_CLUSTERS, pol, bud, seed=rank_seed(rank))
+    if ws > 1:
+        sess.set_workers(POLICY["workers"] * rank, POLICY["workers"] * (rank + 1))
     clocks = ClockSampler(local)
     trace = []                                  # (cumulative device s, f_incumbent) after each round
     t_cum = 0.0
@@ -289,7 +315,10 @@ def run_ours(args):
     f_end = trace[-1][1]
     tto = next(((t, i + 1) for i, (t, f) in enumerate(trace) if f <= f_end * (1 + 1e-4)), (None, None))
     clk = clocks.stop()
-    C, Y_fin, rep_fin = sess.finish(labels=True)
+    if ws > 1:
+        C, Y_fin, rep_fin = finish_sharded(sess, Xd, K_CLUSTERS, fit_policy, rank, ws)
+    else:
+        C, Y_fin, rep_fin = sess.finish(labels=True)
     sess.close()
 
     t_local = sum(step_ms) / 1e3
@@ -352,7 +381,8 @@ def run_ours(args):
         e2e_vals, e2e_parts = [], []
         for i in range(3):
             t0 = time.perf_counter()
-            _, _, r = native.fit_host(Xp, K_CLUSTERS, pol, e2e_bud, seed=77 + i, labels=True)
+            _, _, r = native.fit_host(Xp, K_CLUSTERS, native.make_policy(**POLICY), e2e_bud, seed=77 + i,
+                                      labels=True)
             dt = time.perf_counter() - t0
             e2e_vals.append(r["assign_rows"] * K_CLUSTERS / dt)
             e2e_parts.append((dt, r))

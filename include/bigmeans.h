@@ -199,6 +199,33 @@ bm_status bm_fit_rounds(bm_fit_ctx* ctx, int32_t rounds);
 bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t rounds);
 bm_status bm_fit_finish(bm_fit_ctx* ctx, float* C_out_dev, int32_t* labels_out_dev,
                         bm_report* report_out);
+/* ---------------------------------------------------------------------------
+ * A fit sharded over ranks (one GPU each, X replicated: the paper's workers
+ * all see the whole data set, Sec. 4.3).  Workers are independent until the
+ * end of Alg. 1 except for the list L of improving sizes (Sec. 4.2) and the
+ * final common recheck (Sec. 4.3), so rank r runs the workers [w_begin,
+ * w_end) of a W-worker fit and the ranks exchange three small things on the
+ * host (paper_2403_18766_gb300/shard.py):
+ *   1. after the rounds, every rank's (sum of L, |L|) from bm_fit_report
+ *      (L_sum, accepts), summed: s_opt = the mean of the global L, rounded
+ *      half up and clipped to the size range (s_max if L is empty);
+ *   2. bm_fit_recheck(ctx, s_opt, f): f_hat_w of the rank's workers on the
+ *      common sample of size s_opt (the same draws on every rank), then the
+ *      least (f_hat_w, w) over all ranks (lowest w on ties) picks w*;
+ *   3. the owner of w* exports its centroids (bm_fit_worker_centroids), they
+ *      are broadcast, and the full-data pass (bm_assign) gives labels and f.
+ * The results equal the unsharded fit's bit for bit.
+ * bm_fit_set_workers: before the first round; 0 <= w_begin < w_end <= W;
+ *   not with the exploit policy (its sizes need L every round).  A shard's
+ *   draws are the workers' own (keyed by their global index).
+ * bm_fit_recheck: f_out_host receives w_end - w_begin doubles; s_opt must lie
+ *   in the size range.  bm_fit_finish refuses a shard (BM_EINVAL).
+ * bm_fit_worker_centroids: C_out_dev (k x n floats, device) receives worker
+ *   w's current centroids; w must be one of the context's workers.
+ * ------------------------------------------------------------------------- */
+bm_status bm_fit_set_workers(bm_fit_ctx* ctx, int32_t w_begin, int32_t w_end);
+bm_status bm_fit_recheck(bm_fit_ctx* ctx, int64_t s_opt, double* f_out_host);
+bm_status bm_fit_worker_centroids(bm_fit_ctx* ctx, int32_t w, float* C_out_dev);
 /* Counters and phase times so far (no final recheck); f_full and
  * f_incumbent hold the incumbent's full objective when
  * eval_full_each_round is set, else 0 and +inf. */

@@ -274,6 +274,7 @@ struct bm_fit_ctx {
     long long n_kernels = 0;                // kernels of this library launched so far
     int last_groups = 0;                    // clusters of the last grouped round launch (0: not grouped)
     bool groups_ok = true;                  // groups allowed for this fit (creating thread's setting)
+    int w_lo = 0, w_hi = 0;                 // workers this context runs (a shard of a fit: [w_lo, w_hi))
 };
 
 namespace {
@@ -325,7 +326,11 @@ SampleArgs make_sample_args(bm_fit_ctx* c, int mode, int jobs, int parity = 0) {
     for (int i = 0; i < 16; ++i) a.set[i] = c->pol.set[i];
     a.set_len = c->pol.set_len;
     a.sp = size_policy(c);
-    const long long J = (long long)parity * c->jobs;         // first job of this buffer half
+    // first job of this buffer half, and of the context's first worker (a
+    // shard draws only its own workers' samples, into their usual slots)
+    const long long J = (long long)parity * c->jobs +
+                        ((mode == kSampleRound) ? (long long)c->w_lo * (c->pol.passes + 1) : 0);
+    a.worker_base = (mode == kSampleRound) ? c->w_lo : 0;
     a.S_stride = c->s_cap * c->np; a.S = c->S + J * a.S_stride;
     a.idx_stride = c->s_cap; a.idx = c->idx + J * a.idx_stride;
     a.draws_stride = c->Tcap; a.draws = c->draws + J * a.draws_stride; a.Tcap = c->Tcap;
@@ -655,8 +660,10 @@ int plan_launch(const std::vector<bm_fit_ctx*>& fits, std::vector<PlanItem> item
         for (int i = 0; i < nw; ++i) a.cmap[i] = (unsigned)items[i].w | ((unsigned)items[i].fit << 12) | (1u << 24);
         a.ncl = nw;
     } else {
-        a.ncl = 0;                                  // worker = cluster index (one fit)
-        a.worker_base = 0;
+        a.ncl = 0;                                  // worker = first worker + cluster index (one fit)
+        int wmin = items[0].w;
+        for (const PlanItem& it : items) wmin = std::min(wmin, it.w);
+        a.worker_base = wmin;
     }
     return nw;
 }
@@ -681,7 +688,7 @@ bm_status round_samples(bm_fit_ctx* c, int r0) {
         SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, parity);
         sa.rnd = r0;
         const size_t sp_s = span_begin(c, 2);
-        CU(launch_sample(c->np, sa, c->jobs, c->st));
+        CU(launch_sample(c->np, sa, (c->w_hi - c->w_lo) * (c->pol.passes + 1), c->st));
         span_end(c, sp_s);
         c->n_kernels++;
     }
@@ -699,7 +706,7 @@ bm_status round_prefetch(bm_fit_ctx* c, int r0) {
         SampleArgs sa = make_sample_args(c, kSampleRound, c->jobs, (r0 + 1) & 1);
         sa.rnd = r0 + 1;
         const size_t sp_s = span_begin(c, 2, c->sst);
-        CU(launch_sample(c->np, sa, c->jobs, c->sst));
+        CU(launch_sample(c->np, sa, (c->w_hi - c->w_lo) * (c->pol.passes + 1), c->sst));
         span_end(c, sp_s);
         CU(cudaEventRecord(c->ev_sdone, c->sst));
         c->n_kernels++;
@@ -718,7 +725,7 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     if ((s = round_samples(c, r0))) return s;
     const size_t sp = span_begin(c, 0);
     std::vector<PlanItem> items;
-    for (int w = 0; w < c->pol.workers; ++w) items.push_back({0, w, size_of(c, w, r0)});
+    for (int w = c->w_lo; w < c->w_hi; ++w) items.push_back({0, w, size_of(c, w, r0)});
     WorkerArgs a = make_args(c, kModeRounds, r0 & 1);
     a.round_begin = r0;
     a.round_end = r1;
@@ -818,6 +825,7 @@ bm_status plan_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, const bm
     c->X = X_dev; c->m = m; c->n = n; c->k = k; c->np = padded_dim(n);
     c->pol = pol; c->bud = bud; c->seed = seed;
     c->s_lo = s_lo; c->s_hi = s_hi; c->s_cap = s_hi;
+    c->w_lo = 0; c->w_hi = pol.workers;
     c->max_cs = worker_max_cluster(c->np, k);
     c->rows_per_cta = g_rows_per_cta.load();
     c->cs = cluster_size(s_hi, c->max_cs, c->rows_per_cta, rows_cap(c->np, k));
@@ -996,7 +1004,7 @@ bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t ro
         if (fits[i]->np != fits[0]->np)
             return fail(BM_EINVAL, "fits[%d] has another padded width (n = %d vs %d)", i, fits[i]->n, fits[0]->n);
         if (fits[i]->bud.seconds > 0) return fail(BM_EINVAL, "fits[%d] has a wall-clock budget", i);
-        total += fits[i]->pol.workers;
+        total += fits[i]->w_hi - fits[i]->w_lo;
     }
     if (nfits == 1) return bm_fit_rounds(fits[0], rounds);
     if (total > kMaxLaunchClusters) return fail(BM_EINVAL, "%d workers in all above %d", total, kMaxLaunchClusters);
@@ -1028,7 +1036,7 @@ bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t ro
         for (int i = 0; i < nfits && s == BM_OK; ++i) {
             bm_fit_ctx* c = fits[i];
             if ((s = round_samples(c, c->rounds_run))) break;
-            for (int w = 0; w < c->pol.workers; ++w) items.push_back({i, w, size_of(c, w, c->rounds_run)});
+            for (int w = c->w_lo; w < c->w_hi; ++w) items.push_back({i, w, size_of(c, w, c->rounds_run)});
         }
         if (s) break;
         WorkerArgs plan;
@@ -1082,8 +1090,61 @@ bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t ro
     return BM_OK;
 }
 
+bm_status bm_fit_set_workers(bm_fit_ctx* c, int32_t w_begin, int32_t w_end) {
+    if (!c) return fail(BM_EINVAL, "ctx is NULL");
+    if (c->rounds_run > 0) return fail(BM_EINVAL, "the worker range is set before the first round");
+    if (w_begin < 0 || w_end > c->pol.workers || w_begin >= w_end)
+        return fail(BM_EINVAL, "worker range [%d, %d) not inside [0, %d)", w_begin, w_end, c->pol.workers);
+    if (c->pol.exploit > 0) return fail(BM_EINVAL, "a shard of workers cannot use the exploit policy (L is global)");
+    if (c->prefetched >= 0) {                  // drop a draw-ahead made for the old range
+        CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));
+        c->prefetched = -1;
+    }
+    c->w_lo = w_begin;
+    c->w_hi = w_end;
+    return BM_OK;
+}
+
+bm_status bm_fit_recheck(bm_fit_ctx* c, int64_t s_opt, double* f_out_host) {
+    if (!c || !f_out_host) return fail(BM_EINVAL, "ctx and f_out_host are required");
+    const long long lo = c->pol.set_len > 0 ? c->s_lo : c->pol.s_min;
+    if (s_opt < std::max<long long>(lo, c->k) || s_opt > c->s_hi)
+        return fail(BM_EINVAL, "s_opt = %lld outside the size range [%lld, %lld]", (long long)s_opt, lo, c->s_hi);
+    if (c->prefetched >= 0) {
+        CU(cudaStreamWaitEvent(c->st, c->ev_sdone, 0));
+        c->prefetched = -1;
+    }
+    const size_t sp = span_begin(c, 0);
+    SampleArgs sa = make_sample_args(c, kSampleFinal, 1);
+    sa.step_s = s_opt;
+    CU(launch_sample(c->np, sa, 1, c->st));
+    WorkerArgs a = make_args(c, kModeFinalEval);
+    a.worker_base = c->w_lo;
+    CU(launch_worker(c->np, a, c->w_hi - c->w_lo, c->st));
+    c->n_kernels += 2;
+    span_end(c, sp);
+    CU(cudaMemcpyAsync(f_out_host, c->f_final + c->w_lo, (size_t)(c->w_hi - c->w_lo) * 8, cudaMemcpyDeviceToHost,
+                       c->st));
+    Globals h;
+    bm_status s;
+    if ((s = read_globals(c, &h))) return s;
+    return status_from_flags(h);
+}
+
+bm_status bm_fit_worker_centroids(bm_fit_ctx* c, int32_t w, float* C_out_dev) {
+    if (!c) return fail(BM_EINVAL, "ctx is NULL");
+    if (w < c->w_lo || w >= c->w_hi) return fail(BM_EINVAL, "worker %d not in [%d, %d)", w, c->w_lo, c->w_hi);
+    bm_status s = check_ptr(C_out_dev, "C_out_dev");
+    if (s) return s;
+    CU(launch_unpad(c->Cw + (size_t)w * c->k * c->np, c->k, c->n, c->np, C_out_dev, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return BM_OK;
+}
+
 bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep) {
     if (!c) return fail(BM_EINVAL, "ctx is NULL");
+    if (c->w_lo != 0 || c->w_hi != c->pol.workers)
+        return fail(BM_EINVAL, "a shard of workers finishes through bm_fit_recheck and the ranks' exchange");
     bm_status s = check_ptr(C_out_dev, "C_out_dev");
     if (s) return s;
     WorkerArgs a = make_args(c, kModeFinalEval);
@@ -1199,6 +1260,7 @@ static bm_status step_ctx(bm_fit_ctx* c, const float* X, long long m, int n, int
     c->bud.rounds = 1; c->bud.max_lloyd = 300; c->bud.tol = 1e-4; c->bud.kpp_candidates = 3;
     c->seed = seed;
     c->s_lo = c->s_hi = c->s_cap = std::max<long long>(s_cap, 1);
+    c->w_lo = 0; c->w_hi = 1;
     c->max_cs = worker_max_cluster(c->np, k);
     c->cs = cluster_size(c->s_cap, c->max_cs, 0, rows_cap(c->np, k));
     if (c->cs == 0)

@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(kSampleThreads, 1) sample_kernel(const SampleA
         const long long acc = (long long)a.glob->accepts, Ls = (long long)a.glob->L_sum;
         s = s_hi;
         if (acc > 0) s = min(max((2 * Ls + acc) / (2 * acc), s_lo), s_hi);
+        if (a.step_s > 0) s = a.step_s;        // s_opt given by the host (a fit sharded over ranks)
         purpose = kPurposeFinal; worker = 0; rnd = 0; pss = 0;
         if (threadIdx.x == 0) a.glob->s_opt = (int)s;
     }

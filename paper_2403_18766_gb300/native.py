@@ -93,6 +93,9 @@ SIGNATURES = {
     "bm_fit_create": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_p)]),
     "bm_fit_rounds": (_i32, [_p, _i32]),
     "bm_fit_rounds_batch": (_i32, [ctypes.POINTER(_p), _i32, _i32]),
+    "bm_fit_set_workers": (_i32, [_p, _i32, _i32]),
+    "bm_fit_recheck": (_i32, [_p, _i64, ctypes.POINTER(_dbl)]),
+    "bm_fit_worker_centroids": (_i32, [_p, _i32, _p]),
     "bm_fit_finish": (_i32, [_p, _p, _p, _RP]),
     "bm_fit_destroy": (None, [_p]),
     "bm_fit_report": (_i32, [_p, _RP]),
@@ -244,6 +247,27 @@ class FitSession:
         rep = Report()
         _check(lib.bm_fit_report(self.ctx, ctypes.byref(rep)))
         return rep.as_dict()
+
+    def set_workers(self, w_begin, w_end):
+        """bm_fit_set_workers: run only workers [w_begin, w_end) (a shard of the fit)."""
+        _check(lib.bm_fit_set_workers(self.ctx, int(w_begin), int(w_end)))
+        self.w_range = (int(w_begin), int(w_end))
+
+    def recheck(self, s_opt):
+        """bm_fit_recheck: f_hat of the shard's workers on the common sample of size s_opt."""
+        w0, w1 = getattr(self, "w_range", (0, None))
+        if w1 is None:
+            raise ValueError("set_workers first")
+        f = (ctypes.c_double * (w1 - w0))()
+        _check(lib.bm_fit_recheck(self.ctx, int(s_opt), f))
+        return list(f)
+
+    def worker_centroids(self, w):
+        """bm_fit_worker_centroids: worker w's centroids (k x n, device)."""
+        m, n = self.X.shape
+        C = torch.empty((self.k, n), dtype=torch.float32, device=self.X.device)
+        _check(lib.bm_fit_worker_centroids(self.ctx, int(w), _ptr(C)))
+        return C
 
     def close(self):
         if self.ctx:

@@ -413,3 +413,49 @@ def test_batched_fits_reject_mixed_widths():
     assert e.value.status == native.BM_EINVAL
     a.close()
     b.close()
+
+
+# ------------------------------------- a fit sharded over ranks (emulated)
+def test_sharded_fit_equals_the_unsharded_fit():
+    """Two shards of one fit run one after the other on this GPU (each a rank's
+    part: bm_fit_set_workers), combined as the ranks' exchange would (sum of
+    L, least f_hat on the common sample, the winner's centroids, full pass):
+    the same s_opt, best worker, C, labels and f as the unsharded fit."""
+    from paper_2403_18766_gb300 import shard
+    X = gaussian_mixture(60_000, 16, 8, seed=38, cov="aniso")
+    Xd = _t(X)
+    pol = dict(s_min=2000, s_max=30_000, workers=5, passes=3)
+    bud = dict(rounds=2, max_lloyd=300, tol=1e-4, kpp_candidates=3)
+    C0, Y0, r0 = native.fit(Xd, 8, native.make_policy(**pol), native.make_budget(**bud), seed=9)
+    shards = []
+    for rank in (0, 1):
+        w0, w1 = shard.worker_range(pol["workers"], rank, 2)
+        sess = native.FitSession(Xd, 8, native.make_policy(**pol), native.make_budget(**bud), seed=9)
+        sess.set_workers(w0, w1)
+        sess.rounds(bud["rounds"])
+        shards.append((sess, w0, w1, sess.report()))
+    L_sum = sum(s[3]["L_sum"] for s in shards)
+    L_len = sum(s[3]["accepts"] for s in shards)
+    assert L_sum == r0["L_sum"] and L_len == r0["accepts"]
+    s_opt = shard.s_opt_from(L_sum, L_len, *shard.size_range(pol, X.shape[0]))
+    assert s_opt == r0["s_opt"]
+    pairs = []
+    for sess, w0, w1, _ in shards:
+        pairs += [(v, w0 + i) for i, v in enumerate(sess.recheck(s_opt))]
+    f_best, w_best = shard.least(pairs)
+    assert w_best == r0["best_worker"]
+    owner = next(s for s in shards if s[1] <= w_best < s[2])[0]
+    C = owner.worker_centroids(w_best)
+    for s in shards:
+        s[0].close()
+    Y, f, _ = native.assign(Xd, C)
+    assert torch.equal(C.view(torch.int32), C0.view(torch.int32))
+    assert torch.equal(Y, Y0) and f == r0["f_full"]
+    with pytest.raises(native.BigmeansError):           # a shard does not finish on its own
+        sess = native.FitSession(Xd, 8, native.make_policy(**pol), native.make_budget(**bud), seed=9)
+        sess.set_workers(0, 2)
+        sess.rounds(1)
+        try:
+            sess.finish()
+        finally:
+            sess.close()

@@ -1,6 +1,6 @@
-"""The N > 1 path of bench.py on CPU: two gloo ranks.  Each rank runs its own
-problem (weak scaling) with its own seed; the whole-job time is the slowest
-rank's and the work is the sum over ranks (no data-path collective)."""
+"""The N > 1 path of bench.py on CPU: two gloo ranks.  The ranks run one fit
+together (each its own workers, weak scaling, the same seed); the whole-job
+time is the slowest rank's and the work is the sum over ranks."""
 import os
 import socket
 import sys
@@ -48,4 +48,4 @@ def test_two_gloo_ranks_take_max_time_and_total_work():
     for rank, t, w, seed, (ws, rk) in res:
         assert t == 1.5 and w == 300.0                  # max over ranks, sum over ranks
         assert ws == 2 and rk == rank
-    assert res[0][3] != res[1][3]                       # independent problems per rank
+    assert res[0][3] == res[1][3]                       # one fit: the same seed on every rank
