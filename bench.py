@@ -341,7 +341,7 @@ def run_ours(args):
     flops = 2.0 * n * K_CLUSTERS * rows
     achieved = flops / t_worker / 1e12 if t_worker > 0 else 0.0
     srcs = [os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
-            for f in ("bm_worker_impl.cuh", "bm_sample.cu", "bm_device.cuh")]
+            for f in ("bm_worker_impl.cuh", "bm_worker.cuh", "bm_device.cuh")]
     traffic, digest = _traffic_for(srcs)
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak if alu_peak else None,

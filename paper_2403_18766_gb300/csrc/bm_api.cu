@@ -17,6 +17,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -605,7 +606,12 @@ int plan_launch(const std::vector<bm_fit_ctx*>& fits, std::vector<PlanItem> item
     std::stable_sort(items.begin(), items.end(), [](const PlanItem& x, const PlanItem& y) { return x.s > y.s; });
     const bm_fit_ctx* c0 = fits[0];
     int kmax = 0;
-    bool groups = !g_big_tpb.load() && !g_no_groups.load() && nw <= kMaxLaunchClusters;
+    // Under an injected profiler (CUDA_INJECTION64_PATH set, e.g. Nsight
+    // Compute) groups are off: the profiler was seen to run a cooperative
+    // cluster launch without its cluster shape (the kernel's launch check then
+    // refuses to run).  Results are the same with or without groups.
+    static const bool profiled = std::getenv("CUDA_INJECTION64_PATH") != nullptr;
+    bool groups = !profiled && !g_big_tpb.load() && !g_no_groups.load() && nw <= kMaxLaunchClusters;
     for (const bm_fit_ctx* c : fits) {
         kmax = std::max(kmax, c->k);
         groups = groups && c->xpart && c->groups_ok;

@@ -918,6 +918,14 @@ struct Worker {
 // memory (p.batch[fit of the cluster]); otherwise the kernel parameter itself.
 template <int NP, int TPB, bool BATCH>
 __global__ void __launch_bounds__(TPB, 512 / TPB) worker_kernel(const __grid_constant__ WorkerArgs p) {
+    // The launch must have the cluster shape and grid the arguments describe
+    // (every exchange addresses the other CTAs of the cluster by rank): if
+    // not, record the error and leave before any barrier or remote access.
+    if (cg::this_cluster().num_blocks() != (unsigned)p.cs || gridDim.x % (unsigned)p.cs != 0 ||
+        (p.ncl > 0 && gridDim.x != (unsigned)(p.ncl * p.cs))) {
+        if (threadIdx.x == 0) atomicOr(&p.glob->err, kErrArgs);
+        return;
+    }
     const WorkerArgs& a = BATCH ? p.batch[(p.cmap[blockIdx.x / p.cs] >> 12) & 0xfu] : p;
     Worker<NP, TPB> W(a, cg::this_cluster());
     if (a.glob->nonfinite) return;            // uniform: read before any barrier
