@@ -390,10 +390,11 @@ int32_t bm_last_fullpass_impl(void);
  *   or bm_set_big_clusters(1)): one cluster per worker, all of the size the
  *   largest sample needs (the cluster tile below), in the same launch.
  * Results are identical either way (all reductions are exact).  Groups are
- * also off when the process runs under an injected profiler (environment
- * variable CUDA_INJECTION64_PATH set): Nsight Compute was seen to launch a
- * cooperative cluster kernel without its cluster shape; the worker kernel
- * checks its launch shape and reports BM_EINVAL rather than run so.
+ * also off when a cooperative launch does not keep its cluster shape in the
+ * process (checked once per device with a tiny probe launch): Nsight Compute
+ * was seen to launch a cooperative cluster kernel without its clusters; the
+ * worker kernel checks its launch shape and reports BM_EINVAL rather than
+ * run so.
  * bm_set_worker_groups: 1 (default) allows groups, 0 disables them; other
  * values are BM_EINVAL.  Process-wide, read at each round's launch.
  * ------------------------------------------------------------------------- */

@@ -606,16 +606,15 @@ int plan_launch(const std::vector<bm_fit_ctx*>& fits, std::vector<PlanItem> item
     std::stable_sort(items.begin(), items.end(), [](const PlanItem& x, const PlanItem& y) { return x.s > y.s; });
     const bm_fit_ctx* c0 = fits[0];
     int kmax = 0;
-    // Under an injected profiler (CUDA_INJECTION64_PATH set, e.g. Nsight
-    // Compute) groups are off: the profiler was seen to run a cooperative
-    // cluster launch without its cluster shape (the kernel's launch check then
-    // refuses to run).  Results are the same with or without groups.
-    static const bool profiled = std::getenv("CUDA_INJECTION64_PATH") != nullptr;
-    bool groups = !profiled && !g_big_tpb.load() && !g_no_groups.load() && nw <= kMaxLaunchClusters;
+    bool groups = !g_big_tpb.load() && !g_no_groups.load() && nw <= kMaxLaunchClusters;
     for (const bm_fit_ctx* c : fits) {
         kmax = std::max(kmax, c->k);
         groups = groups && c->xpart && c->groups_ok;
     }
+    // Groups need a cooperative launch that keeps its cluster shape; a tool
+    // that intercepts launches (Nsight Compute was seen to) may drop it, and
+    // then every worker gets one cluster (the same results).
+    groups = groups && cooperative_clusters_ok();
     const long long smax = items[0].s;
     const long long cap = rows_cap(c0->np, kmax);
     const size_t base = worker_smem(c0->np, kmax);
@@ -651,7 +650,13 @@ int plan_launch(const std::vector<bm_fit_ctx*>& fits, std::vector<PlanItem> item
                                    ((unsigned)G[i] << 24);
             a.ncl = ci;
             a.cs = gcs;
-            a.coop = 1;
+            // Under an Nsight tool (which runs one kernel at a time when it
+            // profiles one, and was seen to drop the cluster shape of a
+            // cooperative launch it profiles) the launch is not cooperative:
+            // the grid is within what the device holds at once, so every CTA
+            // is resident while nothing else runs.
+            static const bool nsight = std::getenv("NV_NSIGHT_INJECTION_TRANSPORT_TYPE") != nullptr;
+            a.coop = nsight ? 0 : 1;
             a.rows_cta = (int)rows;
             a.tpb = 256;
             return ci;
@@ -737,11 +742,11 @@ bm_status run_round_launch(bm_fit_ctx* c, int r0, int r1) {
     a.round_end = r1;
     a.deadline_ns = (c->bud.seconds > 0) ? c->t0_gpu + (unsigned long long)(c->bud.seconds * 1e9) : 0ull;
     const int clusters = plan_launch({c}, items, a);
-    if (a.coop) CU(cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, c->st));   // barriers, aborts
+    if (a.ncl > 0 && c->xbar) CU(cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, c->st));   // barriers, aborts
     CU(cudaEventRecord(c->ev_fork, c->st));
     CU(launch_worker(c->np, a, clusters, c->st));
     c->n_kernels++;
-    c->last_groups = a.coop ? clusters : 0;
+    c->last_groups = (a.ncl > 0 && a.cs == kGroupCs) ? clusters : 0;
     if ((s = round_prefetch(c, r0))) return s;
     span_end(c, sp);
     return BM_OK;
@@ -1059,7 +1064,7 @@ bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t ro
             a.tpb = 256; a.k_smem = plan.k_smem;
             memcpy(a.cmap, plan.cmap, sizeof a.cmap);
             a.batch = (const WorkerArgs*)dargs;
-            if (a.coop && cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, st) != cudaSuccess)
+            if (c->xbar && cudaMemsetAsync(c->xbar, 0, (size_t)c->pol.workers * 2 * 4, st) != cudaSuccess)
                 s = fail(BM_ECUDA, "barrier reset");
         }
         if (s) break;
@@ -1075,7 +1080,7 @@ bm_status bm_fit_rounds_batch(bm_fit_ctx* const* fits, int32_t nfits, int32_t ro
         fits[0]->n_kernels++;
         for (int i = 0; i < nfits && s == BM_OK; ++i) {
             bm_fit_ctx* c = fits[i];
-            c->last_groups = plan.coop ? clusters : 0;
+            c->last_groups = clusters;
             if ((s = round_prefetch(c, c->rounds_run))) break;
             c->rounds_run += 1;
             if (c->bud.eval_full_each_round) s = run_fullpass(c, c->fhat, nullptr, 1);

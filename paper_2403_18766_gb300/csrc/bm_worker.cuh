@@ -144,6 +144,8 @@ cudaError_t launch_worker(int np, const WorkerArgs& a, int clusters, cudaStream_
 // Clusters of `cs` CTAs (256 threads, `smem` bytes each) that can be resident
 // at once on the device (0 on error).
 int worker_active_clusters(int np, int cs, size_t smem);
+// Whether a cooperative launch keeps its cluster shape here (checked once per device).
+bool cooperative_clusters_ok();
 size_t worker_smem(int np, int k);
 int worker_max_cluster(int np, int k);   // 16 if 16-CTA clusters fit, else 8
 
