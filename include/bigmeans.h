@@ -297,9 +297,14 @@ bm_status bm_assign(const float* X_dev, int64_t m, int32_t n, const float* C_dev
  * definition (FP32 direct form, lowest index on ties); otherwise its label is
  * the least g and its distance ||x||^2 + g (both in FP32).  f is the exact
  * sum of those distances rounded once to double; report->rescored_rows
- * counts re-scored rows.  1 <= k <= 256.  Labels of rows that are not
- * re-scored can differ from bm_assign where two centroids are within the
- * BF16 error; the difference in f is reported by the tests and the bench.
+ * counts re-scored rows.  A re-scored row is decided among its candidates,
+ * the centroids whose g lies within the certificate bound of
+ * bm_assign_bf16_certified of the least g (they contain the exact-mode
+ * argmin), or over all k when it has more than 8.  1 <= k <= 256.  Labels
+ * of rows that are not re-scored (the least g, lowest index on ties) can
+ * differ from bm_assign where two centroids are within the BF16 error; the
+ * difference in f is reported by the tests and the bench.  Workspace: 256 +
+ * 16 m bytes, stream-ordered, freed before return.
  * ------------------------------------------------------------------------- */
 bm_status bm_pack_bf16(const float* X_dev, int64_t m, int32_t n, void* Xb_out_dev,
                        float* norms_out_dev, void* stream);
@@ -310,9 +315,10 @@ bm_status bm_assign_bf16(const void* Xb_dev, const float* norms_dev, const float
 /* bm_assign_bf16_certified -- bm_assign_bf16 with labels certified equal to
  * those of bm_assign: a row is also re-scored unless its two least g differ
  * by more than the bound of the BF16 form, 2 B + gp2 (g1 + B + ||x||^2) with
- * B = 2^-7 (max ||c||^2 + 2 ||x|| max ||c||) (BF16 rounding of x and c,
- * FP32 accumulation, with a factor 2 of slack) and gp2 the direct form's
- * relative error at 64 dimensions; ||x||^2 is bounded by norms[r] (1 + 2^-7).
+ * B = (2^-7 + 2^-13) (max ||c||^2 + 2 ||x|| max ||c||) (BF16 keeps 8
+ * significant bits: rounding of x and c, FP32 accumulation, the final fma)
+ * and gp2 the direct form's relative error at 64 dimensions; ||x||^2 is
+ * bounded by norms[r] (1 + 2^-6).
  * That is, a row keeps the tensor-core label only where that label is
  * provably the exact-mode argmin.  Distances of rows that are not re-scored
  * are still ||x||^2 + g (f differs from bm_assign as for bm_assign_bf16).

@@ -44,7 +44,7 @@ cudaError_t launch_select_unpad(const float* Cw, const double* sel_f, int W, int
 cudaError_t launch_init_state(double* fhat, int W, unsigned char* deg, long long kdeg, Globals* g,
                               cudaStream_t st);
 cudaError_t launch_globaltimer(unsigned long long* out, cudaStream_t st);
-size_t tc_smem_bytes(int k, int Npad);
+size_t tc_smem_bytes(int k);
 cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad, void* Xb, float* norms,
                              cudaStream_t st);
 void set_fullpass_impl(int impl);
@@ -53,8 +53,8 @@ int fullpass_impl_setting();
 bool tcx_eligible(const float* X, long long m, int n, int np, int k);
 void set_tcx_wait_limit(unsigned polls, unsigned ns);
 cudaError_t launch_tc_fullpass(const void* Xb, const float* xnorm, const float* Xf, long long m, int n,
-                               const float* C, int k, float tau, int certify, int* labels, int* queue, Globals* g,
-                               float gB, float gp2, int sms, cudaStream_t st);
+                               const float* C, int k, float tau, int certify, int* labels, void* queue, Globals* g,
+                               float gp2, int sms, cudaStream_t st);
 }  // namespace bm
 
 using namespace bm;
@@ -1481,20 +1481,20 @@ static bm_status assign_bf16(const void* Xb_dev, const float* norms_dev, const f
     if (!Xb_dev || !norms_dev || !X_dev || !C_dev) return fail(BM_EINVAL, "NULL pointer");
     if (((uintptr_t)Xb_dev) & 1023) return fail(BM_EINVAL, "Xb_dev must be 1024-byte aligned");
     if (!(tau >= 0.f)) return fail(BM_EINVAL, "tau must be >= 0");
-    if (tc_smem_bytes(k, (k + 15) & ~15) > kSmemLimit) return fail(BM_EINVAL, "k too large");
+    if (tc_smem_bytes(k) == 0) return fail(BM_EINVAL, "k too large");
     cudaStream_t sm = (cudaStream_t)stream;
     void* base = nullptr;
     const size_t gb = (sizeof(Globals) + 255) & ~(size_t)255;
-    CU(lib_alloc(&base, gb + (size_t)m * 4, sm));
+    CU(lib_alloc(&base, gb + (size_t)m * 16, sm));     // Globals, queue of m 16-byte entries
     Globals* g = (Globals*)base;
-    int* queue = (int*)((char*)base + gb);
+    void* queue = (char*)base + gb;
     float gB, gp2;
     cert_constants(64, gB, gp2);                   // rows of the precision form are 64 wide
     cudaError_t e;
     if ((e = cudaMemsetAsync(g, 0, sizeof(Globals), sm)) ||
         (e = launch_prepass(C_dev, (long long)k * n, g, 1, sm)) ||
         (e = launch_tc_fullpass(Xb_dev, norms_dev, X_dev, m, n, C_dev, k, tau, certify, labels_out_dev, queue, g,
-                                gB, gp2, sm_count(), sm))) {
+                                gp2, sm_count(), sm))) {
         cudaFreeAsync(base, sm);
         cudaStreamSynchronize(sm);
         return fail(BM_ECUDA, "tensor-core pass launch: %s", cudaGetErrorString(e));

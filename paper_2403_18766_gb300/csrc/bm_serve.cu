@@ -223,6 +223,7 @@ bm_status bm_job_footprint(const bm_job* job, int64_t* bytes_out) {
     if (job->storage == 1) {
         const int64_t m_pad = (job->m + 127) / 128 * 128;
         dev += m_pad * 128 + 1024 + (m_pad + 1) * 4 + job->m * 4;    // packed rows, norms, labels
+        dev += 256 + job->m * 16;                                      // the precision pass's queue
     }
     *bytes_out = ws + dev + 6 * 256;                          // allocation rounding
     return BM_OK;

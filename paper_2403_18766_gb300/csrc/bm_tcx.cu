@@ -592,6 +592,8 @@ void set_tcx_wait_limit(unsigned polls, unsigned ns) {
     g_wait_polls.store(polls ? polls : tc::kDefaultWait.polls);
     g_wait_ns.store(polls ? ns : tc::kDefaultWait.ns);
 }
+// The limit the tensor-core passes (exact and precision form) launch with.
+tc::WaitLimit tcx_wait_limit() { return {g_wait_polls.load(), g_wait_ns.load()}; }
 
 // Launch the tensor-core exact pass; cudaErrorNotSupported when not eligible.
 cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
@@ -599,7 +601,7 @@ cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, cons
                                 int incumbent, int sms, cudaStream_t st) {
     TxShape sh;
     if (!tcx_eligible(X, m, n, np, k) || !tx_shape(np, k, sh)) return cudaErrorNotSupported;
-    sh.wait = {g_wait_polls.load(), g_wait_ns.load()};
+    sh.wait = tcx_wait_limit();
     CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
     const cuuint64_t strides[1] = {(cuuint64_t)n * 4};

@@ -162,3 +162,33 @@ def test_certified_near_ties_and_far_from_origin():
     lab, _ = okm.assign(X, C)
     assert np.array_equal(Y.cpu().numpy(), lab)
     assert rep["rescored_rows"] > 0
+
+
+def test_queued_rows_resolved_among_their_candidates():
+    """A close call carries the centroids whose BF16 g lies within the
+    certificate threshold of the least (at most four; more are flagged for
+    all k).  Groups of 4 and of 6 nearly equal centroids near the origin
+    exercise both: with tau = inf every row is queued, and labels and f must
+    equal the exact pass and the oracle bit for bit."""
+    X = gaussian_mixture(30_000, 32, 6, seed=29)
+    rng = np.random.default_rng(31)
+    C = X[rng.integers(0, X.shape[0], 16)].copy()
+    for j in (1, 2, 3):                                  # 4 centroids within 1e-3 of C[0]
+        C[j] = C[0] + np.float32(1e-3 * j)
+    for j in (5, 6, 7, 8, 9):                            # 6 within 1e-3 of C[4]: all k
+        C[j] = C[4] - np.float32(1e-3 * (j - 4))
+    Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
+    P = native.PackedBF16(Xd)
+    Yr, fr, _ = native.assign(Xd, Cd)
+    lab, fo = okm.assign(X, C)
+    lab_f = okm.exact_sum(fo)
+    assert np.array_equal(Yr.cpu().numpy(), lab) and fr == lab_f
+    for certified in (False, True):
+        Y, f, rep = native.assign_bf16(P, Cd, tau=math.inf, certified=certified)
+        assert rep["rescored_rows"] == X.shape[0]
+        assert torch.equal(Y, Yr) and f == fr
+    counts = np.bincount(lab, minlength=16)
+    assert counts[0:4].sum() > 0 and counts[4:10].sum() > 0   # both groups are nearest to some rows
+    Y, f, rep = native.assign_bf16(P, Cd, tau=0.0, certified=True)
+    assert torch.equal(Y, Yr)
+    assert 0 < rep["rescored_rows"] < X.shape[0]
