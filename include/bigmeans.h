@@ -364,9 +364,10 @@ bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const floa
  * for the full-data pass of Eq. (1) (bm_assign, bm_assign_noalloc and the
  * full passes inside a fit).  All implementations give identical labels and
  * f (the same FP32 direct-form definition, certified).
- *   impl 0 (default): by shape -- the tensor-core pass when n_pad * k > 1600
- *          (n_pad = n rounded up to 4, 8, 16, 32 or 64) and it applies, else
- *          the FP32-ALU pass;
+ *   impl 0 (default): by shape -- the tensor-core pass when n_pad * k > 512
+ *          for n_pad <= 32 and n_pad * k > 1600 for n_pad = 64 (n_pad = n
+ *          rounded up to 4, 8, 16, 32 or 64) and it applies, else the
+ *          FP32-ALU pass;
  *   impl 1: always the FP32-ALU pass (register-tiled expanded form, certified,
  *          uncertain rows re-scored in FP32);
  *   impl 2: the tensor-core pass (tcgen05, TF32 products of the expanded

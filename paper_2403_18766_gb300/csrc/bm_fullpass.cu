@@ -360,8 +360,12 @@ int last_fullpass_impl() { return g_last_impl; }
 int fullpass_impl_setting() { return g_fullpass_impl.load(); }
 // By shape: the FP32-ALU pass costs about k NP / 2 packed FMAs per row, the
 // tensor-core pass a fixed epilogue per row and centroid column, so the
-// tensor cores win once the contraction per row is large.
-bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k > 1600; }
+// tensor cores win once the contraction per row is large.  Measured on GB300
+// (10^6 x 16 and 4 10^6 x 32): the lean pass (NP <= 32) wins from NP k = 800
+// (n = 16, k = 50: 55 against 67 us; n = 32, k = 25: 201 against 264 us) and
+// loses at NP k <= 400 (n = 16, k = 25: 49 against 43 us); the NP = 64 pass
+// from NP k > 1600.
+bool fullpass_prefers_tensor(int np, int k) { return (long long)np * k > (np <= 32 ? 512 : 1600); }
 cudaError_t launch_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                             const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                             int incumbent, int sms, cudaStream_t st) {

@@ -107,76 +107,6 @@ bool tc_shape(int k, TcShape& s) {
     return false;
 }
 
-// 16 tensor-memory columns in flight into r: the wait for them takes r as
-// operands, so that no use of r can be scheduled before the wait.
-__device__ __forceinline__ void wait_ld16(unsigned (&r)[16]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15])
-                 :
-                 : "memory");
-}
-
-// g of the columns c0 + 4 q .. c0 + 4 q + 3 from 16 accumulator cells:
-// fl(ccb - 2 acc).
-__device__ __forceinline__ void g_quad(float (&e)[4], const unsigned (&va)[16], const float* ccb, int c0, int q) {
-    const float4 cq = *reinterpret_cast<const float4*>(ccb + c0 + 4 * q);
-    const float2 e01 = __ffma2_rn(make_float2(-2.f, -2.f),
-                                  make_float2(__uint_as_float(va[4 * q]), __uint_as_float(va[4 * q + 1])),
-                                  make_float2(cq.x, cq.y));
-    const float2 e23 = __ffma2_rn(make_float2(-2.f, -2.f),
-                                  make_float2(__uint_as_float(va[4 * q + 2]), __uint_as_float(va[4 * q + 3])),
-                                  make_float2(cq.z, cq.w));
-    e[0] = e01.x;
-    e[1] = e01.y;
-    e[2] = e23.x;
-    e[3] = e23.y;
-}
-__device__ __forceinline__ float min3f(float a, float b, float c) {
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-// Pass 1 over the columns c0 .. c0 + 15 (the first `nv` of them when PART):
-// four chains of the least and second least g.  Each pair of columns is
-// sorted (lo, hi) and merged: t2 = min(t2, hi, max(t1, lo)), t1 = min(t1, lo).
-template <bool PART>
-__device__ __forceinline__ void min2_chunk(float (&t1)[4], float (&t2)[4], const unsigned (&va)[16], const float* ccb,
-                                           int c0, int nv) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (PART && 4 * q >= nv) break;
-        float e[4];
-        g_quad(e, va, ccb, c0, q);
-        if (PART)                                   // columns past k: +inf
-#pragma unroll
-            for (int i = 0; i < 4; ++i) e[i] = (4 * q + i < nv) ? e[i] : __int_as_float(0x7f800000);
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const int c = (2 * q + p) & 3;
-            const float lo = fminf(e[2 * p], e[2 * p + 1]), hi = fmaxf(e[2 * p], e[2 * p + 1]);
-            t2[c] = min3f(t2[c], hi, fmaxf(t1[c], lo));
-            t1[c] = fminf(t1[c], lo);
-        }
-    }
-}
-// Pass 2 over the columns c0 .. c0 + 15 (the first `nv` when PART): bit i
-// set where g of column c0 + i is <= lim.
-template <bool PART>
-__device__ __forceinline__ unsigned le_mask16(const unsigned (&va)[16], const float* ccb, int c0, float lim, int nv) {
-    unsigned mk = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (PART && 4 * q >= nv) break;
-        float e[4];
-        g_quad(e, va, ccb, c0, q);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) mk |= (e[i] <= lim) ? (1u << (4 * q + i)) : 0u;
-    }
-    return PART ? mk & ((1u << nv) - 1u) : mk;
-}
-
 // ------------------------------------------------------ the full pass
 // Roles of a CTA (one per SM, persistent over tiles blockIdx.x + i * grid):
 //   * warp 4 G: the producer; one bulk copy (TMA) of 128 packed rows per tile
@@ -352,22 +282,22 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
                 unsigned va[16], vb[16];
                 tc::ld16(trow, va);
                 for (int c0 = 0; c0 < k; c0 += 32) {
-                    wait_ld16(va);
+                    tc::wait_ld16(va);
                     if (c0 + 16 < k) tc::ld16(trow + (unsigned)(c0 + 16), vb);
-                    if (c0 + 16 <= k) min2_chunk<false>(t1, t2, va, ccb, c0, 16);
-                    else min2_chunk<true>(t1, t2, va, ccb, c0, k - c0);
+                    if (c0 + 16 <= k) tc::min2_chunk<false>(t1, t2, va, ccb, c0, 16);
+                    else tc::min2_chunk<true>(t1, t2, va, ccb, c0, k - c0);
                     if (c0 + 16 < k) {
-                        wait_ld16(vb);
+                        tc::wait_ld16(vb);
                         if (c0 + 32 < k) tc::ld16(trow + (unsigned)(c0 + 32), va);
-                        if (c0 + 32 <= k) min2_chunk<false>(t1, t2, vb, ccb, c0 + 16, 16);
-                        else min2_chunk<true>(t1, t2, vb, ccb, c0 + 16, k - c0 - 16);
+                        if (c0 + 32 <= k) tc::min2_chunk<false>(t1, t2, vb, ccb, c0 + 16, 16);
+                        else tc::min2_chunk<true>(t1, t2, vb, ccb, c0 + 16, k - c0 - 16);
                     }
                 }
             }
             float g1 = t1[0], g2 = t2[0];
 #pragma unroll
             for (int c = 1; c < 4; ++c) {   // merge two sorted pairs
-                g2 = min3f(g2, t2[c], fmaxf(g1, t1[c]));
+                g2 = tc::min3f(g2, t2[c], fmaxf(g1, t1[c]));
                 g1 = fminf(g1, t1[c]);
             }
             // 2. the rule; for a close call the certificate threshold (the
@@ -390,15 +320,15 @@ tc_fullpass_kernel(const __nv_bfloat16* __restrict__ Xb, const float* __restrict
                 unsigned va[16], vb[16];
                 tc::ld16(trow, va);
                 for (int c0 = 0; c0 < k; c0 += 32) {
-                    wait_ld16(va);
+                    tc::wait_ld16(va);
                     if (c0 + 16 < k) tc::ld16(trow + (unsigned)(c0 + 16), vb);
-                    unsigned mk = (c0 + 16 <= k) ? le_mask16<false>(va, ccb, c0, lim, 16)
-                                                 : le_mask16<true>(va, ccb, c0, lim, k - c0);
+                    unsigned mk = (c0 + 16 <= k) ? tc::le_mask16<false>(va, ccb, c0, lim, 16)
+                                                 : tc::le_mask16<true>(va, ccb, c0, lim, k - c0);
                     if (c0 + 16 < k) {
-                        wait_ld16(vb);
+                        tc::wait_ld16(vb);
                         if (c0 + 32 < k) tc::ld16(trow + (unsigned)(c0 + 32), va);
-                        mk |= ((c0 + 32 <= k) ? le_mask16<false>(vb, ccb, c0 + 16, lim, 16)
-                                              : le_mask16<true>(vb, ccb, c0 + 16, lim, k - c0 - 16)) << 16;
+                        mk |= ((c0 + 32 <= k) ? tc::le_mask16<false>(vb, ccb, c0 + 16, lim, 16)
+                                              : tc::le_mask16<true>(vb, ccb, c0 + 16, lim, k - c0 - 16)) << 16;
                     }
                     if (cnt == 0 && mk) j1 = c0 + __ffs(mk) - 1;      // a settled row's label
                     if (!close) cnt += mk != 0u;

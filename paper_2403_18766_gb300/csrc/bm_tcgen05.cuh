@@ -148,6 +148,81 @@ __device__ __forceinline__ void ld16(unsigned taddr, unsigned (&r)[16]) {
 }
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------- epilogue helpers (g top-2)
+// Both tensor-core passes read, per row, g_j = fl(ccb_j - 2 acc_j) from the
+// accumulator columns in chunks of 16 and keep the two least g (pass 1),
+// then a bit mask of the columns with g <= lim (pass 2).
+
+// 16 tensor-memory columns in flight into r: the wait for them takes r as
+// operands, so that no use of r can be scheduled before the wait.
+__device__ __forceinline__ void wait_ld16(unsigned (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// g of the columns c0 + 4 q .. c0 + 4 q + 3 from 16 accumulator cells:
+// fl(ccb - 2 acc).
+__device__ __forceinline__ void g_quad(float (&e)[4], const unsigned (&va)[16], const float* ccb, int c0, int q) {
+    const float4 cq = *reinterpret_cast<const float4*>(ccb + c0 + 4 * q);
+    const float2 e01 = __ffma2_rn(make_float2(-2.f, -2.f),
+                                  make_float2(__uint_as_float(va[4 * q]), __uint_as_float(va[4 * q + 1])),
+                                  make_float2(cq.x, cq.y));
+    const float2 e23 = __ffma2_rn(make_float2(-2.f, -2.f),
+                                  make_float2(__uint_as_float(va[4 * q + 2]), __uint_as_float(va[4 * q + 3])),
+                                  make_float2(cq.z, cq.w));
+    e[0] = e01.x;
+    e[1] = e01.y;
+    e[2] = e23.x;
+    e[3] = e23.y;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+// Pass 1 over the columns c0 .. c0 + 15 (the first `nv` of them when PART):
+// four chains of the least and second least g.  Each pair of columns is
+// sorted (lo, hi) and merged: t2 = min(t2, hi, max(t1, lo)), t1 = min(t1, lo).
+template <bool PART>
+__device__ __forceinline__ void min2_chunk(float (&t1)[4], float (&t2)[4], const unsigned (&va)[16], const float* ccb,
+                                           int c0, int nv) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (PART && 4 * q >= nv) break;
+        float e[4];
+        g_quad(e, va, ccb, c0, q);
+        if (PART)                                   // columns past k: +inf
+#pragma unroll
+            for (int i = 0; i < 4; ++i) e[i] = (4 * q + i < nv) ? e[i] : __int_as_float(0x7f800000);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const int c = (2 * q + p) & 3;
+            const float lo = fminf(e[2 * p], e[2 * p + 1]), hi = fmaxf(e[2 * p], e[2 * p + 1]);
+            t2[c] = min3f(t2[c], hi, fmaxf(t1[c], lo));
+            t1[c] = fminf(t1[c], lo);
+        }
+    }
+}
+// Pass 2 over the columns c0 .. c0 + 15 (the first `nv` when PART): bit i
+// set where g of column c0 + i is <= lim.
+template <bool PART>
+__device__ __forceinline__ unsigned le_mask16(const unsigned (&va)[16], const float* ccb, int c0, float lim, int nv) {
+    unsigned mk = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (PART && 4 * q >= nv) break;
+        float e[4];
+        g_quad(e, va, ccb, c0, q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) mk |= (e[i] <= lim) ? (1u << (4 * q + i)) : 0u;
+    }
+    return PART ? mk & ((1u << nv) - 1u) : mk;
+}
+
 // Round to TF32 (10 explicit mantissa bits), to nearest, ties away from zero.
 __device__ __forceinline__ float to_tf32(float x) {
     unsigned r;

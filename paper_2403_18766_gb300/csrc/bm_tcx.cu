@@ -46,6 +46,7 @@
 #include <atomic>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -57,7 +58,6 @@ namespace bm {
 
 constexpr int kTxRows = 128;                  // rows per tile (MMA M)
 constexpr int kTxAtomBytes = kTxRows * 128;   // one 32-float column block of a tile
-constexpr int kTxMaxGroups = 3;              // epilogue warpgroups per CTA (2 or 3)
 constexpr int kTxMaxStages = 6;
 __host__ __device__ constexpr int tx_threads(int groups) { return 32 * (4 * groups + 2); }
 constexpr int kTxPairs = 64;                  // candidate pairs per warp and tile
@@ -483,6 +483,408 @@ tcx_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, long long m, const
     }
 }
 
+// ------------------------------------------------- lean pass for n <= 32
+// The same result as tcx_fullpass_kernel, for rows of at most 32 floats (one
+// 16 KB column block per tile), with the roles of the BF16 precision pass:
+//   * a producer warp keeps S tiles in flight (2-D TMA, 128-byte swizzle);
+//   * G epilogue warpgroups; group b takes the tiles i = b (mod G) and has NB
+//     buffer pairs (hi(x), r(x)) and NB accumulators.  It reads tile u + NB -
+//     1 into registers (x of its row), writes hi(x) = trunc_tf32(x) and r(x)
+//     = x - hi(x) to a buffer pair (the stage is then free) and hands it to
+//     the MMA warp before it reads the accumulator of tile u;
+//   * the MMA warp issues r(x).hi(c), hi(x).r(c), hi(x).hi(c) into the
+//     accumulator (the split-TF32 products and bound of tcx_fullpass_kernel).
+// Epilogue per row: pass 1 keeps the two least g (pairs of columns merged
+// with a three-input min), pass 2 the bit mask of the columns with g <= lim,
+// lim = g1 for a certified row (the first such column is its label) and
+// fl_ru(g1 + thr) otherwise (its candidates: any other centroid has a larger
+// direct form).  The distance is d32 of x (registers) against the label, or
+// the least over the candidates (lowest index on ties), c read from an FP32
+// copy; more than 8 candidates (or none: a NaN bound) are resolved by the
+// whole warp over all k, the rows read again from X.
+constexpr int kTx2MaxStages = 8;
+constexpr int kTx2Cand = 8;
+constexpr int kTx2CStride = 36;              // FP32 centroid rows: 9 units of 16 bytes apart
+
+struct Tx2Shape {
+    int ksteps, Npad, acc_stride, tmem_cols, stages, groups, nbuf;
+    tc::WaitLimit wait;
+};
+
+// [X stages: S x 16 KB][hi(x): G NB x 16 KB][r(x): G NB x 16 KB][hi(c), r(c):
+// 2 x Npad x 128 B][Cf: k x kTx2CStride floats][CC: Npad floats]
+__host__ __device__ inline size_t tx2_smem_bytes(const Tx2Shape& s, int k) {
+    return 1024 + (size_t)(s.stages + 2 * s.groups * s.nbuf) * kTxAtomBytes + (size_t)2 * s.Npad * 128 +
+           (size_t)k * kTx2CStride * 4 + (size_t)s.Npad * 4;
+}
+
+template <int NP, int NG, int NB>
+__global__ void __launch_bounds__(tx_threads(NG), 1)
+tcx2_fullpass_kernel(const __grid_constant__ CUtensorMap tmap, const float* __restrict__ X, long long m, int n,
+                     const float* __restrict__ Cw, int k, const double* sel_f, int W, int* __restrict__ labels,
+                     Globals* g, float gB, float gp2, int incumbent, Tx2Shape sh) {
+    static_assert(NP <= 32, "one column block per row");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((1024 - (tc::s_addr(smem_raw) & 1023)) & 1023);
+    const int S = sh.stages;
+    unsigned char* xs = base;                                        // X stages
+    unsigned char* xh = xs + (size_t)S * kTxAtomBytes;               // hi(x), NB per group
+    unsigned char* xl = xh + (size_t)NG * NB * kTxAtomBytes;         // r(x), NB per group
+    unsigned char* bh = xl + (size_t)NG * NB * kTxAtomBytes;         // hi(c)
+    unsigned char* bl = bh + (size_t)sh.Npad * 128;                  // r(c)
+    float* Cf = reinterpret_cast<float*>(bl + (size_t)sh.Npad * 128);
+    float* CC = Cf + (size_t)k * kTx2CStride;
+    constexpr int kEpi = 4 * NG, kProducer = kEpi, kMma = kEpi + 1, kThreads = tx_threads(NG);
+    __shared__ __align__(8) unsigned long long full[kTx2MaxStages], empty[kTx2MaxStages], conv[NG * NB],
+        accf[NG * NB];
+    __shared__ unsigned tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ unsigned __int128 red128[kThreads / 32];
+    __shared__ unsigned long long red64[kThreads / 32];
+    __shared__ unsigned int redu[kThreads / 32];
+    __shared__ CertC cert;
+    __shared__ int wsel;
+    __shared__ bool last;
+
+    if (g->nonfinite) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort = &abort_flag;
+    if (tid == 0) {
+        int best = 0;
+        if (sel_f)
+            for (int w = 1; w < W; ++w)
+                if (sel_f[w] < sel_f[best]) best = w;
+        wsel = best;
+        abort_flag = 0;
+        for (int s = 0; s < S; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 4); }
+        for (int b = 0; b < NG * NB; ++b) { tc::mbar_init(&conv[b], 4); tc::mbar_init(&accf[b], 1); }
+        tc::mbar_init_fence();
+    }
+    if (warp == kMma) tc::tmem_alloc(&tmem_slot, (unsigned)sh.tmem_cols);
+    __syncthreads();
+    const float* C = Cw + (long long)wsel * k * NP;
+    // B operands hi(c), r(c) (swizzled like the X tiles), the FP32 copy, CC
+    // and the certificate constants
+    for (int e = tid; e < sh.Npad * 8; e += kThreads) {
+        const int j = e >> 3, c = e & 7;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+        if (j < k && 4 * c < NP) {
+            const float4 cv = *reinterpret_cast<const float4*>(C + (size_t)j * NP + 4 * c);
+            h = make_float4(trunc_tf32(cv.x), trunc_tf32(cv.y), trunc_tf32(cv.z), trunc_tf32(cv.w));
+            l = make_float4(cv.x - h.x, cv.y - h.y, cv.z - h.z, cv.w - h.w);     // exact
+            *reinterpret_cast<float4*>(Cf + (size_t)j * kTx2CStride + 4 * c) = cv;
+        }
+        const size_t off = (size_t)j * 128 + ((c ^ (j & 7)) << 4);
+        *reinterpret_cast<float4*>(bh + off) = h;
+        *reinterpret_cast<float4*>(bl + off) = l;
+    }
+    unsigned int mx = 0;
+    for (int j = tid; j < sh.Npad; j += kThreads) {
+        float acc = 0.f, up = 0.f;
+        if (j < k) {
+#pragma unroll
+            for (int d = 0; d < NP; ++d) {
+                const float c = C[(size_t)j * NP + d];
+                acc = __fmaf_rn(c, c, acc);
+                up = __fmaf_ru(c, c, up);
+            }
+        }
+        CC[j] = (j < k) ? acc : __int_as_float(0x7f800000);
+        mx = max(mx, __float_as_uint(up));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) redu[warp] = mx;
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+        unsigned int mm = 0;
+        for (int i = 0; i < kThreads / 32; ++i) mm = max(mm, redu[i]);
+        cert.cmax2 = __uint_as_float(mm);
+        cert.cmax = __fsqrt_ru(cert.cmax2);
+    }
+    __syncthreads();
+    const unsigned tmem = tmem_slot;
+    const long long ntiles = (m + kTxRows - 1) / kTxRows;
+    const long long grid = gridDim.x;
+
+    unsigned __int128 facc = 0;
+    unsigned int inex = 0, resc = 0;
+    long long issued = 0;
+    if (warp == kProducer) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            long long it = 0;
+            int s = 0;
+            unsigned ph = 0;
+            for (;; ++it) {
+                const long long tile = blockIdx.x + it * grid;
+                if (tile >= ntiles) break;
+                if (it >= S && !tc::wait(&empty[s], ph ^ 1u, abort, g, sh.wait)) break;
+                tc::expect_tx(&full[s], (unsigned)kTxAtomBytes);
+                tc::tma_load_2d(xs + (size_t)s * kTxAtomBytes, &tmap, 0, (int)(tile * kTxRows), &full[s]);
+                if (++s == S) { s = 0; ph ^= 1u; }
+            }
+            issued = it;
+        }
+    } else if (warp == kMma) {
+        // --------------------------------------------------------------- MMA
+        if (lane == 0) {
+            const unsigned idesc = tc::idesc_tf32(kTxRows, sh.Npad);
+            const unsigned ah = tc::s_addr(bh), alo = tc::s_addr(bl);
+            long long it = 0;
+            for (;; ++it) {
+                const long long tile = blockIdx.x + it * grid;
+                if (tile >= ntiles) break;
+                const long long u = it / NG;                     // the group's tile index
+                const int b = (int)(it % NG) * NB + (int)(u % NB);   // buffer and accumulator
+                if (!tc::wait(&conv[b], (unsigned)((u / NB) & 1), abort, g, sh.wait)) break;
+                tc::fence_after();
+                const unsigned ax = tc::s_addr(xh + (size_t)b * kTxAtomBytes);
+                const unsigned al = tc::s_addr(xl + (size_t)b * kTxAtomBytes);
+                const unsigned d = tmem + (unsigned)(b * sh.acc_stride);
+                for (int kk = 0; kk < sh.ksteps; ++kk) {          // the correction terms first
+                    tc::mma_tf32(d, tc::desc_sw128(al + 32 * kk), tc::desc_sw128(ah + 32 * kk), idesc, kk > 0);
+                    tc::mma_tf32(d, tc::desc_sw128(ax + 32 * kk), tc::desc_sw128(alo + 32 * kk), idesc, 1);
+                }
+                for (int kk = 0; kk < sh.ksteps; ++kk)
+                    tc::mma_tf32(d, tc::desc_sw128(ax + 32 * kk), tc::desc_sw128(ah + 32 * kk), idesc, 1);
+                tc::commit(&accf[b]);
+            }
+            issued = it;
+        }
+    } else {
+        // --------------------------------------------------- epilogue groups
+        const Grids gr = grids_from_maxbits(g->maxbits);
+        const CertC cc = cert;
+        const int b = warp >> 2, q4 = warp & 3;
+        const int r = q4 * 32 + lane;                        // row within the tile = TMEM lane
+        constexpr int Q = (NP < 8 ? 8 : NP) / 4;            // 16-byte chunks the MMAs read
+        int s = b;                                          // the splits' stage: it % S, (it / S) & 1
+        unsigned ph = 0;                                    // (S is a multiple of NG)
+        float xr[NB][Q * 4];                                // x of this thread's row, per buffer
+        float xn2s[NB];                                     // bound on ||x||^2, per buffer
+        // read the group's next tile into buffer XB; false on abort
+        auto split = [&](auto XB) -> bool {
+            constexpr int x = decltype(XB)::value;
+            int ok = 1;
+            if (lane == 0) ok = tc::wait(&full[s], ph, abort, g, sh.wait);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) return false;
+            const unsigned char* st = xs + (size_t)s * kTxAtomBytes;
+            unsigned char* xhb = xh + (size_t)(b * NB + x) * kTxAtomBytes;
+            unsigned char* xlb = xl + (size_t)(b * NB + x) * kTxAtomBytes;
+            float xn2 = 0.f;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const float4 w = *reinterpret_cast<const float4*>(st + tile_off(r, q));
+                xr[x][4 * q] = w.x;
+                xr[x][4 * q + 1] = w.y;
+                xr[x][4 * q + 2] = w.z;
+                xr[x][4 * q + 3] = w.w;
+                xn2 = __fmaf_ru(w.x, w.x, xn2);
+                xn2 = __fmaf_ru(w.y, w.y, xn2);
+                xn2 = __fmaf_ru(w.z, w.z, xn2);
+                xn2 = __fmaf_ru(w.w, w.w, xn2);
+                const float4 h = make_float4(trunc_tf32(w.x), trunc_tf32(w.y), trunc_tf32(w.z), trunc_tf32(w.w));
+                *reinterpret_cast<float4*>(xhb + tile_off(r, q)) = h;
+                *reinterpret_cast<float4*>(xlb + tile_off(r, q)) =
+                    make_float4(w.x - h.x, w.y - h.y, w.z - h.z, w.w - h.w);      // exact
+            }
+            xn2s[x] = xn2;
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                tc::arrive(&empty[s]);
+                tc::arrive(&conv[b * NB + x]);
+            }
+            s += NG;
+            if (s >= S) { s -= S; ph ^= 1u; }
+            return true;
+        };
+        // the epilogue of the group's tile u, held in buffer XB: returns false
+        // when the group is done (no tile u) or on abort
+        auto epilogue = [&](long long u, auto XB) -> bool {
+            constexpr int x = decltype(XB)::value;
+            const long long it = b + u * NG;
+            const long long tile = blockIdx.x + it * grid;
+            if (tile >= ntiles) return false;
+            {   // the next tile's split, before this tile's epilogue
+                const long long ia = it + (long long)(NB - 1) * NG;
+                if (blockIdx.x + ia * grid < ntiles && !split(std::integral_constant<int, (x + NB - 1) % NB>{}))
+                    return false;
+            }
+            const long long row = tile * kTxRows + r;
+            const unsigned trow = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)((b * NB + x) * sh.acc_stride);
+            const float xn2 = xn2s[x];
+            // d32 of x against c_j (ascending d, squares rounded then added)
+            auto d32x = [&](int j) {
+                const float* cj = Cf + (size_t)j * kTx2CStride;
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < NP / 4; ++q) {
+                    const float4 c = *reinterpret_cast<const float4*>(cj + 4 * q);
+                    float t;
+                    t = __fsub_rn(xr[x][4 * q], c.x); acc = __fadd_rn(acc, __fmul_rn(t, t));
+                    t = __fsub_rn(xr[x][4 * q + 1], c.y); acc = __fadd_rn(acc, __fmul_rn(t, t));
+                    t = __fsub_rn(xr[x][4 * q + 2], c.z); acc = __fadd_rn(acc, __fmul_rn(t, t));
+                    t = __fsub_rn(xr[x][4 * q + 3], c.w); acc = __fadd_rn(acc, __fmul_rn(t, t));
+                }
+                return acc;
+            };
+            const float xn = __fsqrt_ru(xn2);
+            int okw = 1;
+            if (lane == 0) okw = tc::wait(&accf[b * NB + x], (unsigned)((u / NB) & 1), abort, g, sh.wait);
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) return false;
+            tc::fence_after();
+            // pass 1: the two least g (chunks of 16 columns)
+            float t1[4], t2[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) { t1[c] = __int_as_float(0x7f800000); t2[c] = t1[c]; }
+            for (int c0 = 0; c0 < k; c0 += 16) {
+                unsigned va[16];
+                tc::ld16(trow + (unsigned)c0, va);
+                tc::wait_ld16(va);
+                if (c0 + 16 <= k) tc::min2_chunk<false>(t1, t2, va, CC, c0, 16);
+                else tc::min2_chunk<true>(t1, t2, va, CC, c0, k - c0);
+            }
+            float g1 = t1[0], g2 = t2[0];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                g2 = tc::min3f(g2, t2[c], fmaxf(g1, t1[c]));
+                g1 = fminf(g1, t1[c]);
+            }
+            const float thr = fmaxf(cert_threshold(g1, xn2, xn, cc, gB, gp2), 0x1p-60f);
+            const bool good = row >= m || __fsub_rd(g2, g1) > thr;
+            const float lim = good ? g1 : __fadd_ru(g1, thr);
+            // pass 2: the label of a certified row, the candidates of another
+            int j1 = 0, cnt = 0;
+            unsigned lo = 0, hi = 0;
+            for (int c0 = 0; c0 < k; c0 += 16) {
+                unsigned va[16];
+                tc::ld16(trow + (unsigned)c0, va);
+                tc::wait_ld16(va);
+                const unsigned mk = (c0 + 16 <= k) ? tc::le_mask16<false>(va, CC, c0, lim, 16)
+                                                   : tc::le_mask16<true>(va, CC, c0, lim, k - c0);
+                if (cnt == 0 && mk) j1 = c0 + __ffs(mk) - 1;
+                if (good) cnt += mk != 0u;
+                unsigned mc = good ? 0u : mk;
+                while (mc) {
+                    const int j = c0 + __ffs(mc) - 1;
+                    mc &= mc - 1u;
+                    if (cnt < kTx2Cand) {
+                        hi = (hi << 8) | (lo >> 24);
+                        lo = (lo << 8) | (unsigned)j;
+                    }
+                    ++cnt;
+                }
+            }
+            tc::fence_before();             // accumulator read; its next MMA waits on conv
+            // the distance: d32 to the label, or the least over the candidates
+            int lab = j1;
+            float dv = __int_as_float(0x7f800000);
+            const bool many = !good && (cnt < 1 || cnt > kTx2Cand);
+            const int nd = (row >= m || many) ? 0 : (good ? 1 : cnt);
+            for (int c = 0; c < nd; ++c) {
+                const int j = good ? j1 : (int)(((c < 4 ? lo : hi) >> (8 * (c & 3))) & 0xffu);
+                const float d = d32x(j);
+                if (d < dv || (d == dv && j < lab)) { dv = d; lab = j; }
+            }
+            if (!good && row < m) ++resc;
+            unsigned pend = __ballot_sync(0xffffffffu, many && row < m);
+            while (pend) {                                  // all k, lanes over centroids
+                const int src = __ffs(pend) - 1;
+                pend &= pend - 1u;
+                const long long srow = __shfl_sync(0xffffffffu, row, src);
+                const float* xg = X + srow * n;
+                float bd = __int_as_float(0x7f800000);
+                int bj = 0x7fffffff;
+                for (int j = lane; j < k; j += 32) {
+                    const float* cj = Cf + (size_t)j * kTx2CStride;
+                    float acc = 0.f;
+                    for (int d = 0; d < n; ++d) {
+                        const float t = __fsub_rn(xg[d], cj[d]);
+                        acc = __fadd_rn(acc, __fmul_rn(t, t));
+                    }
+                    if (acc < bd || bj == 0x7fffffff) { bd = acc; bj = j; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+                    if (od < bd || (od == bd && oj < bj)) { bd = od; bj = oj; }
+                }
+                if (lane == src) { dv = bd; lab = bj; }
+            }
+            if (row < m) {
+                acc_obj(facc, dv, gr.gf, inex);
+                if (labels) labels[row] = lab;
+            }
+            return true;
+        };
+        bool ok = true;
+        if (NB == 2 && blockIdx.x + (long long)b * grid < ntiles)   // run ahead by one tile
+            ok = split(std::integral_constant<int, 0>{});
+        for (long long u = 0; ok; u += NB) {
+            if (!epilogue(u, std::integral_constant<int, 0>{})) break;
+            if (NB == 2 && !epilogue(u + 1, std::integral_constant<int, (NB == 2 ? 1 : 0)>{})) break;
+        }
+    }
+
+    // teardown (as in tcx_fullpass_kernel)
+    tc::fence_before();
+    __syncthreads();
+    if (*abort) {
+        if (warp == kProducer && lane == 0)
+            for (long long i = (issued > S ? issued - S : 0); i < issued; ++i)
+                for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&full[i % S], (unsigned)((i / S) & 1)); ++p) {}
+        if (warp == kMma && lane == 0 && issued > 0) {
+            const long long il = issued - 1, ul = il / NG;
+            const int bl = (int)(il % NG) * NB + (int)(ul % NB);
+            for (unsigned p = 0; p < (1u << 22) && !tc::try_wait(&accf[bl], (unsigned)((ul / NB) & 1)); ++p) {}
+        }
+        __syncthreads();
+    }
+    if (warp == kMma) {
+        tc::fence_after();
+        tc::tmem_dealloc(tmem, (unsigned)sh.tmem_cols);
+    }
+    const unsigned __int128 F = warp_sum_u128(facc);
+    const unsigned long long IR = warp_sum(((unsigned long long)inex << 32) | resc);
+    if (lane == 0) { red128[warp] = F; red64[warp] = IR; }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned __int128 T = 0;
+        unsigned long long ir = 0;
+        for (int i = 0; i < kThreads / 32; ++i) { T += red128[i]; ir += red64[i]; }
+        for (int i = 0; i < 4; ++i) {
+            const unsigned long long chunk = (unsigned long long)((T >> (32 * i)) & 0xffffffffu);
+            if (chunk) atomicAdd(&g->obj_words[i], chunk);
+        }
+        if (ir >> 32) atomicAdd(&g->inexact, ir >> 32);
+        if (ir & 0xffffffffull) atomicAdd(&g->rescored, ir & 0xffffffffull);
+        __threadfence();
+        last = (atomicAdd(&g->done_ctas, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        unsigned __int128 T = 0;
+        for (int i = 0; i < 4; ++i) {
+            T += (unsigned __int128)atomicAdd(&g->obj_words[i], 0ull) << (32 * i);
+            g->obj_words[i] = 0;
+        }
+        const double f = u128_to_double(T, grids_from_maxbits(g->maxbits).gf);
+        g->f_full = f;
+        if (incumbent && f < g->f_incumbent) g->f_incumbent = f;
+        g->best_worker = wsel;
+        g->done_ctas = 0;
+    }
+}
+
 // ------------------------------------------------------------ host side
 namespace {
 
@@ -570,14 +972,72 @@ cudaError_t launch_g(const CUtensorMap& tm, long long m, const float* C, int k, 
     return launch_t<NP, 1>(tm, m, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
 }
 
+// Lean pass (n <= 32): four groups with one buffer pair each where tensor
+// memory and shared memory allow, else two groups with two pairs, else two
+// with one; the stage count a multiple of the group count.
+bool tx2_shape(int np, int k, Tx2Shape& s) {
+    if (np > 32 || k < 1 || k > 256) return false;
+    s.ksteps = std::max(1, np / 8);
+    s.Npad = (k + 15) & ~15;
+    s.acc_stride = (s.Npad + 31) & ~31;
+    constexpr size_t kDyn = 219 * 1024;
+    const int order[3][2] = {{4, 1}, {2, 2}, {2, 1}};
+    for (const auto& o : order) {
+        s.groups = o[0];
+        s.nbuf = o[1];
+        int cols = 32;
+        while (cols < s.groups * s.nbuf * s.acc_stride) cols <<= 1;
+        if (cols > 512) continue;
+        s.tmem_cols = cols;
+        for (s.stages = (kTx2MaxStages / s.groups) * s.groups; s.stages >= s.groups; s.stages -= s.groups)
+            if (tx2_smem_bytes(s, k) <= kDyn) return true;
+    }
+    return false;
+}
+
+template <int NP, int NG, int NB>
+cudaError_t launch2_t(const CUtensorMap& tm, const float* X, long long m, int n, const float* C, int k,
+                      const double* sel_f, int W,
+                      int* labels, Globals* g, float gB, float gp2, int incumbent, int sms, const Tx2Shape& sh,
+                      cudaStream_t st) {
+    constexpr int threads = tx_threads(NG);
+    const size_t smem = tx2_smem_bytes(sh, k);
+    cudaFuncAttributes fa;
+    cudaError_t e = func_attributes((const void*)tcx2_fullpass_kernel<NP, NG, NB>, &fa);
+    if (e != cudaSuccess) return e;
+    const int warps_alloc = (threads / 32 + 3) & ~3;
+    if ((long long)fa.numRegs * 32 * warps_alloc > 65536 || smem + fa.sharedSizeBytes > 227 * 1024)
+        return cudaErrorNotSupported;
+    e = allow_max_smem((const void*)tcx2_fullpass_kernel<NP, NG, NB>);
+    if (e != cudaSuccess) return e;
+    // one CTA per SM (its registers), persistent over tiles
+    const long long tiles = (m + kTxRows - 1) / kTxRows;
+    const long long grid = std::max<long long>(1, std::min<long long>((long long)sms, tiles));
+    tcx2_fullpass_kernel<NP, NG, NB><<<(unsigned)grid, threads, smem, st>>>(tm, X, m, n, C, k, sel_f, W, labels, g,
+                                                                            gB, gp2, incumbent, sh);
+    return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t launch2_g(const CUtensorMap& tm, const float* X, long long m, int n, const float* C, int k,
+                      const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2, int incumbent, int sms,
+                      const Tx2Shape& sh, cudaStream_t st) {
+    if (sh.groups == 4)
+        return launch2_t<NP, 4, 1>(tm, X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
+    if (sh.nbuf == 2)
+        return launch2_t<NP, 2, 2>(tm, X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
+    return launch2_t<NP, 2, 1>(tm, X, m, n, C, k, sel_f, W, labels, g, gB, gp2, incumbent, sms, sh, st);
+}
+
 }  // namespace
 
 // Whether the tensor-core pass takes (X, n, k): n % 4 == 0 (TMA row
 // stride), X 16-byte aligned, n <= 64, 1 <= k <= 256, m < 2^31.
 bool tcx_eligible(const float* X, long long m, int n, int np, int k) {
     TxShape s;
-    return n % 4 == 0 && (((uintptr_t)X) & 15) == 0 && m >= 1 && m < (1ll << 31) && tx_shape(np, k, s) &&
-           encode_fn() != nullptr;
+    Tx2Shape s2;
+    return n % 4 == 0 && (((uintptr_t)X) & 15) == 0 && m >= 1 && m < (1ll << 31) &&
+           (np <= 32 ? tx2_shape(np, k, s2) : tx_shape(np, k, s)) && encode_fn() != nullptr;
 }
 
 // Certificate factor of the split-TF32 products (see the file comment).
@@ -585,6 +1045,7 @@ float tcx_gamma(int np) {
     const int ksteps = std::max(1, np / 8);
     return 2.0f * (float)(ksteps * 9) * 0x1p-23f + 8.0f * 0x1p-20f;
 }
+
 
 // Limits of the bounded waits of the next launches (process-wide).
 static std::atomic<unsigned> g_wait_polls{tc::kDefaultWait.polls}, g_wait_ns{tc::kDefaultWait.ns};
@@ -599,9 +1060,7 @@ tc::WaitLimit tcx_wait_limit() { return {g_wait_polls.load(), g_wait_ns.load()};
 cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, const float* C, int k,
                                 const double* sel_f, int W, int* labels, Globals* g, float gB, float gp2,
                                 int incumbent, int sms, cudaStream_t st) {
-    TxShape sh;
-    if (!tcx_eligible(X, m, n, np, k) || !tx_shape(np, k, sh)) return cudaErrorNotSupported;
-    sh.wait = tcx_wait_limit();
+    if (!tcx_eligible(X, m, n, np, k)) return cudaErrorNotSupported;
     CUtensorMap tm;
     const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
     const cuuint64_t strides[1] = {(cuuint64_t)n * 4};
@@ -612,6 +1071,20 @@ cudaError_t launch_tcx_fullpass(int np, const float* X, long long m, int n, cons
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
     const float gBt = std::max(gB, tcx_gamma(np));
+    Tx2Shape s2;
+    if (np <= 32 && tx2_shape(np, k, s2)) {
+        s2.wait = tcx_wait_limit();
+        switch (np) {
+            case 4: return launch2_g<4>(tm, X, m, n, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, s2, st);
+            case 8: return launch2_g<8>(tm, X, m, n, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, s2, st);
+            case 16: return launch2_g<16>(tm, X, m, n, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, s2, st);
+            case 32: return launch2_g<32>(tm, X, m, n, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, s2, st);
+        }
+        return cudaErrorNotSupported;
+    }
+    TxShape sh;
+    if (!tx_shape(np, k, sh)) return cudaErrorNotSupported;
+    sh.wait = tcx_wait_limit();
     switch (np) {
         case 4: return launch_g<4>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);
         case 8: return launch_g<8>(tm, m, C, k, sel_f, W, labels, g, gBt, gp2, incumbent, sms, sh, st);

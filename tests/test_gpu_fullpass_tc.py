@@ -76,9 +76,11 @@ def test_widest_case_both_passes():
     assert np.array_equal(Y1, Y0) and f1 == f0
 
 
-@pytest.mark.parametrize("n,k,want", [(16, 25, 1), (64, 100, 2), (32, 50, 1), (32, 64, 2), (3, 100, 1)])
+@pytest.mark.parametrize("n,k,want", [(16, 25, 1), (16, 50, 2), (32, 10, 1), (32, 50, 2), (64, 25, 1), (64, 100, 2),
+                                     (3, 100, 1)])
 def test_default_choice_by_shape(n, k, want):
-    """impl 0 takes the tensor cores once n_pad * k > 1600 (and n % 4 == 0)."""
+    """impl 0 takes the tensor cores once n_pad * k > 512 (n_pad <= 32) or
+    > 1600 (n_pad = 64), where n % 4 == 0."""
     X = gaussian_mixture(5000, n, 6, seed=n + k)
     C = X[np.random.default_rng(k).integers(0, X.shape[0], k)].copy()
     native.set_fullpass_impl(0)
