@@ -172,6 +172,35 @@ bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k
                             bm_report* report_out);
 
 /* ---------------------------------------------------------------------------
+ * bigmeans_fit_dt -- bigmeans_fit with the storage type of X and the mode of
+ * the full-data pass (the precision form of the full pass, NEXT-2, reached
+ * through the fit entry point).
+ *   dt = BM_F32:  X_dev is the m x n float32 matrix; X_master_dev is NULL or
+ *                 X_dev.
+ *   dt = BM_BF16: X_dev holds X packed by bm_pack_bf16 (m_pad x 128 bytes,
+ *                 1024-byte aligned) and X_master_dev the m x n float32
+ *                 master, the same matrix (required).
+ *   mode = BM_MODE_EXACT: results of bigmeans_fit on the FP32 rows.
+ *   mode = BM_MODE_FAST:  the same fit (samples, Lloyd and the recheck read
+ *                 the FP32 rows: the exact-mode sums and certificates are
+ *                 defined on them), then labels and f(C_best, X) from the
+ *                 precision pass, bm_assign_bf16 with tau = 1e-3, on the BF16
+ *                 rows (BM_F32: packed into a workspace of m_pad x 128 bytes
+ *                 first); report->f_full is that f and report->rescored_rows
+ *                 its re-scored rows.  n <= 64.
+ * Other arguments, ownership and errors as for bigmeans_fit; BM_EINVAL for
+ * an unknown dt or mode, a missing master, or a misaligned BF16 X_dev.
+ * ------------------------------------------------------------------------- */
+typedef enum { BM_F32 = 0, BM_BF16 = 1 } bm_dtype;
+typedef enum { BM_MODE_EXACT = 0, BM_MODE_FAST = 1 } bm_mode;
+bm_status bigmeans_fit_dt(const void* X_dev, const float* X_master_dev, bm_dtype dt,
+                          int64_t m, int32_t n, int32_t k,
+                          const bm_sample_policy* policy, const bm_budget* budget,
+                          uint64_t seed, bm_mode mode, void* stream,
+                          float* C_out_dev, int32_t* labels_out_dev,
+                          bm_report* report_out);
+
+/* ---------------------------------------------------------------------------
  * Staged fit: the same computation as bigmeans_fit, split so that rounds can
  * be run (and timed) one batch at a time.  bm_fit_create validates X,
  * allocates the workspace and initialises the workers (Alg. 1

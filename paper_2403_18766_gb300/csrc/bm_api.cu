@@ -1152,7 +1152,16 @@ bm_status bm_fit_worker_centroids(bm_fit_ctx* c, int32_t w, float* C_out_dev) {
     return BM_OK;
 }
 
+static bm_status fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep,
+                            bool full_pass);
 bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep) {
+    return fit_finish(c, C_out_dev, labels_out_dev, rep, true);
+}
+
+// The common recheck and C_best; with full_pass, the exact full-data pass
+// gives the labels and f(C_best, X) (else the caller takes them another way).
+static bm_status fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev, bm_report* rep,
+                            bool full_pass) {
     if (!c) return fail(BM_EINVAL, "ctx is NULL");
     if (c->w_lo != 0 || c->w_hi != c->pol.workers)
         return fail(BM_EINVAL, "a shard of workers finishes through bm_fit_recheck and the ranks' exchange");
@@ -1169,7 +1178,7 @@ bm_status bm_fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out_dev
     CU(launch_worker(c->np, a, c->pol.workers, c->st));
     c->n_kernels += 2;
     span_end(c, sp);
-    if ((s = run_fullpass(c, c->f_final, labels_out_dev, 1))) return s;
+    if (full_pass && (s = run_fullpass(c, c->f_final, labels_out_dev, 1))) return s;
     CU(launch_select_unpad(c->Cw, c->f_final, c->pol.workers, c->k, c->n, c->np, C_out_dev, c->st));
     Globals h;
     if ((s = read_globals(c, &h))) return s;
@@ -1219,6 +1228,62 @@ bm_status bigmeans_fit(const float* X_dev, int64_t m, int32_t n, int32_t k, cons
     s = bm_fit_finish(c, C_out_dev, labels_out_dev, report_out);
     bm_fit_destroy(c);
     return s;
+}
+
+static bm_status assign_bf16(const void* Xb_dev, const float* norms_dev, const float* X_dev, int64_t m, int32_t n,
+                             const float* C_dev, int32_t k, float tau, int certify, int32_t* labels_out_dev,
+                             double* f_out_host, bm_report* rep, void* stream);
+
+bm_status bigmeans_fit_dt(const void* X_dev, const float* X_master_dev, bm_dtype dt, int64_t m, int32_t n,
+                          int32_t k, const bm_sample_policy* policy, const bm_budget* budget, uint64_t seed,
+                          bm_mode mode, void* stream, float* C_out_dev, int32_t* labels_out_dev,
+                          bm_report* report_out) {
+    if (dt != BM_F32 && dt != BM_BF16) return fail(BM_EINVAL, "dt = %d is not BM_F32 or BM_BF16", (int)dt);
+    if (mode != BM_MODE_EXACT && mode != BM_MODE_FAST) return fail(BM_EINVAL, "mode = %d is not a bm_mode", (int)mode);
+    if (!X_dev) return fail(BM_EINVAL, "X_dev is NULL");
+    if (dt == BM_F32 && X_master_dev && (const void*)X_master_dev != X_dev)
+        return fail(BM_EINVAL, "BM_F32: X_master_dev must be NULL or X_dev");
+    if (dt == BM_BF16 && !X_master_dev) return fail(BM_EINVAL, "BM_BF16 needs the FP32 master X_master_dev");
+    const float* Xf = dt == BM_F32 ? static_cast<const float*>(X_dev) : X_master_dev;
+    if (mode == BM_MODE_EXACT)
+        return bigmeans_fit(Xf, m, n, k, policy, budget, seed, stream, C_out_dev, labels_out_dev, report_out);
+    // fast: the fit on the FP32 rows, then labels and f(C_best, X) from the
+    // precision pass (tau = 1e-3) on the BF16 rows
+    bm_status s = check_shape(m, n, k);
+    if (s) return s;
+    if (n > 64) return fail(BM_EINVAL, "BM_MODE_FAST needs n <= 64");
+    if (dt == BM_BF16 && (((uintptr_t)X_dev) & 1023)) return fail(BM_EINVAL, "BF16 X_dev must be 1024-byte aligned");
+    bm_fit_ctx* c = nullptr;
+    if ((s = bm_fit_create(Xf, m, n, k, policy, budget, seed, stream, &c))) return s;
+    const int T = budget->rounds > 0 ? budget->rounds : 0x3fffffff;
+    if (!(s = bm_fit_rounds(c, T))) s = fit_finish(c, C_out_dev, nullptr, report_out, false);
+    bm_fit_destroy(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long m_pad = (m + 127) / 128 * 128;
+    const size_t xb_bytes = dt == BM_F32 ? (size_t)m_pad * 128 : 0;
+    void* base = nullptr;
+    CU(lib_alloc(&base, xb_bytes + (size_t)(m_pad + 1) * 4 + 1024, st));
+    void* Xb = dt == BM_F32 ? (void*)(((uintptr_t)base + 1023) & ~(uintptr_t)1023) : const_cast<void*>(X_dev);
+    float* norms = reinterpret_cast<float*>(((uintptr_t)base + 1023) & ~(uintptr_t)1023) + xb_bytes / 4;
+    cudaError_t e = launch_pack_bf16(Xf, m, n, m_pad, dt == BM_F32 ? Xb : nullptr, norms, st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, st);
+        cudaStreamSynchronize(st);
+        return fail(BM_ECUDA, "pack: %s", cudaGetErrorString(e));
+    }
+    double f = 0.0;
+    bm_report rb;
+    s = assign_bf16(Xb, norms, Xf, m, n, C_out_dev, k, 1e-3f, 0, labels_out_dev, &f, &rb, stream);
+    cudaFreeAsync(base, st);
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s) return s;
+    if (e2 != cudaSuccess) return fail(BM_ECUDA, "fast pass: %s", cudaGetErrorString(e2));
+    if (report_out) {
+        report_out->f_full = f;
+        report_out->rescored_rows = rb.rescored_rows;
+    }
+    return BM_OK;
 }
 
 bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k,

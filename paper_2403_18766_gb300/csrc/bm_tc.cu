@@ -38,9 +38,10 @@ constexpr int kTcK = 64;               // packed row width (BF16 elements)
 // ------------------------------------------------------------------ pack
 // Xb[r][chunk c ^ (r & 7)] holds elements 8c .. 8c+7 of row r (BF16, RN);
 // rows m .. m_pad-1 and elements n .. 63 are zero.  norms[r] = fl(sum x_b^2).
+// Xb may be NULL: the norms (and the max |x|) alone.
 __global__ void pack_bf16_kernel(const float* __restrict__ X, long long m, int n, long long m_pad,
                                  __nv_bfloat16* __restrict__ Xb, float* __restrict__ norms) {
-    const long long total = m_pad * (kTcK / 8);                 // 16-byte chunks
+    const long long total = Xb ? m_pad * (kTcK / 8) : 0;       // 16-byte chunks (none: norms only)
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const long long r = e / (kTcK / 8);
@@ -545,7 +546,7 @@ size_t tc_smem_bytes(int k) {
 
 cudaError_t launch_pack_bf16(const float* X, long long m, int n, long long m_pad, void* Xb, float* norms,
                              cudaStream_t st) {
-    const long long total = m_pad * (kTcK / 8);
+    const long long total = std::max<long long>(m_pad * (kTcK / 8) * (Xb ? 1 : 0), m_pad);
     const int grid = (int)std::min<long long>(8192, (total + 255) / 256);
     cudaError_t e = cudaMemsetAsync(norms + m_pad, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;

@@ -89,6 +89,7 @@ _PP, _BP, _RP = ctypes.POINTER(SamplePolicy), ctypes.POINTER(Budget), ctypes.POI
 # Every symbol include/bigmeans.h declares, with its signature.
 SIGNATURES = {
     "bigmeans_fit": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
+    "bigmeans_fit_dt": (_i32, [_p, _p, _i32, _i64, _i32, _i32, _PP, _BP, _u64, _i32, _p, _p, _p, _RP]),
     "bigmeans_fit_host": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
     "bm_fit_create": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_p)]),
     "bm_fit_rounds": (_i32, [_p, _i32]),
@@ -202,6 +203,29 @@ def fit(X, k, policy, budget, seed=0, labels=True, stream=None):
     rep = Report()
     _check(lib.bigmeans_fit(_ptr(X), m, n, k, ctypes.byref(policy), ctypes.byref(budget), seed,
                             _stream(stream), _ptr(C), _ptr(Y), ctypes.byref(rep)))
+    return C, Y, rep.as_dict()
+
+
+BM_F32, BM_BF16 = 0, 1
+BM_MODE_EXACT, BM_MODE_FAST = 0, 1
+
+
+def fit_dt(X, k, policy, budget, seed=0, mode=BM_MODE_EXACT, labels=True, stream=None):
+    """bigmeans_fit_dt.  X: a CUDA float32 tensor (BM_F32) or a PackedBF16
+    (BM_BF16, its FP32 master as X_master).  mode: BM_MODE_EXACT or
+    BM_MODE_FAST.  Returns (C, labels|None, report)."""
+    if isinstance(X, PackedBF16):
+        Xd, Xm, dt = X.Xb, X.X, BM_BF16
+    else:
+        Xd = _dev_f32(X, "X")
+        Xm, dt = None, BM_F32
+    master = Xm if Xm is not None else Xd
+    m, n = master.shape
+    C = torch.empty((k, n), dtype=torch.float32, device=master.device)
+    Y = torch.empty(m, dtype=torch.int32, device=master.device) if labels else None
+    rep = Report()
+    _check(lib.bigmeans_fit_dt(_ptr(Xd), _ptr(Xm), dt, m, n, k, ctypes.byref(policy), ctypes.byref(budget), seed,
+                               int(mode), _stream(stream), _ptr(C), _ptr(Y), ctypes.byref(rep)))
     return C, Y, rep.as_dict()
 
 
