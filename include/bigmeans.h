@@ -261,6 +261,29 @@ bm_status bm_fit_worker_centroids(bm_fit_ctx* ctx, int32_t w, float* C_out_dev);
 bm_status bm_fit_report(bm_fit_ctx* ctx, bm_report* report_out);
 void bm_fit_destroy(bm_fit_ctx* ctx);
 
+/* Checkpoint and resume of a staged fit (between rounds).
+ * bm_fit_state_size: bytes of the state of ctx now (it grows with |L|).
+ * bm_fit_export: waits for ctx's work, then writes its state to host_buf
+ *   (bytes >= bm_fit_state_size): the workers' incumbent centroids,
+ *   degenerate flags and f_hat, the list L of accepted sizes, the device
+ *   counters of the report and the number of rounds run.  ctx is unchanged.
+ * bm_fit_import: loads such a state into ctx, which must have been created
+ *   by bm_fit_create on the same X with the same n, k, seed, size policy,
+ *   max_lloyd, tol, kpp_candidates and eval_full_each_round (budget.rounds
+ *   and budget.seconds may differ; L must fit the new budget), the same
+ *   worker range, and must not have run a round yet.  Rounds run after the
+ *   import continue the fit exactly: samples, seeds and sizes are functions
+ *   of (seed, worker, round, pass), so in round-count mode the result equals
+ *   the uninterrupted fit's bit for bit.  A wall-clock budget counts from the
+ *   new context's creation.  BM_EINVAL for a truncated or foreign state or a
+ *   context that differs (checked: shape, workers, passes, worker range,
+ *   seed, a fingerprint of the policy and budget settings and of max |x|).
+ *   host_buf is the caller's (plain host memory; the format is this
+ *   library's, versioned, with no pointers in it). */
+bm_status bm_fit_state_size(bm_fit_ctx* ctx, int64_t* bytes_out);
+bm_status bm_fit_export(bm_fit_ctx* ctx, void* host_buf, int64_t bytes);
+bm_status bm_fit_import(bm_fit_ctx* ctx, const void* host_buf, int64_t bytes);
+
 /* ---------------------------------------------------------------------------
  * Step entry points (each one is a single step of the hot path; the fit runs
  * the same device code fused into one kernel per round).

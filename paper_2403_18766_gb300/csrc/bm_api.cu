@@ -1187,6 +1187,157 @@ static bm_status fit_finish(bm_fit_ctx* c, float* C_out_dev, int32_t* labels_out
     return BM_OK;
 }
 
+// ------------------------------------------------------ checkpoint/resume
+// The state of a fit between rounds: the workers' incumbent centroids,
+// degenerate flags and f_hat, the list L, the device counters and the round
+// index.  Samples, seeds and sizes are functions of (seed, worker, round,
+// pass), so a fit resumed from this state on the same X with the same
+// arguments draws what the uninterrupted fit would draw.
+}  // extern "C"
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int64_t m;
+    int32_t n, k, np, W, P, w_lo, w_hi, rounds_run;
+    uint64_t seed, fingerprint;
+    int64_t n_L;                                  // entries of L exported
+    uint64_t b_glob, b_Cw, b_deg, b_fhat, b_L;   // section sizes in bytes
+    double t_worker, t_full, t_sample;
+    int64_t n_worker, n_full, n_kernels;
+};
+constexpr char kStateMagic[8] = {'B', 'M', 'F', 'I', 'T', 'S', 'T', '1'};
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+// The arguments that decide the computation (not the wall budget or T).
+uint64_t state_fingerprint(const bm_fit_ctx* c, unsigned int maxbits) {
+    uint64_t h = 1469598103934665603ull;
+    const auto add = [&](const auto& v) { h = fnv1a(h, &v, sizeof v); };
+    add(c->pol.s_min); add(c->s_hi); add(c->pol.set_len);
+    for (int i = 0; i < c->pol.set_len && i < 16; ++i) add(c->pol.set[i]);
+    add(c->pol.workers); add(c->pol.passes); add(c->pol.kind); add(c->pol.exploit);
+    add(c->bud.max_lloyd); add(c->bud.tol); add(c->bud.kpp_candidates); add(c->bud.eval_full_each_round);
+    add(maxbits);
+    return h;
+}
+size_t state_sections(const bm_fit_ctx* c, int64_t n_L, uint64_t* b) {
+    b[0] = sizeof(Globals);
+    b[1] = (uint64_t)c->pol.workers * c->k * c->np * 4;
+    b[2] = (uint64_t)c->pol.workers * c->k;
+    b[3] = (uint64_t)c->pol.workers * 8;
+    b[4] = (uint64_t)n_L * 8;
+    return sizeof(StateHeader) + b[0] + b[1] + b[2] + b[3] + b[4];
+}
+// Both streams of the fit idle (the next round's samples may be drawn ahead).
+bm_status fit_quiesce(bm_fit_ctx* c) {
+    if (c->sst) CU(cudaStreamSynchronize(c->sst));
+    CU(cudaStreamSynchronize(c->st));
+    return BM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+bm_status bm_fit_state_size(bm_fit_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return fail(BM_EINVAL, "ctx and bytes are required");
+    bm_status s = fit_quiesce(c);
+    if (s) return s;
+    Globals h;
+    if ((s = read_globals(c, &h))) return s;
+    uint64_t b[5];
+    *bytes = (int64_t)state_sections(c, std::min<long long>((long long)h.accepts, c->L_cap), b);
+    return BM_OK;
+}
+
+bm_status bm_fit_export(bm_fit_ctx* c, void* host_buf, int64_t bytes) {
+    if (!c || !host_buf) return fail(BM_EINVAL, "ctx and host_buf are required");
+    bm_status s = fit_quiesce(c);
+    if (s) return s;
+    Globals h;
+    if ((s = read_globals(c, &h))) return s;
+    if ((s = status_from_flags(h))) return s;
+    const int64_t n_L = std::min<long long>((long long)h.accepts, c->L_cap);
+    StateHeader hd;
+    memset(&hd, 0, sizeof hd);
+    uint64_t b[5];
+    const size_t total = state_sections(c, n_L, b);
+    hd.b_glob = b[0]; hd.b_Cw = b[1]; hd.b_deg = b[2]; hd.b_fhat = b[3]; hd.b_L = b[4];
+    if (bytes < (int64_t)total) return fail(BM_EINVAL, "host_buf holds %lld bytes, the state %zu", (long long)bytes, total);
+    memcpy(hd.magic, kStateMagic, 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof hd;
+    hd.m = c->m; hd.n = c->n; hd.k = c->k; hd.np = c->np; hd.W = c->pol.workers; hd.P = c->pol.passes;
+    hd.w_lo = c->w_lo; hd.w_hi = c->w_hi; hd.rounds_run = c->rounds_run;
+    hd.seed = c->seed;
+    hd.fingerprint = state_fingerprint(c, h.maxbits);
+    hd.n_L = n_L;
+    hd.t_worker = c->t_worker; hd.t_full = c->t_full; hd.t_sample = c->t_sample;
+    hd.n_worker = c->n_worker; hd.n_full = c->n_full; hd.n_kernels = c->n_kernels;
+    char* out = static_cast<char*>(host_buf);
+    memcpy(out, &hd, sizeof hd);
+    size_t off = sizeof hd;
+    memcpy(out + off, &h, sizeof h);
+    off += hd.b_glob;
+    const void* src[4] = {c->Cw, c->deg, c->fhat, c->L_buf};
+    const uint64_t len[4] = {hd.b_Cw, hd.b_deg, hd.b_fhat, hd.b_L};
+    for (int i = 0; i < 4; ++i) {
+        if (len[i]) CU(cudaMemcpyAsync(out + off, src[i], len[i], cudaMemcpyDeviceToHost, c->st));
+        off += len[i];
+    }
+    CU(cudaStreamSynchronize(c->st));
+    return BM_OK;
+}
+
+bm_status bm_fit_import(bm_fit_ctx* c, const void* host_buf, int64_t bytes) {
+    if (!c || !host_buf) return fail(BM_EINVAL, "ctx and host_buf are required");
+    if (c->rounds_run != 0 || c->prefetched >= 0) return fail(BM_EINVAL, "import into a context before its first round");
+    if (bytes < (int64_t)sizeof(StateHeader)) return fail(BM_EINVAL, "state of %lld bytes is truncated", (long long)bytes);
+    StateHeader hd;
+    memcpy(&hd, host_buf, sizeof hd);
+    if (memcmp(hd.magic, kStateMagic, 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof hd)
+        return fail(BM_EINVAL, "not a fit state of this library version");
+    bm_status s = fit_quiesce(c);
+    if (s) return s;
+    Globals h;
+    if ((s = read_globals(c, &h))) return s;
+    if (hd.m != c->m || hd.n != c->n || hd.k != c->k || hd.np != c->np || hd.W != c->pol.workers ||
+        hd.P != c->pol.passes || hd.w_lo != c->w_lo || hd.w_hi != c->w_hi || hd.seed != c->seed)
+        return fail(BM_EINVAL, "state of another fit (shape, workers, passes, shard or seed differ)");
+    if (hd.fingerprint != state_fingerprint(c, h.maxbits))
+        return fail(BM_EINVAL, "state of another fit (size policy, budget settings or X differ)");
+    if (hd.rounds_run < 0 || hd.n_L < 0 || hd.n_L > c->L_cap)
+        return fail(BM_EINVAL, "state's L (%lld entries) does not fit this context (%lld)", (long long)hd.n_L,
+                    (long long)c->L_cap);
+    uint64_t b[5];
+    const size_t total = state_sections(c, hd.n_L, b);
+    if (b[0] != hd.b_glob || b[1] != hd.b_Cw || b[2] != hd.b_deg || b[3] != hd.b_fhat || b[4] != hd.b_L)
+        return fail(BM_EINVAL, "state sections do not match this context");
+    if (bytes < (int64_t)total) return fail(BM_EINVAL, "state of %lld bytes is truncated (%zu)", (long long)bytes, total);
+    const char* in = static_cast<const char*>(host_buf);
+    size_t off = sizeof hd;
+    Globals g;
+    memcpy(&g, in + off, sizeof g);
+    if (g.maxbits != h.maxbits) return fail(BM_EINVAL, "state of another X");
+    off += hd.b_glob;
+    CU(cudaMemcpyAsync(c->glob, &g, sizeof g, cudaMemcpyHostToDevice, c->st));
+    void* dst[4] = {c->Cw, c->deg, c->fhat, c->L_buf};
+    const uint64_t len[4] = {hd.b_Cw, hd.b_deg, hd.b_fhat, hd.b_L};
+    for (int i = 0; i < 4; ++i) {
+        if (len[i]) CU(cudaMemcpyAsync(dst[i], in + off, len[i], cudaMemcpyHostToDevice, c->st));
+        off += len[i];
+    }
+    CU(cudaStreamSynchronize(c->st));
+    c->rounds_run = hd.rounds_run;
+    c->t_worker = hd.t_worker; c->t_full = hd.t_full; c->t_sample = hd.t_sample;
+    c->n_worker = hd.n_worker; c->n_full = hd.n_full; c->n_kernels = hd.n_kernels;
+    return BM_OK;
+}
+
 bm_status bm_fit_report(bm_fit_ctx* c, bm_report* rep) {
     if (!c || !rep) return fail(BM_EINVAL, "ctx and report are required");
     Globals h;

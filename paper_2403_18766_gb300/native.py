@@ -90,6 +90,9 @@ _PP, _BP, _RP = ctypes.POINTER(SamplePolicy), ctypes.POINTER(Budget), ctypes.POI
 SIGNATURES = {
     "bigmeans_fit": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
     "bigmeans_fit_dt": (_i32, [_p, _p, _i32, _i64, _i32, _i32, _PP, _BP, _u64, _i32, _p, _p, _p, _RP]),
+    "bm_fit_state_size": (_i32, [_p, ctypes.POINTER(_i64)]),
+    "bm_fit_export": (_i32, [_p, _p, _i64]),
+    "bm_fit_import": (_i32, [_p, _p, _i64]),
     "bigmeans_fit_host": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, _p, _p, _RP]),
     "bm_fit_create": (_i32, [_p, _i64, _i32, _i32, _PP, _BP, _u64, _p, ctypes.POINTER(_p)]),
     "bm_fit_rounds": (_i32, [_p, _i32]),
@@ -271,6 +274,19 @@ class FitSession:
         rep = Report()
         _check(lib.bm_fit_report(self.ctx, ctypes.byref(rep)))
         return rep.as_dict()
+
+    def export_state(self):
+        """bm_fit_export: the fit's state between rounds, as bytes."""
+        n = _i64(0)
+        _check(lib.bm_fit_state_size(self.ctx, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(int(n.value))
+        _check(lib.bm_fit_export(self.ctx, buf, n.value))
+        return buf.raw
+
+    def import_state(self, state):
+        """bm_fit_import: continue from a state exported by another session of the same fit."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(lib.bm_fit_import(self.ctx, buf, len(state)))
 
     def set_workers(self, w_begin, w_end):
         """bm_fit_set_workers: run only workers [w_begin, w_end) (a shard of the fit)."""
