@@ -243,35 +243,6 @@ __device__ __forceinline__ bool fixed_of(float x, int gx, unsigned int& inexact,
     return true;
 }
 
-// The same integer in two signed parts, x / 2^gx = hi 2^48 + lo with
-// |hi|, |lo| < 2^48 (both with the sign of x): sums of up to 2^15 of them
-// stay exact in int64 registers.
-__device__ __forceinline__ bool fixed48_of(float x, int gx, unsigned int& inexact, long long& hi, long long& lo) {
-    hi = lo = 0;
-    const uint32_t bits = __float_as_uint(x);
-    const uint32_t mag = bits & 0x7fffffffu;
-    if (mag == 0) return true;
-    uint32_t mant; int e2;
-    f32_parts(mag, mant, e2);
-    int sh = e2 - gx;
-    if (sh < 0) {
-        const int r = -sh;
-        if (r >= 24) { inexact++; return true; }
-        if (mant & ((1u << r) - 1u)) inexact++;
-        mant >>= r;
-        sh = 0;
-        if (!mant) return true;
-    }
-    if (sh + (32 - __clz((int)mant)) > 96) return false;
-    const unsigned long long m = mant;
-    unsigned long long h, l;
-    if (sh >= 48) { h = m << (sh - 48); l = 0; }
-    else { l = (m << sh) & ((1ull << 48) - 1ull); h = sh ? (m >> (48 - sh)) : 0ull; }
-    hi = (bits >> 31) ? -(long long)h : (long long)h;
-    lo = (bits >> 31) ? -(long long)l : (long long)l;
-    return true;
-}
-
 // Correctly rounded double of a (signed) 128-bit integer times 2^g.
 __device__ __forceinline__ double i128_to_double(__int128 v, int g) {
     if (v == 0) return 0.0;

@@ -269,8 +269,9 @@ struct Worker {
     // cluster without per-element atomics: the rows are bucketed by label
     // (counting sort of 16-bit row offsets in shared memory), each warp walks
     // an equal share of the sorted rows with its lanes over (row, dimension),
-    // keeps the exact sum in registers (two int64 parts of 48-bit-aligned
-    // pieces) and adds it to the owner's words once per cluster it meets.
+    // in batches whose loads are issued one batch ahead, keeps the exact sum
+    // in registers (two int64 parts of 48-bit-aligned pieces) and adds it to
+    // the owner's words once per cluster it meets.
     __device__ bool bucket_sums(long long lo, long long hi, unsigned int& inex) {
         const int nrows = (int)(hi - lo);
         __syncthreads();                                   // labs and lcnt complete
@@ -303,36 +304,70 @@ struct Worker {
         constexpr int LPR = NP < 32 ? NP : 32;             // lanes per row
         constexpr int RPS = 32 / LPR;                      // rows per warp step
         constexpr int DPL = NP / LPR;                      // dimensions per lane (2 for NP = 64)
-        constexpr int U = 4;                               // steps whose loads are issued together
+        constexpr int U = 4;                               // steps per batch
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         const int sub = lane / LPR, d0 = lane % LPR;
         const int b0 = (int)((long long)nrows * wid / (TPB / 32));
         const int b1 = (int)((long long)nrows * (wid + 1) / (TPB / 32));
         const float* Sl = S + lo * NP;
         bool ok = true;
-        int j = 0;                                         // cluster of this lane's current row
-        int cur = -1;
+        int cur = -1;                                      // cluster of this lane's running sum
         long long shi[DPL], slo[DPL];
 #pragma unroll
         for (int t = 0; t < DPL; ++t) shi[t] = slo[t] = 0;
-        for (int p0 = b0 + sub; p0 < b1; p0 += U * RPS) {
-            float xv[U][DPL];
+        // x 2^-gx as two exact power-of-two factors (each at most 2^127)
+        const int eg = -g.gx;
+        const int e1 = eg > 127 ? 127 : eg;
+        const float s1 = __int_as_float((unsigned)(e1 + 127) << 23);
+        const float s2 = __int_as_float((unsigned)(eg - e1 + 127) << 23);
+        // the rows of a batch (values and labels); the next batch is loaded
+        // while this one is converted and added
+        auto load_batch = [&](int q0, float (&xv)[U][DPL], int (&jl)[U]) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int p = p0 + u * RPS;
+                const int p = q0 + u * RPS;
                 const int r = p < b1 ? sm.rowlist[p] : 0;
+                jl[u] = p < b1 ? (int)sm.labs[r] : -1;
 #pragma unroll
                 for (int t = 0; t < DPL; ++t) {
                     const int d = d0 + t * LPR;
                     xv[u][t] = (p < b1 && d < n) ? Sl[(long long)r * NP + d] : 0.f;
                 }
             }
+        };
+        float xn[U][DPL];
+        int jn[U];
+        load_batch(b0 + sub, xn, jn);
+        for (int p0 = b0 + sub; p0 < b1; p0 += U * RPS) {
+            long long hv[U][DPL], lv[U][DPL];
+            int jv[U];
+            // the batch's coordinates on the grid, all at once, without
+            // branches: y = x 2^-gx exactly (|y| < 2^96 by the choice of gx),
+            // y = hf 2^48 + lf with hf an integer and lf the exact remainder,
+            // whose bits below the grid are truncated (and counted): the
+            // integer fixed_of gives, split at 2^48
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int p = p0 + u * RPS;
-                if (p >= b1) break;
-                while (sm.lstart[j + 1] <= p) ++j;
-                if (j != cur) {
+                jv[u] = jn[u];
+#pragma unroll
+                for (int t = 0; t < DPL; ++t) {
+                    const float y = __fmul_rn(__fmul_rn(xn[u][t], s1), s2);
+                    const float hf = truncf(__fmul_rn(y, 0x1p-48f));
+                    const float lf = __fmaf_rn(-hf, 0x1p48f, y);
+                    const float lt = truncf(lf);
+                    inex += (lf != lt) ? 1u : 0u;
+                    ok &= fabsf(y) < 0x1p96f;
+                    hv[u][t] = __float2ll_rz(hf);
+                    lv[u][t] = __float2ll_rz(lt);
+                }
+            }
+            if (p0 + U * RPS < b1) load_batch(p0 + U * RPS, xn, jn);
+            // rows are sorted by cluster: a running sum per lane, added to the
+            // owner's words when the cluster changes
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (jv[u] < 0) break;                      // past this warp's rows
+                if (jv[u] != cur) {
                     if (cur >= 0)
 #pragma unroll
                         for (int t = 0; t < DPL; ++t) {
@@ -340,14 +375,12 @@ struct Worker {
                                       ((__int128)shi[t] << 48) + (__int128)slo[t]);
                             shi[t] = slo[t] = 0;
                         }
-                    cur = j;
+                    cur = jv[u];
                 }
 #pragma unroll
                 for (int t = 0; t < DPL; ++t) {
-                    long long h, l;
-                    ok &= fixed48_of(xv[u][t], g.gx, inex, h, l);
-                    shi[t] += h;
-                    slo[t] += l;
+                    shi[t] += hv[u][t];
+                    slo[t] += lv[u][t];
                 }
             }
         }
