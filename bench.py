@@ -530,6 +530,20 @@ def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
     t_tc0, _ = _timed(lambda: native.assign_bf16(P, C, tau=0.0), steps, warmup, flush)
     t_ex, (Ye, fe, re_) = _timed(lambda: native.assign(Xd, C), steps, warmup, flush)
     t_ce, (Yc, fc, rc) = _timed(lambda: native.assign_bf16(P, C, tau=1e-3, certified=True), steps, warmup, flush)
+    # the fit entry point in both modes, X packed once beside its FP32 master:
+    # the wall time of each call and the gap of the fast mode's f(C_best, X)
+    pol_f = native.make_policy(s_min=20000, s_max=60000, workers=8, passes=4)
+    bud_f = native.make_budget(rounds=1)
+    t_fx, (_, _, r_fx) = _timed(lambda: native.fit_dt(Xd, k, pol_f, bud_f, seed=3, mode=native.BM_MODE_EXACT),
+                                3, 1, flush)
+    t_ff, (_, _, r_ff) = _timed(lambda: native.fit_dt(P, k, pol_f, bud_f, seed=3, mode=native.BM_MODE_FAST),
+                                3, 1, flush)
+    gap = abs(r_ff["f_full"] - r_fx["f_full"]) / r_fx["f_full"]
+    fit_modes = {"exact_ms": t_fx * 1e3, "fast_ms": t_ff * 1e3, "f_exact": r_fx["f_full"],
+                 "f_fast": r_ff["f_full"], "f_rel_gap": gap, "within_1e-4": bool(gap <= 1e-4),
+                 "what": "bigmeans_fit_dt (W = 8, p = 4, T = 1, s in [20000, 60000]) in exact mode on the FP32 X "
+                         "and in fast mode on the packed X: labels and f(C_best, X) from the exact pass or from "
+                         "the precision pass (tau = 1e-3); the fit itself is the same"}
     clk = clocks.stop()
     # the same forms on the first rows, for the comparison with the FP64 oracle
     ns = min(slice_rows, m)
@@ -565,6 +579,7 @@ def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
                           "rescored_rows": rc["rescored_rows"],
                           "label_mismatch_vs_exact": int((Yc != Ye).sum().item()),
                           "f_rel_err_vs_exact": abs(fc - fe) / fe},
+            "fit_modes": fit_modes,
             "clocks": clk}
     del P, Ps, Xd, Xs
     torch.cuda.empty_cache()
@@ -699,7 +714,8 @@ def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
     `pool_size` data sets of such shapes, generated on the device before the
     clock starts and kept in pinned host memory; a job's latency runs from its
     arrival (submit) to its result on the host (H2D copy, Algorithm 1, the
-    full-data pass -- BF16 for BF16 jobs -- and the D2H copy included)."""
+    full-data pass -- BF16 for BF16 jobs -- and the D2H copy included);
+    `without_h2d` gives the same less each job's copy of X to the device."""
     import torch
     from paper_2403_18766_gb300 import native
     from paper_2403_18766_gb300.synthetic import gaussian_mixture_device
@@ -739,6 +755,7 @@ def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
     st = ctx.stats()
     ctx.close()
     lat = np.array([r["t_done_s"] - r["t_submit_s"] for r in res])
+    lat_nocopy = np.array([r["t_done_s"] - r["t_submit_s"] - r["report"]["t_h2d_s"] for r in res])
     qwait = np.array([r["t_admit_s"] - r["t_submit_s"] for r in res])
     ok = all(r["status"] == native.BM_OK for r in res)
     errors = sorted({r.get("error", "") for r in res if r["status"] != native.BM_OK})
@@ -747,6 +764,9 @@ def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
     return {"metric": "p50/p99 job latency (serving, continuous batching)",
             "value": float(np.percentile(lat, 99)) * 1e3, "unit": "ms (p99)", "higher_is_better": False,
             "p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3,
+            "without_h2d": {"p50_ms": float(np.percentile(lat_nocopy, 50)) * 1e3,
+                            "p99_ms": float(np.percentile(lat_nocopy, 99)) * 1e3,
+                            "what": "the same latencies less each job's copy of X to the device (CUDA events)"},
             "queue_wait_p50_ms": float(np.percentile(qwait, 50)) * 1e3,
             "jobs": n_jobs, "bf16_jobs": int(sum(j[5] for j in jobs)), "all_ok": ok, "errors": errors[:3],
             "makespan_s": t_end, "jobs_per_s": n_jobs / t_end,

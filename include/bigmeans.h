@@ -148,6 +148,9 @@ typedef struct {
                                  barrier, [13] centroid pull + prep     */
     double t_sample_s;      /* device time of the sampling launches (part of
                                t_worker_s)                                    */
+    double t_h2d_s;         /* host-buffer calls (bigmeans_fit_host, serving
+                               jobs): device time of the copy of X to the
+                               device (CUDA events); 0 elsewhere               */
 } bm_report;
 
 /* ---------------------------------------------------------------------------

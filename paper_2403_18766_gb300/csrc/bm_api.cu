@@ -1455,7 +1455,12 @@ bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k
         cudaStreamSynchronize(st);
         return fail(BM_ENOMEM, "device buffers for the host-buffer fit");
     }
+    cudaEvent_t hc[2] = {nullptr, nullptr};              // around the copy of X
+    if (cudaEventCreate(&hc[0]) != cudaSuccess || cudaEventCreate(&hc[1]) != cudaSuccess) cudaGetLastError();
+    if (hc[0]) cudaEventRecord(hc[0], st);
     cudaError_t e = cudaMemcpyAsync(Xd, X_host, xb, cudaMemcpyHostToDevice, st);
+    if (hc[1]) cudaEventRecord(hc[1], st);
+    float h2d_ms = 0.f;
     if (e == cudaSuccess) {
         s = bigmeans_fit(Xd, m, n, k, policy, budget, seed, stream, Cd, Ld, rep);
         if (s == BM_OK) {
@@ -1468,10 +1473,16 @@ bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k
     cudaFreeAsync(Cd, st);
     if (Ld) cudaFreeAsync(Ld, st);
     const cudaError_t e2 = cudaStreamSynchronize(st);
+    if (hc[0] && hc[1] && cudaEventElapsedTime(&h2d_ms, hc[0], hc[1]) != cudaSuccess) cudaGetLastError();
+    for (cudaEvent_t ev : hc)
+        if (ev) cudaEventDestroy(ev);
     if (s) return s;
     if (e != cudaSuccess) return fail(BM_ECUDA, "copy: %s", cudaGetErrorString(e));
     if (e2 != cudaSuccess) return fail(BM_ECUDA, "sync: %s", cudaGetErrorString(e2));
-    if (rep) rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) {
+        rep->t_total_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        rep->t_h2d_s = h2d_ms * 1e-3;
+    }
     return BM_OK;
 }
 

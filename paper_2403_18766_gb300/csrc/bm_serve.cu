@@ -76,8 +76,12 @@ bm_status run_bf16_job(const bm_job& s, cudaStream_t st, bm_report* rep, double*
     alloc((void**)&raw, (size_t)m_pad * 128 + 1024);
     alloc((void**)&norms, (size_t)(m_pad + 1) * 4);
     alloc((void**)&Ld, (size_t)m * 4);
+    cudaEvent_t hc[2] = {nullptr, nullptr};              // around the copy of X
+    if (cudaEventCreate(&hc[0]) != cudaSuccess || cudaEventCreate(&hc[1]) != cudaSuccess) cudaGetLastError();
+    if (hc[0]) cudaEventRecord(hc[0], st);
     if (r == BM_OK && cudaMemcpyAsync(Xd, s.X_host, (size_t)m * s.n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess)
         r = set_error(BM_ECUDA, "copy of X");
+    if (hc[1]) cudaEventRecord(hc[1], st);
     if (r == BM_OK) r = bigmeans_fit(Xd, m, s.n, s.k, &s.policy, &s.budget, s.seed, st, Cd, nullptr, rep);
     void* Xb = raw ? (void*)(raw + ((1024 - ((uintptr_t)raw & 1023)) & 1023)) : nullptr;
     if (r == BM_OK) r = bm_pack_bf16(Xd, m, s.n, Xb, norms, st);
@@ -92,7 +96,14 @@ bm_status run_bf16_job(const bm_job& s, cudaStream_t st, bm_report* rep, double*
     for (void* p : {(void*)Xd, (void*)Cd, (void*)raw, (void*)norms, (void*)Ld})
         if (p) cudaFreeAsync(p, st);
     if (cudaStreamSynchronize(st) != cudaSuccess && r == BM_OK) r = set_error(BM_ECUDA, "job stream");
-    if (rep) rep->rescored_rows += rb.rescored_rows;
+    float h2d_ms = 0.f;
+    if (hc[0] && hc[1] && cudaEventElapsedTime(&h2d_ms, hc[0], hc[1]) != cudaSuccess) cudaGetLastError();
+    for (cudaEvent_t ev : hc)
+        if (ev) cudaEventDestroy(ev);
+    if (rep) {
+        rep->rescored_rows += rb.rescored_rows;
+        rep->t_h2d_s = h2d_ms * 1e-3;
+    }
     return r;
 }
 

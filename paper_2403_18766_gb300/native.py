@@ -43,7 +43,8 @@ class Report(ctypes.Structure):
                 ("t_total_s", ctypes.c_double), ("t_worker_s", ctypes.c_double),
                 ("t_fullpass_s", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("fullpass_launches", ctypes.c_int64), ("reseeded", ctypes.c_int64),
-                ("trace_cycles", ctypes.c_int64 * 16), ("t_sample_s", ctypes.c_double)]
+                ("trace_cycles", ctypes.c_int64 * 16), ("t_sample_s", ctypes.c_double),
+                ("t_h2d_s", ctypes.c_double)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
