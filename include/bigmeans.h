@@ -425,8 +425,9 @@ bm_status bm_assign_noalloc(const float* X_dev, int64_t m, int32_t n, const floa
  *          FP32-ALU pass;
  *   impl 1: always the FP32-ALU pass (register-tiled expanded form, certified,
  *          uncertain rows re-scored in FP32);
- *   impl 2: the tensor-core pass (tcgen05, TF32 products of the expanded
- *          form, certified, uncertain rows re-scored in FP32) where it
+ *   impl 2: the tensor-core pass (tcgen05, split-TF32 products of the
+ *          expanded form, certified, uncertain rows decided in the FP32
+ *          direct form among the centroids the certificate leaves) where it
  *          applies -- n % 4 == 0, X 16-byte aligned, k <= 256 -- else the
  *          FP32-ALU pass.
  * Any other value is rejected with BM_EINVAL.  The setting is process-wide;
