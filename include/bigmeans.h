@@ -190,7 +190,8 @@ bm_status bigmeans_fit_host(const float* X_host, int64_t m, int32_t n, int32_t k
  *                 precision pass, bm_assign_bf16 with tau = 1e-3, on the BF16
  *                 rows (BM_F32: packed into a workspace of m_pad x 128 bytes
  *                 first); report->f_full is that f and report->rescored_rows
- *                 its re-scored rows.  n <= 64.
+ *                 its re-scored rows.  n <= 64 and k <= 256 (checked before
+ *                 the fit runs).
  * Other arguments, ownership and errors as for bigmeans_fit; BM_EINVAL for
  * an unknown dt or mode, a missing master, or a misaligned BF16 X_dev.
  * ------------------------------------------------------------------------- */

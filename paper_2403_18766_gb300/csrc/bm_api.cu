@@ -1402,7 +1402,7 @@ bm_status bigmeans_fit_dt(const void* X_dev, const float* X_master_dev, bm_dtype
     // precision pass (tau = 1e-3) on the BF16 rows
     bm_status s = check_shape(m, n, k);
     if (s) return s;
-    if (n > 64) return fail(BM_EINVAL, "BM_MODE_FAST needs n <= 64");
+    if (n > 64 || k > 256) return fail(BM_EINVAL, "BM_MODE_FAST needs n <= 64 and k <= 256");
     if (dt == BM_BF16 && (((uintptr_t)X_dev) & 1023)) return fail(BM_EINVAL, "BF16 X_dev must be 1024-byte aligned");
     bm_fit_ctx* c = nullptr;
     if ((s = bm_fit_create(Xf, m, n, k, policy, budget, seed, stream, &c))) return s;
