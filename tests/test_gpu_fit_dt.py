@@ -80,3 +80,9 @@ def test_invalid_dtype_mode_and_master():
     other = Xd.clone()
     assert call(native.BM_F32, native.BM_MODE_EXACT, other) == native.BM_EINVAL       # master not X
     assert call(native.BM_F32, native.BM_MODE_EXACT, Xd) == native.BM_OK              # master = X is fine
+    C300 = torch.empty((300, n), dtype=torch.float32, device="cuda")
+    st = native.lib.bigmeans_fit_dt(native._ptr(Xd), native._ptr(None), native.BM_F32, m, n, 300,
+                                    ctypes.byref(native.make_policy(s_min=600, s_max=4000, workers=2, passes=1)),
+                                    ctypes.byref(bud), 1, native.BM_MODE_FAST, native._stream(None), native._ptr(C300),
+                                    native._ptr(None), ctypes.byref(rep))
+    assert st == native.BM_EINVAL and "k <= 256" in native.lib.bm_last_error().decode()
