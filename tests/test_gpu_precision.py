@@ -73,7 +73,9 @@ def test_pack_bf16_layout_and_norms(m, n):
     assert P.norms[m_pad].item() == X.abs().max().item()
 
 
-CASES = [(100_003, 64, 100), (5000, 40, 17), (384, 16, 256), (1000, 8, 3), (70_001, 16, 25)]
+# n = 30 (not a multiple of 4): the re-score kernel reads its rows element by
+# element; the other n with 16-byte loads
+CASES = [(100_003, 64, 100), (5000, 40, 17), (384, 16, 256), (1000, 8, 3), (70_001, 16, 25), (20_011, 30, 40)]
 
 
 @pytest.mark.parametrize("m,n,k", CASES)
@@ -166,16 +168,16 @@ def test_certified_near_ties_and_far_from_origin():
 
 def test_queued_rows_resolved_among_their_candidates():
     """A close call carries the centroids whose BF16 g lies within the
-    certificate threshold of the least (at most four; more are flagged for
-    all k).  Groups of 4 and of 6 nearly equal centroids near the origin
+    certificate threshold of the least (at most eight; more are flagged for
+    all k).  Groups of 4 and of 11 nearly equal centroids near the origin
     exercise both: with tau = inf every row is queued, and labels and f must
     equal the exact pass and the oracle bit for bit."""
     X = gaussian_mixture(30_000, 32, 6, seed=29)
     rng = np.random.default_rng(31)
-    C = X[rng.integers(0, X.shape[0], 16)].copy()
+    C = X[rng.integers(0, X.shape[0], 20)].copy()
     for j in (1, 2, 3):                                  # 4 centroids within 1e-3 of C[0]
         C[j] = C[0] + np.float32(1e-3 * j)
-    for j in (5, 6, 7, 8, 9):                            # 6 within 1e-3 of C[4]: all k
+    for j in range(5, 15):                               # 11 within 1e-2 of C[4]: all k
         C[j] = C[4] - np.float32(1e-3 * (j - 4))
     Xd, Cd = torch.from_numpy(X).cuda(), torch.from_numpy(C).cuda()
     P = native.PackedBF16(Xd)
@@ -187,8 +189,30 @@ def test_queued_rows_resolved_among_their_candidates():
         Y, f, rep = native.assign_bf16(P, Cd, tau=math.inf, certified=certified)
         assert rep["rescored_rows"] == X.shape[0]
         assert torch.equal(Y, Yr) and f == fr
-    counts = np.bincount(lab, minlength=16)
-    assert counts[0:4].sum() > 0 and counts[4:10].sum() > 0   # both groups are nearest to some rows
+    counts = np.bincount(lab, minlength=20)
+    assert counts[0:4].sum() > 0 and counts[4:15].sum() > 0   # both groups are nearest to some rows
     Y, f, rep = native.assign_bf16(P, Cd, tau=0.0, certified=True)
     assert torch.equal(Y, Yr)
     assert 0 < rep["rescored_rows"] < X.shape[0]
+
+
+@pytest.mark.parametrize("tau", [1e-3, math.inf])
+def test_rescore_of_aligned_and_misaligned_master_agree(tau):
+    """The same FP32 master at a 16-byte aligned and at a misaligned address:
+    the re-score kernel reads the queued rows with 16-byte loads in the first
+    case and element by element in the second; labels, f and the re-scored
+    count agree."""
+    m, n, k = 50_021, 32, 60
+    X, C = _case(m, n, k, 23)
+    P = native.PackedBF16(X)
+    Y0, f0, r0 = native.assign_bf16(P, C, tau=tau)
+    raw = torch.empty(m * n + 4, dtype=torch.float32, device="cuda")
+    Xu = raw[1:1 + m * n].view(m, n)                     # 4 bytes past a 16-byte boundary
+    Xu.copy_(X)
+    assert Xu.data_ptr() % 16 == 4
+    P.X = Xu
+    Y1, f1, r1 = native.assign_bf16(P, C, tau=tau)
+    assert torch.equal(Y0, Y1) and f0 == f1
+    assert r0["rescored_rows"] == r1["rescored_rows"] > 0
+    if tau == math.inf:
+        assert r0["rescored_rows"] == m
