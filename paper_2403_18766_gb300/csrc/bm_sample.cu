@@ -72,7 +72,8 @@ __device__ __forceinline__ long long pow2_at_least(long long v) {
 }
 
 // The same sample with a shared-memory bitmap of the m values (used when it
-// fits): the draws are taken in chunks of kSampleThreads in counter order.  A draw
+// fits): the draws are taken in chunks of kSampleDraws x kSampleThreads in
+// counter order, kSampleDraws consecutive draws per thread.  A draw
 // t of value r is the first occurrence of r when r's bit is clear at the
 // start of t's chunk and t is the least draw of r inside the chunk (a small
 // shared hash table keyed by r keeps that least t).  The chunk's first
@@ -89,36 +90,58 @@ __device__ long long sample_by_bitmap(const SampleArgs& a, long long s, unsigned
     __syncthreads();
     const unsigned long long thr = lemire_thr((unsigned long long)m);
     long long got = 0;
-    for (long long t0 = 0; t0 < cap && got < s; t0 += kSampleThreads) {     // block-uniform
-        const long long t = t0 + threadIdx.x;
-        unsigned int r = 0, h = 0;
-        bool cand = false;
-        if (t < cap) {
-            const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
-            r = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
-            cand = ((bits[r >> 5] >> (r & 31)) & 1u) == 0u;
-        }
-        const unsigned long long key = ((unsigned long long)r << 32) | (unsigned int)t;
-        if (cand) {   // at most kSampleThreads keys in 2 kSampleThreads slots: a free slot always exists
-            h = tab_hash(r) & (kMiniSlots - 1);
-            for (int p = 0; p < kMiniSlots; ++p) {
-                unsigned long long cur = mini[h];
-                if (cur == ~0ull) {
-                    cur = atomicCAS(&mini[h], ~0ull, key);
-                    if (cur == ~0ull) break;
+    constexpr int D = kSampleDraws;
+    for (long long t0 = 0; t0 < cap && got < s; t0 += (long long)D * kSampleThreads) {     // block-uniform
+        unsigned int r[D], h[D];
+        bool cand[D];
+        unsigned long long key[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {             // this thread's D consecutive draws
+            const long long t = t0 + (long long)D * threadIdx.x + d;
+            r[d] = 0; h[d] = 0; cand[d] = false;
+            if (t < cap) {
+                const P4 blk = philox4x64_10((unsigned long long)t, 0, 0, 0, a.seed, k1);
+                r[d] = (unsigned int)uniform_below(blk, (unsigned long long)m, thr);
+                cand[d] = ((bits[r[d] >> 5] >> (r[d] & 31)) & 1u) == 0u;
+            }
+            key[d] = ((unsigned long long)r[d] << 32) | (unsigned int)t;
+            // at most D kSampleThreads keys in 2 D kSampleThreads slots: a
+            // free slot always exists
+            if (cand[d]) {
+                h[d] = tab_hash(r[d]) & (kMiniSlots - 1);
+                for (int p = 0; p < kMiniSlots; ++p) {
+                    unsigned long long cur = mini[h[d]];
+                    if (cur == ~0ull) {
+                        cur = atomicCAS(&mini[h[d]], ~0ull, key[d]);
+                        if (cur == ~0ull) break;
+                    }
+                    if ((unsigned int)(cur >> 32) == r[d]) { atomicMin(&mini[h[d]], key[d]); break; }
+                    h[d] = (h[d] + 1u) & (kMiniSlots - 1);
                 }
-                if ((unsigned int)(cur >> 32) == r) { atomicMin(&mini[h], key); break; }
-                h = (h + 1u) & (kMiniSlots - 1);
             }
         }
         __syncthreads();
-        const bool first = cand && mini[h] == key;
+        bool first[D];
+        int cnt = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            first[d] = cand[d] && mini[h[d]] == key[d];
+            cnt += first[d];
+        }
         __syncthreads();
-        if (cand) mini[h] = ~0ull;                       // empty again for the next chunk
-        if (first) atomicOr(&bits[r >> 5], 1u << (r & 31));
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            if (cand[d]) mini[h[d]] = ~0ull;             // empty again for the next chunk
+            if (first[d]) atomicOr(&bits[r[d] >> 5], 1u << (r[d] & 31));
+        }
         long long total;
-        const long long excl = block_exscan(first ? 1ll : 0ll, red64, &total);
-        if (first && got + excl < s) idx[got + excl] = (long long)r;
+        long long pos = got + block_exscan((long long)cnt, red64, &total);
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (first[d]) {
+                if (pos < s) idx[pos] = (long long)r[d];
+                ++pos;
+            }
         got += total;
     }
     __syncthreads();

@@ -90,11 +90,12 @@ struct SampleArgs {
     Globals* glob;
 };
 
-// Threads of a sampling CTA (one CTA per sample): the draws are taken in
-// chunks of this many, in counter order.
+// Threads of a sampling CTA (one CTA per sample).
 constexpr int kSampleThreads = 1024;
-// Slots of the per-chunk hash table of the bitmap path (2 per thread).
-constexpr int kMiniSlots = 2 * kSampleThreads;
+// Draws per thread in a chunk of the bitmap path, and the slots of its
+// per-chunk hash table (2 per draw).
+constexpr int kSampleDraws = 2;
+constexpr int kMiniSlots = 2 * kSampleDraws * kSampleThreads;
 // Dynamic shared memory of a sampling launch.
 inline size_t sample_smem_bytes(int bitmap_words) {
     return bitmap_words > 0 ? (size_t)kMiniSlots * 8 + (((size_t)bitmap_words * 4 + 15) & ~(size_t)15) : 0;
