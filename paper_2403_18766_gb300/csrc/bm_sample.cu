@@ -246,29 +246,42 @@ __global__ void __launch_bounds__(kSampleThreads, 1) sample_kernel(const SampleA
         return;
     }
     // gather (padded rows, zeros in the padding); 16-byte loads when the rows
-    // of X are 16-byte aligned
+    // of X are 16-byte aligned.  A thread takes kGatherBatch items (16-byte
+    // pieces of padded rows) at a time: their row indices, then their loads,
+    // are all in flight together, so that a large sample does not pay two
+    // dependent memory latencies per item.
     const int n = a.n;
     const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(a.X) & 15) == 0;
-    const long long items = s * (NP / 4);
-    for (long long e = threadIdx.x; e < items; e += kSampleThreads) {
-        const long long i = e / (NP / 4);
-        const int q = (int)(e % (NP / 4));
-        const long long row = idx[i];
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row >= 0 && row < a.m) {
-            const float* xr = a.X + row * (long long)n;
-            if (vec) {
-                if (4 * q < n) v = __ldg(reinterpret_cast<const float4*>(xr) + q);
-            } else {
-                v.x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
-                v.y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
-                v.z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
-                v.w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+    constexpr int U = kGatherBatch;
+    constexpr int RS = kSampleThreads / (NP / 4);          // rows a pass of the CTA covers
+    static_assert(kSampleThreads % (NP / 4) == 0, "a thread keeps its piece q of every row");
+    const int q = threadIdx.x % (NP / 4);                  // this thread's 16-byte piece of a row
+    for (long long i0 = threadIdx.x / (NP / 4); i0 < s; i0 += (long long)U * RS) {
+        long long row[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) row[u] = (i0 + u * RS < s) ? idx[i0 + u * RS] : 0;
+        float4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i0 + u * RS >= s) continue;
+            if (row[u] >= 0 && row[u] < a.m) {
+                const float* xr = a.X + row[u] * (long long)n;
+                if (vec) {
+                    if (4 * q < n) v[u] = __ldg(reinterpret_cast<const float4*>(xr) + q);
+                } else {
+                    v[u].x = (4 * q + 0 < n) ? xr[4 * q + 0] : 0.f;
+                    v[u].y = (4 * q + 1 < n) ? xr[4 * q + 1] : 0.f;
+                    v[u].z = (4 * q + 2 < n) ? xr[4 * q + 2] : 0.f;
+                    v[u].w = (4 * q + 3 < n) ? xr[4 * q + 3] : 0.f;
+                }
+            } else if (q == 0) {
+                atomicOr(&a.glob->err, kErrArgs);
             }
-        } else if (q == 0) {
-            atomicOr(&a.glob->err, kErrArgs);
         }
-        reinterpret_cast<float4*>(S + i * NP)[q] = v;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * RS < s) reinterpret_cast<float4*>(S + (i0 + u * RS) * NP)[q] = v[u];
     }
     if (threadIdx.x == 0 && a.job_s) a.job_s[job] = (int)s;
 }

@@ -96,6 +96,8 @@ constexpr int kSampleThreads = 1024;
 // per-chunk hash table (2 per draw).
 constexpr int kSampleDraws = 2;
 constexpr int kMiniSlots = 2 * kSampleDraws * kSampleThreads;
+// Items a thread of the gather has in flight at once.
+constexpr int kGatherBatch = 8;
 // Dynamic shared memory of a sampling launch.
 inline size_t sample_smem_bytes(int bitmap_words) {
     return bitmap_words > 0 ? (size_t)kMiniSlots * 8 + (((size_t)bitmap_words * 4 + 15) & ~(size_t)15) : 0;
