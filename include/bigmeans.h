@@ -491,8 +491,9 @@ int32_t bm_get_big_clusters(void);
  * s distinct points, here the first s distinct values of the job's counter
  * stream of bounded draws, in order of first occurrence).  impl 0 (default):
  * a shared-memory bitmap of the m indices where it fits (m up to about
- * 1.1e6, less when the worker's shared memory is large), else per-job
- * open-addressing tables in device memory; impl 1: always the tables.
+ * 1.37e6: the bitmap and the per-chunk hash table within 200 KB), else
+ * per-job open-addressing tables in device memory; impl 1: always the
+ * tables.
  * Both give identical samples.  Other values: BM_EINVAL.  Process-wide,
  * read when each sampling launch is prepared. */
 bm_status bm_set_sampler_impl(int32_t impl);
