@@ -104,44 +104,88 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock / throttle sampling around the timed region.
+
+    nvidia-smi samples every `interval_ms` (line-buffered through stdbuf where
+    available) and stamps each sample itself; a reader thread collects the
+    lines.  The constructor waits (up to 3 s) for the first sample, so that
+    sampling is running before the timed region starts; begin() and end()
+    mark the region on the host clock, and stop() summarises the samples
+    stamped inside it (all samples of the run when the region was too short
+    to hold one, said by `in_region`)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    def __init__(self, device_index):
-        self.proc = None
+    def __init__(self, device_index, interval_ms=20):
+        import shutil
+        import threading
+        self.proc, self.lines, self.t0, self.t1 = None, [], None, None
+        self._first = threading.Event()
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", str(interval_ms), "-i", str(device_index)]
+        if shutil.which("stdbuf"):
+            cmd = ["stdbuf", "-oL"] + cmd
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100", "-i", str(device_index)],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self._reader = threading.Thread(target=self._read, daemon=True)
+        self._reader.start()
+        self._first.wait(timeout=3.0)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.count(",") >= 9:
+                self.lines.append(line.strip())
+                self._first.set()
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        from datetime import datetime
+        try:
+            return datetime.strptime(text.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self):
         if not self.proc:
             return None
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+            self.proc.wait()
+        self._reader.join(timeout=5)
+        rows = [r.split(", ") for r in self.lines]
+        rows = [r for r in rows if len(r) >= 10]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        inside = []
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows if (self._stamp(r[0]) or -1.0) >= self.t0 - 0.005
+                      and (self._stamp(r[0]) or -1.0) <= self.t1 + 0.005]
+        use = inside or rows
+        sm = [float(r[2]) for r in use if r[2].strip().replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in use if r[3].strip().replace(".", "").isdigit()]
         reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            for nm, v in zip(names, r[5:9]):
+        for r in use:
+            for nm, v in zip(self.REASONS, r[6:10]):
                 if v.strip() == "Active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(rows)}
+                "reasons": sorted(reasons), "samples": len(use), "in_region": bool(inside),
+                "region_ms": (self.t1 - self.t0) * 1e3 if self.t0 is not None and self.t1 is not None else None}
 
 
 def _traffic_for(kernel_sources):
@@ -297,6 +341,7 @@ def run_ours(args):
         trace.append((t_cum, sess.report()["f_incumbent"]))
     rep0 = sess.report()
     step_ms = []
+    clocks.begin()
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize(dev)
@@ -311,6 +356,7 @@ def run_ours(args):
         step_ms.append(a.elapsed_time(b))
         t_cum += step_ms[-1] / 1e3
         trace.append((t_cum, sess.report()["f_incumbent"]))
+    clocks.end()
     rep1 = sess.report()
     f_end = trace[-1][1]
     tto = next(((t, i + 1) for i, (t, f) in enumerate(trace) if f <= f_end * (1 + 1e-4)), (None, None))
@@ -533,6 +579,7 @@ def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
     P = native.PackedBF16(Xd)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     clocks = ClockSampler(0)
+    clocks.begin()
     t_bf, (Yb, fb, rb) = _timed(lambda: native.assign_bf16(P, C, tau=1e-3), steps, warmup, flush)
     t_tc0, _ = _timed(lambda: native.assign_bf16(P, C, tau=0.0), steps, warmup, flush)
     t_ex, (Ye, fe, re_) = _timed(lambda: native.assign(Xd, C), steps, warmup, flush)
@@ -551,6 +598,7 @@ def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
                  "what": "bigmeans_fit_dt (W = 8, p = 4, T = 1, s in [20000, 60000]) in exact mode on the FP32 X "
                          "and in fast mode on the packed X: labels and f(C_best, X) from the exact pass or from "
                          "the precision pass (tau = 1e-3); the fit itself is the same"}
+    clocks.end()
     clk = clocks.stop()
     # the same forms on the first rows, for the comparison with the FP64 oracle
     ns = min(slice_rows, m)
@@ -656,6 +704,7 @@ def batched_bench(steps=5, warmup=3, rows=None):
         rep0 = [s_.report() for s_ in sess]
         clocks = ClockSampler(0)
         step_ms = []
+        clocks.begin()
         for _ in range(steps):
             flush.fill_(1)
             torch.cuda.synchronize()
@@ -666,6 +715,7 @@ def batched_bench(steps=5, warmup=3, rows=None):
             b.record()
             torch.cuda.synchronize()
             step_ms.append(a.elapsed_time(b))
+        clocks.end()
         clk = clocks.stop()
         rep1 = [s_.report() for s_ in sess]
         fin = {}
@@ -749,6 +799,7 @@ def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
     for Xh, k, pol, bud, sd, bf in jobs[:warmup]:          # warm-up jobs (not timed)
         ctx.wait(ctx.submit(Xh, k, pol, bud, sd, bf16=bf))
     clocks = ClockSampler(0)
+    clocks.begin()
     t0 = time.perf_counter()
     ids = []
     for (Xh, k, pol, bud, sd, bf), at in zip(jobs, arrivals):
@@ -758,6 +809,7 @@ def serve_bench(rate=20.0, n_jobs=40, warmup=3, pool_size=8, seed=5005):
         ids.append(ctx.submit(Xh, k, pol, bud, sd, bf16=bf))
     res = [ctx.wait(j) for j in ids]
     t_end = time.perf_counter() - t0
+    clocks.end()
     clk = clocks.stop()
     st = ctx.stats()
     ctx.close()
