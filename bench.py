@@ -611,13 +611,20 @@ def precision_bench(steps=5, warmup=3, rows=None, slice_rows=200_000):
     peaks, src = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bytes_bf = m * (128 + 4 + 4)                 # packed row + norm + label
+    # DRAM traffic of the call from the committed capture (per row of the
+    # pass, per re-scored row of the re-score kernel), while the sources match
+    tr, digest_tc = _traffic_for([os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
+                                  for f in ("bm_tc.cu", "bm_tcgen05.cuh", "bm_device.cuh")])
+    traffic_bf = (tr["dram_bytes_per_row"] * m + tr["dram_bytes_per_rescored_row"] * rb["rescored_rows"]
+                  if tr and "dram_bytes_per_row" in tr else None)
     line = {"metric": "precision-form full pass (labels + f)", "value": bytes_bf / t_bf / 1e9,
             "unit": "GB/s", "higher_is_better": True, "steps": steps, "warmup": warmup,
             "config": {"workload": f"gmm_10m_n64_k100z: m={m}, n=64, 100 Gaussians (Zipf 1.2), k=100",
                        "dtype": "bf16 distance tiles, FP32 accumulate (tcgen05), FP32 re-score",
                        "tau": 1e-3, "l2": "flushed between calls"},
             "roofline": {"bound": "hbm", "achieved": bytes_bf / t_bf / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": bytes_bf / t_bf / 1e9 / hbm, "traffic": None,
+                         "frac": bytes_bf / t_bf / 1e9 / hbm, "traffic": traffic_bf,
+                         "source_digest": digest_tc,
                          "kernel": "tc_fullpass_kernel + rescore_kernel (tcgen05.mma kind::f16, 1-D bulk tiles)",
                          "algorithmic": "136 bytes per row (128 B packed row, 4 B norm, 4 B label)",
                          "peak_source": src},
