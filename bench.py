@@ -188,8 +188,10 @@ class ClockSampler:
                 "region_ms": (self.t1 - self.t0) * 1e3 if self.t0 is not None and self.t1 is not None else None}
 
 
-def _traffic_for(kernel_sources):
-    """DRAM bytes per launch from a committed ncu summary, if it matches the source."""
+def _traffic_for(kernel_sources, workload=None):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the
+    source (entries keyed by the digest of the sources, and by the workload
+    where one kernel has captures of several)."""
     h = hashlib.sha256()
     for p in kernel_sources:
         with open(p, "rb") as fh:
@@ -200,7 +202,7 @@ def _traffic_for(kernel_sources):
             tr = json.load(fh)
     except OSError:
         return None, digest
-    ent = tr.get(digest)
+    ent = tr.get(f"{digest}/{workload}" if workload else digest)
     return (ent if ent else None), digest
 
 
@@ -741,11 +743,14 @@ def batched_bench(steps=5, warmup=3, rows=None):
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", NOMINAL_MAX_MHZ))
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    tr, digest = _traffic_for([os.path.join(ROOT, "paper_2403_18766_gb300", "csrc", f)
+                               for f in ("bm_worker_impl.cuh", "bm_worker.cuh", "bm_device.cuh")], "gmm_4m_n32_k50o")
     return {"metric": "Lloyd pts·k/s (batched workers, workload 3)", "value": ptsk / t, "unit": UNIT,
             "higher_is_better": True, "steps": steps, "warmup": warmup,
             "ms_per_step": t * 1e3 / steps, "dtype": "f32", "data": "synthetic",
             "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": flops / t / 1e12 / alu_peak,
+                         "traffic": tr.get("dram_bytes_per_launch") if tr else None, "source_digest": digest,
                          "kernel": "worker_kernel<32> (one launch for the 64 workers of the 3 fits) + "
                                    "sample_kernel<32> x 3 per step, CUDA events around the step",
                          "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
